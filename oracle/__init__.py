@@ -1,0 +1,201 @@
+"""ORACLE -- test infrastructure only.
+
+Python front end of the plain FP64 CPU oracle (`cgref.cpp`) for the per-cell
+chemistry of ChemGen (arXiv 2510.10005). Only the tests, the smoke check and
+the CPU baseline of the benchmark may import this package; the product path
+never does. It shares no code with the CUDA library: the only module both
+sides use is the seeded input generator (`paper_2510_10005_gb300.inputs`),
+which holds none of the method's arithmetic.
+
+State layout here: cell-major, y[c] = (T, C_1..C_ns) (eq. extracted_problem-1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+from . import tableau as _tableau
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libcgref.so")
+R_UNIV = 8314.46261815324
+
+CONV, CONP, CONP_LITERAL = 0, 1, 2
+BE, SDIRK2, SDIRK4 = 0, 1, 2
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (portable flags only)."""
+    src = os.path.join(_HERE, "cgref.cpp")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread",
+                           "-o", tmp, src])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.cgref_mech_create.restype = P
+        lib.cgref_mech_create.argtypes = [ctypes.c_int, ctypes.c_int] + [P] * 14
+        lib.cgref_mech_destroy.argtypes = [P]
+        lib.cgref_thermo.argtypes = [P, ctypes.c_double] + [P] * 6
+        lib.cgref_rates.argtypes = [P, ctypes.c_double, P, P, P, P]
+        lib.cgref_source.argtypes = [P, ctypes.c_int, ctypes.c_long, P, P]
+        lib.cgref_source_complex.argtypes = [P, ctypes.c_int, P, P, P, P]
+        lib.cgref_jacobian.argtypes = [P, ctypes.c_int, ctypes.c_long, P, P]
+        lib.cgref_lu_solve.restype = ctypes.c_int
+        lib.cgref_lu_solve.argtypes = [ctypes.c_int, P, P]
+        lib.cgref_temperature.argtypes = [P, ctypes.c_int, ctypes.c_long, P, P, P, ctypes.c_int, P]
+        lib.cgref_integrate.argtypes = [P, P, P, P, ctypes.c_long, P, P, P, ctypes.c_int]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def lu_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Dense solve with LU and partial pivoting (Section 3.4)."""
+    lib = _load()
+    A = _f64(A).copy(); x = _f64(b).copy()
+    if not lib.cgref_lu_solve(A.shape[0], _p(A), _p(x)):
+        raise np.linalg.LinAlgError("singular matrix")
+    return x
+
+
+def default_opts(**kw) -> dict:
+    o = dict(method=SDIRK4, reactor=CONP, adaptive=1, nsub=1, max_newton=7, max_steps=100000,
+             max_halvings=10, err_filter=1, dt=1e-6, rtol=1e-6, atol=1e-12, newton_tol=0.03,
+             h0=0.0, hmin=1e-20, neg_tol=1e-6)
+    o.update(kw)
+    return o
+
+
+class RefMech:
+    """Oracle handle of one mechanism (host copy)."""
+
+    def __init__(self, mech):
+        self.mech = mech
+        lib = _load()
+        self._keep = [_f64(mech.W), _f64(mech.nasa7), _i32(mech.rtype), _i32(mech.reversible),
+                      _i32(mech.rf_idx), _i32(mech.rf_nu), _i32(mech.rr_idx), _i32(mech.rr_nu),
+                      _f64(mech.arr), _f64(mech.arr0), _f64(mech.troe), _i32(mech.eff_ptr),
+                      _i32(mech.eff_idx) if len(mech.eff_idx) else np.zeros(1, np.int32),
+                      _f64(mech.eff_val) if len(mech.eff_val) else np.zeros(1)]
+        self.h = lib.cgref_mech_create(mech.ns, mech.nr, *[_p(a) for a in self._keep])
+        self.ns, self.nr = mech.ns, mech.nr
+        self.n = mech.ns + 1
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.cgref_mech_destroy(self.h)
+            self.h = None
+
+    # -- single-state helpers -------------------------------------------
+    def thermo(self, T: float) -> dict:
+        """Mass-specific cp, h, u, s, g, cv of every species at T (Table 1)."""
+        out = {k: np.zeros(self.ns) for k in ("cp", "h", "u", "s", "g", "cv")}
+        _load().cgref_thermo(self.h, float(T), *[_p(out[k]) for k in ("cp", "h", "u", "s", "g", "cv")])
+        return out
+
+    def rates(self, T: float, C: np.ndarray):
+        kf, kr, q = np.zeros(self.nr), np.zeros(self.nr), np.zeros(self.nr)
+        C = _f64(C)
+        _load().cgref_rates(self.h, float(T), _p(C), _p(kf), _p(kr), _p(q))
+        return kf, kr, q
+
+    # -- batched over cells (cell-major) -----------------------------------
+    @staticmethod
+    def _state(T, C):
+        T = np.atleast_1d(np.asarray(T, dtype=np.float64))
+        C = np.atleast_2d(np.asarray(C, dtype=np.float64))
+        return np.ascontiguousarray(np.concatenate([T[:, None], C], axis=1))
+
+    def source(self, T, C, reactor: int = CONV) -> np.ndarray:
+        """S = (omega_T, dC/dt) for each cell; returns [N, ns+1]."""
+        y = self._state(T, C)
+        S = np.zeros_like(y)
+        _load().cgref_source(self.h, reactor, y.shape[0], _p(y), _p(S))
+        return S
+
+    def source_complex(self, y: np.ndarray, reactor: int = CONV) -> np.ndarray:
+        y = np.asarray(y, dtype=np.complex128)
+        yr, yi = _f64(y.real), _f64(y.imag)
+        Sr, Si = np.zeros(self.n), np.zeros(self.n)
+        _load().cgref_source_complex(self.h, reactor, _p(yr), _p(yi), _p(Sr), _p(Si))
+        return Sr + 1j * Si
+
+    def jacobian(self, T, C, reactor: int = CONV) -> np.ndarray:
+        """Analytical J = dS/dy, [N, n, n]."""
+        y = self._state(T, C)
+        J = np.zeros((y.shape[0], self.n, self.n))
+        _load().cgref_jacobian(self.h, reactor, y.shape[0], _p(y), _p(J))
+        return J
+
+    def temperature(self, e, Y, T0, iters: int = 5, reactor: int = CONV) -> np.ndarray:
+        e = _f64(np.atleast_1d(e)); Y = _f64(np.atleast_2d(Y)); T0 = _f64(np.atleast_1d(T0))
+        T = np.zeros_like(e)
+        _load().cgref_temperature(self.h, reactor, e.shape[0], _p(e), _p(Y), _p(T0), iters, _p(T))
+        return T
+
+    # -- state conversions (Section 2 definitions) -------------------------
+    def concentrations(self, T, Y, p_or_rho, reactor: int):
+        """C_i = rho Y_i / W_i; rho given (CONV) or rho = p/(R T sum Y/W)."""
+        T = np.asarray(T, dtype=np.float64); Y = np.asarray(Y, dtype=np.float64)
+        if reactor == CONV:
+            rho = np.asarray(p_or_rho, dtype=np.float64)
+        else:
+            rho = np.asarray(p_or_rho) / (R_UNIV * T * (Y / self.mech.W).sum(axis=1))
+        return rho[:, None] * Y / self.mech.W
+
+    def mass_fractions(self, C):
+        rho_i = np.asarray(C) * self.mech.W
+        return rho_i / rho_i.sum(axis=1, keepdims=True)
+
+    def integrate_y(self, y: np.ndarray, opts: dict, nthreads: int = 1):
+        """Integrate states y[N, ns+1] over opts['dt']; returns (y, status, stats)."""
+        o = default_opts(**opts)
+        iopt = _i32([o["method"], o["reactor"], o["adaptive"], o["nsub"], o["max_newton"],
+                     o["max_steps"], o["max_halvings"], o["err_filter"]])
+        dopt = _f64([o["dt"], o["rtol"], o["atol"], o["newton_tol"], o["h0"], o["hmin"],
+                     o["neg_tol"]])
+        tab = _tableau.pack(_tableau.tableau(o["method"]))
+        y = _f64(y).copy()
+        N = y.shape[0]
+        status = np.zeros(N, dtype=np.int32)
+        stats = np.zeros((N, 4), dtype=np.int32)
+        _load().cgref_integrate(self.h, _p(iopt), _p(dopt), _p(tab), N, _p(y), _p(status),
+                                _p(stats), int(nthreads))
+        return y, status, stats
+
+    def integrate(self, T, Y, p_or_rho, opts: dict, nthreads: int = 1):
+        """Integrate cells given (T, Y, p) (CONP) or (T, Y, rho) (CONV) over
+        opts['dt']; returns (T, Y, status, stats)."""
+        reactor = default_opts(**opts)["reactor"]
+        C = self.concentrations(T, Y, p_or_rho, reactor)
+        y = self._state(T, C)
+        y, status, stats = self.integrate_y(y, opts, nthreads)
+        return y[:, 0].copy(), self.mass_fractions(y[:, 1:]), status, stats

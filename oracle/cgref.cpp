@@ -1,0 +1,799 @@
+// ORACLE -- test infrastructure only.
+//
+// A plain, slow, FP64 CPU restatement of the per-cell chemistry of ChemGen
+// (arXiv 2510.10005): thermodynamics (Section 2.1, Table 1), reaction rates
+// (Section 2.2), the temperature source (Section 3, eq. temperature_source;
+// Appendix B, eq. temperature_source_h), the analytical Jacobian (Section 3.2,
+// eqs. derivative_matrices_temp_evol ff.), a dense direct solver (Section 3.4),
+// temperature recovery (Section 2.1, eqs. temperature-nonlinear ff.),
+// backward Euler with Newton (Section 3.2, eqs. Backward_euler,
+// newtons-method-2, jacobian) and the SDIRK schemes in stage-derivative form
+// (Appendix A.1, A.2), plus the step-size control the paper leaves open.
+//
+// It is the reference the CUDA path is checked against. Only the tests, the
+// smoke check and the CPU baseline of the benchmark may load it. It shares no
+// code, header or table with the CUDA library: the two are written
+// independently from the paper. One cell is processed at a time, in the
+// order the paper writes the steps; there is no blocking, fusion or reordering.
+//
+// Units: SI-kmol (C in kmol/m^3, Ea in J/kmol, p in Pa, W in kg/kmol).
+// State y = (T, C_1..C_ns) (eq. extracted_problem-1); S = (omega_T, omega_i).
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+typedef std::complex<double> cplx;
+
+const double R_U = 8314.46261815324;   // universal gas constant, J/(kmol K)
+const double P_REF = 101325.0;         // reference pressure, 1 atm (Section 2.1)
+const double LN10 = 2.302585092994045684;
+
+enum { ELEMENTARY = 0, THREE_BODY = 1, LINDEMANN = 2, TROE = 3 };
+enum { CONV = 0, CONP = 1, CONP_LITERAL = 2 };
+enum { ST_OK = 0, ST_NEWTON_FAIL = 1, ST_STEP_TOO_SMALL = 2, ST_MAX_STEPS = 3, ST_NONFINITE = 4 };
+
+inline double re(double x) { return x; }
+inline double re(const cplx& x) { return x.real(); }
+
+struct Reaction {
+    int type = ELEMENTARY;
+    int reversible = 1;
+    int f_idx[3], f_nu[3], r_idx[3], r_nu[3];
+    double lnA, b, Ea;          // Arrhenius (k_inf for falloff)
+    double lnA0, b0, Ea0;       // low-pressure limit k_0
+    double alpha, T3, T1, T2;   // Troe parameters
+    bool has_T2 = false;
+    std::vector<int> eff_sp;    // third-body efficiencies different from 1
+    std::vector<double> eff_val;
+    int sum_nu = 0;             // sum_i nu_ij = sum nu^r - sum nu^f
+};
+
+// Mechanism with the coefficient sets of Table 1 in mass-specific form,
+// n_p = 4 (a NASA-7 range is the n_p = 4 instance: a_k = R_i * a_{k+1}^{NASA},
+// h_ref = R_i * a6, s_ref = R_i * a7).
+struct Mech {
+    int ns = 0, nr = 0;
+    std::vector<double> W, Ri;
+    std::vector<double> a, bc, cc, dc, fc;   // a: ns x 5; b, c, f: ns x 6; d: ns x 5
+    std::vector<Reaction> rx;
+};
+
+// ---------------------------------------------------------------------------
+// Thermodynamics, Table 1 (Section 2.1). Each quantity is an inner product of
+// its coefficients with a monomial basis in T.
+
+template <class S> S poly(const double* coef, int deg, const S& T) {
+    S out = 0.0, Tk = 1.0;
+    for (int k = 0; k <= deg; ++k) { out += coef[k] * Tk; Tk *= T; }
+    return out;
+}
+
+// c_p,i = sum_{k=0}^{n_p} a_ik T^k   (eq. specific_heat_polynomial)
+template <class S> S cp_i(const Mech& m, int i, const S& T) { return poly(&m.a[5 * i], 4, T); }
+// h_i = sum_{k=0}^{n_p+1} b_ik T^k   (eq. enthalpy-polynomial)
+template <class S> S h_i(const Mech& m, int i, const S& T) { return poly(&m.bc[6 * i], 5, T); }
+// u_i = sum_{k=0}^{n_p+1} c_ik T^k   (eq. internal-energy-polynomial)
+template <class S> S u_i(const Mech& m, int i, const S& T) { return poly(&m.cc[6 * i], 5, T); }
+// s_i^o = a_i0 ln T + sum_{k=0}^{n_p} d_ik T^k   (eq. entropy_polynomial)
+template <class S> S s_i(const Mech& m, int i, const S& T, const S& lnT) {
+    return m.a[5 * i] * lnT + poly(&m.dc[5 * i], 4, T);
+}
+// g_i^o = -a_i0 T ln T + sum_{k=0}^{n_p+1} f_ik T^k   (eq. gibbs-polynomial)
+template <class S> S g_i(const Mech& m, int i, const S& T, const S& lnT) {
+    return -m.a[5 * i] * T * lnT + poly(&m.fc[6 * i], 5, T);
+}
+// c_v,i = c_p,i - R_i   (eq. cv_equation)
+template <class S> S cv_i(const Mech& m, int i, const S& T) { return cp_i(m, i, T) - m.Ri[i]; }
+// d c_p,i / dT
+double dcp_i(const Mech& m, int i, double T) {
+    double out = 0.0, Tk = 1.0;
+    for (int k = 1; k <= 4; ++k) { out += k * m.a[5 * i + k] * Tk; Tk *= T; }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// Rates (Section 2.2).
+
+template <class S> S clamp_pr(const S& Pr) { return re(Pr) < 1e-300 ? S(1e-300) : Pr; }
+
+// forward rate constant k_f and the effective third-body concentration
+template <class S>
+S forward_rate(const Reaction& r, const S& T, const S& lnT, const S* C, const S& Mc) {
+    // k_A = A exp(b ln T - E/(R T))  (Section 2.2.1)
+    S kA = exp(r.lnA + r.b * lnT - r.Ea / (R_U * T));
+    if (r.type == ELEMENTARY) return kA;
+    // [M] = M_c + sum (alpha_ij - 1) C_i  (eq. TB_optimization)
+    S M = Mc;
+    for (size_t e = 0; e < r.eff_sp.size(); ++e) M += (r.eff_val[e] - 1.0) * C[r.eff_sp[e]];
+    if (r.type == THREE_BODY) return M * kA;
+    // falloff: k_f = k_inf Pr/(1+Pr) F  (eq. falloff-reaction)
+    S k0 = exp(r.lnA0 + r.b0 * lnT - r.Ea0 / (R_U * T));
+    S Pr = k0 * M / kA;
+    S F = 1.0;
+    if (r.type == TROE) {
+        // eq. f_and_fcent; alpha used in both terms of F_cent, T2 term dropped
+        // when T2 is absent (Appendix C.1)
+        S Fc = (1.0 - r.alpha) * exp(-T / r.T3) + r.alpha * exp(-T / r.T1);
+        if (r.has_T2) Fc += exp(-r.T2 / T);
+        S logFc = log(Fc) / LN10;
+        S c = -0.4 - 0.67 * logFc;
+        S n = 0.75 - 1.27 * logFc;
+        S P = log(clamp_pr(Pr)) / LN10;
+        S f1 = (P + c) / (n - 0.14 * (P + c));
+        S logF = logFc / (1.0 + f1 * f1);
+        F = exp(LN10 * logF);
+    }
+    return kA * (Pr / (1.0 + Pr)) * F;
+}
+
+// equilibrium constant, eq. equilibrium-constant-1 with molar Gibbs energies
+template <class S>
+S equilibrium_constant(const Mech& m, const Reaction& r, const S& T, const S* g) {
+    S dG = 0.0;   // Delta G'_j = sum_i nu_ij W_i g_i^o  (molar)
+    for (int s = 0; s < 3; ++s) {
+        if (r.r_idx[s] >= 0) dG += double(r.r_nu[s]) * m.W[r.r_idx[s]] * g[r.r_idx[s]];
+        if (r.f_idx[s] >= 0) dG -= double(r.f_nu[s]) * m.W[r.f_idx[s]] * g[r.f_idx[s]];
+    }
+    S K = exp(-dG / (R_U * T));
+    // (p_ref / (R T))^{sum nu} as repeated multiplication (Section 2.2)
+    S base = r.sum_nu >= 0 ? P_REF / (R_U * T) : (R_U * T) / P_REF;
+    for (int k = 0; k < std::abs(r.sum_nu); ++k) K *= base;
+    return K;
+}
+
+template <class S> S prod_conc(const int* idx, const int* nu, const S* C) {
+    S p = 1.0;
+    for (int s = 0; s < 3; ++s)
+        if (idx[s] >= 0)
+            for (int k = 0; k < nu[s]; ++k) p *= C[idx[s]];
+    return p;
+}
+
+// Rates of progress q_j (eq. chemical-reaction-rate-of-progress).
+template <class S>
+void progress_rates(const Mech& m, const S& T, const S* C, S* kf_out, S* kr_out, S* q) {
+    S lnT = log(T);
+    S Mc = 0.0;
+    for (int i = 0; i < m.ns; ++i) Mc += C[i];
+    std::vector<S> g(m.ns);
+    for (int i = 0; i < m.ns; ++i) g[i] = g_i(m, i, T, lnT);
+    for (int j = 0; j < m.nr; ++j) {
+        const Reaction& r = m.rx[j];
+        S kf = forward_rate(r, T, lnT, C, Mc);
+        S kr = 0.0;
+        if (r.reversible) kr = kf / equilibrium_constant(m, r, T, g.data());   // eq. reverse_rate
+        q[j] = kf * prod_conc(r.f_idx, r.f_nu, C) - kr * prod_conc(r.r_idx, r.r_nu, C);
+        if (kf_out) kf_out[j] = kf;
+        if (kr_out) kr_out[j] = kr;
+    }
+}
+
+// Source term S(y) = (omega_T, dC/dt).
+//   omega_i = sum_j nu_ij q_j.
+//   CONV: omega_T = -sum W_i u_i omega_i / (rho c_v)  (eq. temperature_source)
+//   CONP_LITERAL: omega_T = -sum W_i h_i omega_i / (rho c_p), dC/dt = omega
+//       (Appendix B, eq. temperature_source_h, the rest unchanged)
+//   CONP: same omega_T; dC_i/dt = omega_i - C_i (omega_T/T + sum omega/sum C),
+//       the dilution of an ideal gas held at constant pressure.
+// The c_v and c_p of the temperature source are volumetric: rho c = sum W_i C_i c_i.
+template <class S>
+void source(const Mech& m, int reactor, const S* y, S* out) {
+    const S T = y[0];
+    const S* C = y + 1;
+    std::vector<S> q(m.nr), w(m.ns, S(0.0));
+    progress_rates(m, T, C, (S*)nullptr, (S*)nullptr, q.data());
+    for (int j = 0; j < m.nr; ++j) {
+        const Reaction& r = m.rx[j];
+        for (int s = 0; s < 3; ++s) {
+            if (r.r_idx[s] >= 0) w[r.r_idx[s]] += double(r.r_nu[s]) * q[j];
+            if (r.f_idx[s] >= 0) w[r.f_idx[s]] -= double(r.f_nu[s]) * q[j];
+        }
+    }
+    S num = 0.0, den = 0.0;
+    for (int i = 0; i < m.ns; ++i) {
+        S e = reactor == CONV ? u_i(m, i, T) : h_i(m, i, T);
+        S c = reactor == CONV ? cv_i(m, i, T) : cp_i(m, i, T);
+        num += m.W[i] * e * w[i];
+        den += m.W[i] * C[i] * c;
+    }
+    S wT = -num / den;
+    out[0] = wT;
+    if (reactor == CONP) {
+        S sw = 0.0, sc = 0.0;
+        for (int i = 0; i < m.ns; ++i) { sw += w[i]; sc += C[i]; }
+        S dil = wT / T + sw / sc;
+        for (int i = 0; i < m.ns; ++i) out[1 + i] = w[i] - C[i] * dil;
+    } else {
+        for (int i = 0; i < m.ns; ++i) out[1 + i] = w[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Analytical Jacobian J_ij = dS_i/dy_j (eq. derivative_matrices_temp_evol),
+// with T and C independent state variables, row/column 0 = T.
+
+// derivative of prod_s C^nu with respect to C_m (product rule, exact at C = 0)
+double dprod(const int* idx, const int* nu, const double* C, int mcol) {
+    double total = 0.0;
+    for (int s = 0; s < 3; ++s) {
+        if (idx[s] != mcol) continue;
+        double p = nu[s];
+        for (int k = 0; k < nu[s] - 1; ++k) p *= C[mcol];
+        for (int t = 0; t < 3; ++t)
+            if (t != s && idx[t] >= 0)
+                for (int k = 0; k < nu[t]; ++k) p *= C[idx[t]];
+        total += p;
+    }
+    return total;
+}
+
+void jacobian(const Mech& m, int reactor, const double* y, double* J) {
+    const int ns = m.ns, n = ns + 1;
+    const double T = y[0];
+    const double* C = y + 1;
+    const double lnT = std::log(T), RT = R_U * T;
+    double Mc = 0.0;
+    for (int i = 0; i < ns; ++i) Mc += C[i];
+    std::vector<double> g(ns), h(ns);
+    for (int i = 0; i < ns; ++i) { g[i] = g_i(m, i, T, lnT); h[i] = h_i(m, i, T); }
+
+    // dw[i*n + col] = d omega_i / d y_col ; w = omega
+    std::vector<double> dw(ns * n, 0.0), w(ns, 0.0), dq(n);
+    for (int j = 0; j < m.nr; ++j) {
+        const Reaction& r = m.rx[j];
+        std::fill(dq.begin(), dq.end(), 0.0);
+        double kA = std::exp(r.lnA + r.b * lnT - r.Ea / RT);
+        double dkA = kA * (r.b / T + r.Ea / (R_U * T * T));
+        double M = Mc;
+        std::vector<double> alpha(ns, 1.0);
+        for (size_t e = 0; e < r.eff_sp.size(); ++e) {
+            M += (r.eff_val[e] - 1.0) * C[r.eff_sp[e]];
+            alpha[r.eff_sp[e]] = r.eff_val[e];
+        }
+        double kf, dkf_dT, dkf_dM;
+        if (r.type == ELEMENTARY) {
+            kf = kA; dkf_dT = dkA; dkf_dM = 0.0;
+        } else if (r.type == THREE_BODY) {
+            kf = M * kA; dkf_dT = M * dkA; dkf_dM = kA;
+        } else {
+            double k0 = std::exp(r.lnA0 + r.b0 * lnT - r.Ea0 / RT);
+            double Pr = k0 * M / kA;
+            double dPr_dT = Pr * ((r.b0 - r.b) / T + (r.Ea0 - r.Ea) / (R_U * T * T));
+            double dPr_dM = k0 / kA;
+            double F = 1.0, dlogF_dP = 0.0, dlogF_dT = 0.0;   // log = log10
+            if (r.type == TROE) {
+                double e3 = std::exp(-T / r.T3), e1 = std::exp(-T / r.T1);
+                double Fc = (1.0 - r.alpha) * e3 + r.alpha * e1;
+                double dFc = -(1.0 - r.alpha) / r.T3 * e3 - r.alpha / r.T1 * e1;
+                if (r.has_T2) {
+                    double e2 = std::exp(-r.T2 / T);
+                    Fc += e2;
+                    dFc += r.T2 / (T * T) * e2;
+                }
+                double L = std::log10(Fc);
+                double dL_dT = dFc / (Fc * LN10);
+                double c = -0.4 - 0.67 * L, nn = 0.75 - 1.27 * L;
+                bool clamped = Pr < 1e-300;
+                double P = std::log10(clamped ? 1e-300 : Pr);
+                double x = P + c, den = nn - 0.14 * x;
+                double f1 = x / den;
+                double g1 = 1.0 + f1 * f1;
+                double logF = L / g1;
+                F = std::pow(10.0, logF);
+                double df1_dx = nn / (den * den);
+                double df1_dn = -x / (den * den);
+                double df1_dL = df1_dx * (-0.67) + df1_dn * (-1.27);
+                dlogF_dP = clamped ? 0.0 : -L * 2.0 * f1 / (g1 * g1) * df1_dx;
+                double dlogF_dL = 1.0 / g1 - L * 2.0 * f1 / (g1 * g1) * df1_dL;
+                dlogF_dT = dlogF_dL * dL_dT;   // at fixed Pr
+            }
+            double fr = Pr / (1.0 + Pr);
+            kf = kA * fr * F;
+            // d kf / d Pr = kA F [1/(1+Pr)^2 + dlog10F/dlog10Pr / (1+Pr)]
+            double dkf_dPr = kA * F * (1.0 / ((1.0 + Pr) * (1.0 + Pr)) + dlogF_dP / (1.0 + Pr));
+            dkf_dT = dkA * fr * F + dkf_dPr * dPr_dT + kf * LN10 * dlogF_dT;
+            dkf_dM = dkf_dPr * dPr_dM;
+        }
+        double pf = prod_conc(r.f_idx, r.f_nu, C), pr = prod_conc(r.r_idx, r.r_nu, C);
+        double invK = 0.0, dlnK = 0.0;
+        if (r.reversible) {
+            invK = 1.0 / equilibrium_constant(m, r, T, g.data());
+            // d ln K / dT = sum nu_i W_i h_i / (R T^2) - sum nu / T
+            double dH = 0.0;
+            for (int s = 0; s < 3; ++s) {
+                if (r.r_idx[s] >= 0) dH += r.r_nu[s] * m.W[r.r_idx[s]] * h[r.r_idx[s]];
+                if (r.f_idx[s] >= 0) dH -= r.f_nu[s] * m.W[r.f_idx[s]] * h[r.f_idx[s]];
+            }
+            dlnK = dH / (R_U * T * T) - r.sum_nu / T;
+        }
+        double phi = pf - pr * invK;
+        double q = kf * phi;
+        dq[0] = dkf_dT * phi + kf * pr * invK * dlnK;
+        for (int mm = 0; mm < ns; ++mm) {
+            double d = dkf_dM * alpha[mm] * phi;
+            d += kf * (dprod(r.f_idx, r.f_nu, C, mm) - invK * dprod(r.r_idx, r.r_nu, C, mm));
+            dq[1 + mm] = d;
+        }
+        for (int s = 0; s < 3; ++s) {
+            for (int side = 0; side < 2; ++side) {
+                int sp = side ? r.r_idx[s] : r.f_idx[s];
+                if (sp < 0) continue;
+                double nu = side ? r.r_nu[s] : -r.f_nu[s];
+                w[sp] += nu * q;
+                for (int col = 0; col < n; ++col) dw[sp * n + col] += nu * dq[col];
+            }
+        }
+    }
+
+    // temperature row: omega_T = -Q/D, Q = sum W e omega, D = sum W C c
+    double Q = 0.0, D = 0.0, dD_dT = 0.0, dQ_dT = 0.0;
+    std::vector<double> e(ns), c(ns);
+    for (int i = 0; i < ns; ++i) {
+        e[i] = reactor == CONV ? u_i(m, i, T) : h_i(m, i, T);
+        c[i] = reactor == CONV ? cv_i(m, i, T) : cp_i(m, i, T);
+        Q += m.W[i] * e[i] * w[i];
+        D += m.W[i] * C[i] * c[i];
+        dD_dT += m.W[i] * C[i] * dcp_i(m, i, T);
+        dQ_dT += m.W[i] * c[i] * w[i] + m.W[i] * e[i] * dw[i * n];
+    }
+    double wT = -Q / D;
+    J[0] = -dQ_dT / D + Q * dD_dT / (D * D);
+    for (int mm = 0; mm < ns; ++mm) {
+        double dQ = 0.0;
+        for (int i = 0; i < ns; ++i) dQ += m.W[i] * e[i] * dw[i * n + 1 + mm];
+        J[1 + mm] = -dQ / D + Q * m.W[mm] * c[mm] / (D * D);
+    }
+    for (int i = 0; i < ns; ++i)
+        for (int col = 0; col < n; ++col) J[(1 + i) * n + col] = dw[i * n + col];
+
+    if (reactor == CONP) {
+        // dC_i/dt = omega_i - C_i s, s = omega_T/T + sum omega / sum C
+        double sw = 0.0, sc = Mc;
+        for (int i = 0; i < ns; ++i) sw += w[i];
+        double sdil = wT / T + sw / sc;
+        std::vector<double> ds(n);
+        for (int col = 0; col < n; ++col) {
+            double dsw = 0.0;
+            for (int i = 0; i < ns; ++i) dsw += dw[i * n + col];
+            ds[col] = J[col] / T + dsw / sc;
+        }
+        ds[0] -= wT / (T * T);
+        for (int col = 1; col < n; ++col) ds[col] -= sw / (sc * sc);
+        for (int i = 0; i < ns; ++i) {
+            for (int col = 0; col < n; ++col) J[(1 + i) * n + col] -= C[i] * ds[col];
+            J[(1 + i) * n + 1 + i] -= sdil;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dense direct solver (Section 3.4): LU with partial pivoting.
+
+bool lu_factor(int n, double* A, int* piv) {
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(A[i * n + k]) > std::fabs(A[p * n + k])) p = i;
+        piv[k] = p;
+        if (p != k)
+            for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[p * n + j]);
+        if (A[k * n + k] == 0.0) return false;
+        for (int i = k + 1; i < n; ++i) {
+            A[i * n + k] /= A[k * n + k];
+            for (int j = k + 1; j < n; ++j) A[i * n + j] -= A[i * n + k] * A[k * n + j];
+        }
+    }
+    return true;
+}
+
+void lu_solve(int n, const double* LU, const int* piv, double* b) {
+    for (int k = 0; k < n; ++k) std::swap(b[k], b[piv[k]]);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) b[i] -= LU[i * n + j] * b[j];
+    for (int i = n - 1; i >= 0; --i) {
+        for (int j = i + 1; j < n; ++j) b[i] -= LU[i * n + j] * b[j];
+        b[i] /= LU[i * n + i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Integrators.
+
+struct Tableau {
+    int s;                 // stages
+    double A[5][5];        // lower triangular incl. diagonal
+    double b[5], bhat[5];  // weights and embedded weights
+    int err_order;         // order of the embedded solution (controller exponent 1/(q+1))
+};
+
+struct Opts {
+    int method;            // 0 BE, 1 SDIRK-2, 2 SDIRK-4
+    int reactor;
+    int adaptive;
+    int nsub;              // fixed-step mode: number of equal steps
+    double dt, rtol, atol, newton_tol, h0, hmin, neg_tol;
+    int max_newton, max_steps, max_halvings, err_filter;
+};
+
+struct Stats { int steps = 0, rejects = 0, newton = 0, lu = 0; };
+
+bool finite_vec(const std::vector<double>& v) {
+    for (double x : v) if (!std::isfinite(x)) return false;
+    return true;
+}
+
+// A converged step is admissible when T > 0 and no concentration is below
+// -neg_tol * sum(C) (the paper does not say what to do with a Newton root
+// outside the physical domain; such a step is treated as a failed step).
+bool admissible(const std::vector<double>& y, double neg_tol) {
+    if (!(y[0] > 0.0)) return false;
+    double sc = 0.0;
+    for (size_t i = 1; i < y.size(); ++i) sc += y[i];
+    for (size_t i = 1; i < y.size(); ++i)
+        if (y[i] < -neg_tol * sc) return false;
+    return true;
+}
+
+double wrms(int n, const double* v, const double* ya, const double* yb, double rtol, double atol) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double w = atol + rtol * std::max(std::fabs(ya[i]), std::fabs(yb[i]));
+        double r = v[i] / w;
+        s += r * r;
+    }
+    return std::sqrt(s / n);
+}
+
+struct Cell {
+    const Mech& m;
+    const Opts& o;
+    Stats st;
+    int n;
+    std::vector<double> S, J, G, f, d;
+    std::vector<int> piv;
+    Cell(const Mech& mm, const Opts& oo) : m(mm), o(oo), n(mm.ns + 1),
+        S(n), J(n * n), G(n * n), f(n), d(n), piv(n) {}
+
+    // Backward Euler (eq. Backward_euler) with full Newton (eq. newtons-method-2):
+    // G(y_k) (y_{k+1} - y_k) = -f(y_k), f = (y_k - y^n)/h - S(y_k),
+    // G = I/h - J(y_k) (eq. jacobian), J re-evaluated at every iterate.
+    // Starts from y^n; converged when WRMS(y_{k+1} - y_k) <= newton_tol.
+    bool be_step(const std::vector<double>& yn, double h, std::vector<double>& y) {
+        y = yn;
+        for (int k = 0; k < o.max_newton; ++k) {
+            source(m, o.reactor, y.data(), S.data());
+            jacobian(m, o.reactor, y.data(), J.data());
+            for (int i = 0; i < n; ++i) {
+                f[i] = (y[i] - yn[i]) / h - S[i];
+                for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 / h : 0.0) - J[i * n + j];
+            }
+            st.newton++;
+            st.lu++;
+            if (!lu_factor(n, G.data(), piv.data())) return false;
+            for (int i = 0; i < n; ++i) d[i] = -f[i];
+            lu_solve(n, G.data(), piv.data(), d.data());
+            for (int i = 0; i < n; ++i) y[i] += d[i];
+            if (!finite_vec(y)) return false;
+            if (wrms(n, d.data(), yn.data(), y.data(), o.rtol, o.atol) <= o.newton_tol)
+                return admissible(y, o.neg_tol);
+        }
+        return false;
+    }
+
+    // One SDIRK step in stage-derivative form (Appendix A.1/A.2):
+    //   Gamma_p = S(y_n + h sum_{j<p} a_pj Gamma_j + h a_pp Gamma_p),
+    //   Newton on f(Gamma_p) = Gamma_p - S(Y_p) with G = I - a_pp h J(Y_p),
+    //   first iterate Gamma_{p,1} = S(y_n), converged when the change of the
+    //   stage state, WRMS(h a_pp dGamma), is <= newton_tol;
+    //   y_{n+1} = y_n + h sum b_i Gamma_i.
+    // On success also returns the embedded error estimate
+    //   e = h sum (b_i - bhat_i) Gamma_i, optionally filtered by the last
+    //   Newton matrix: e <- (I - a_pp h J)^{-1} e.
+    bool sdirk_step(const Tableau& tb, const std::vector<double>& yn, double h,
+                    std::vector<double>& y1, std::vector<double>& err) {
+        std::vector<std::vector<double>> Gam(tb.s, std::vector<double>(n));
+        std::vector<double> S0(n), Y(n), base(n);
+        source(m, o.reactor, yn.data(), S0.data());
+        for (int p = 0; p < tb.s; ++p) {
+            double gh = tb.A[p][p] * h;
+            for (int i = 0; i < n; ++i) {
+                base[i] = yn[i];
+                for (int j = 0; j < p; ++j) base[i] += h * tb.A[p][j] * Gam[j][i];
+            }
+            std::vector<double>& Gp = Gam[p];
+            Gp = S0;
+            bool conv = false;
+            for (int k = 0; k < o.max_newton; ++k) {
+                for (int i = 0; i < n; ++i) Y[i] = base[i] + gh * Gp[i];
+                source(m, o.reactor, Y.data(), S.data());
+                jacobian(m, o.reactor, Y.data(), J.data());
+                for (int i = 0; i < n; ++i) {
+                    f[i] = Gp[i] - S[i];
+                    for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 : 0.0) - gh * J[i * n + j];
+                }
+                st.newton++;
+                st.lu++;
+                if (!lu_factor(n, G.data(), piv.data())) return false;
+                for (int i = 0; i < n; ++i) d[i] = -f[i];
+                lu_solve(n, G.data(), piv.data(), d.data());
+                for (int i = 0; i < n; ++i) { Gp[i] += d[i]; d[i] *= gh; Y[i] = base[i] + gh * Gp[i]; }
+                if (!finite_vec(Gp)) return false;
+                if (wrms(n, d.data(), yn.data(), Y.data(), o.rtol, o.atol) <= o.newton_tol) {
+                    conv = true;
+                    break;
+                }
+            }
+            if (!conv) return false;
+        }
+        y1 = yn;
+        err.assign(n, 0.0);
+        for (int p = 0; p < tb.s; ++p)
+            for (int i = 0; i < n; ++i) {
+                y1[i] += h * tb.b[p] * Gam[p][i];
+                err[i] += h * (tb.b[p] - tb.bhat[p]) * Gam[p][i];
+            }
+        if (o.err_filter) lu_solve(n, G.data(), piv.data(), err.data());
+        return finite_vec(y1) && admissible(y1, o.neg_tol);
+    }
+
+    bool fixed_step(const Tableau& tb, const std::vector<double>& yn, double h, std::vector<double>& y) {
+        if (o.method == 0) return be_step(yn, h, y);
+        std::vector<double> err;
+        return sdirk_step(tb, yn, h, y, err);
+    }
+
+    // Fixed step with deterministic halving on Newton failure (after YASS,
+    // Appendix A.4): a failed step is replaced by two steps of half the size,
+    // recursively, at most max_halvings levels deep.
+    int fixed_recursive(const Tableau& tb, std::vector<double>& y, double h, int depth) {
+        std::vector<double> y1;
+        if (fixed_step(tb, y, h, y1)) { y = y1; st.steps++; return ST_OK; }
+        st.rejects++;
+        if (depth >= o.max_halvings) return ST_NEWTON_FAIL;
+        int s = fixed_recursive(tb, y, 0.5 * h, depth + 1);
+        if (s != ST_OK) return s;
+        return fixed_recursive(tb, y, 0.5 * h, depth + 1);
+    }
+
+    // Adaptive step-size control (not specified by the paper): accept when the
+    // WRMS error <= 1; h_new = h min(5, max(0.2, 0.9 err^{-1/(q+1)}));
+    // Newton failure: h <- h/4; last step clipped to end at dt.
+    int adaptive(const Tableau& tb, std::vector<double>& y) {
+        double t = 0.0, h = o.h0 > 0.0 ? std::min(o.h0, o.dt) : o.dt;
+        double expo = -1.0 / (tb.err_order + 1.0);
+        std::vector<double> y1, err;
+        int attempts = 0;
+        while (t < o.dt) {
+            if (attempts++ >= o.max_steps) return ST_MAX_STEPS;
+            if (h < o.hmin) return ST_STEP_TOO_SMALL;
+            bool last = t + h >= o.dt;
+            double hh = last ? o.dt - t : h;
+            if (!sdirk_step(tb, y, hh, y1, err)) {
+                st.rejects++;
+                h = 0.25 * hh;
+                continue;
+            }
+            double e = wrms(n, err.data(), y.data(), y1.data(), o.rtol, o.atol);
+            double fac = e > 0.0 ? 0.9 * std::pow(e, expo) : 5.0;
+            fac = std::min(5.0, std::max(0.2, fac));
+            if (e <= 1.0) {
+                y = y1;
+                t = last ? o.dt : t + hh;
+                st.steps++;
+            } else {
+                st.rejects++;
+            }
+            h = hh * fac;
+        }
+        return ST_OK;
+    }
+
+    int integrate(const Tableau& tb, std::vector<double>& y) {
+        if (!finite_vec(y)) return ST_NONFINITE;
+        if (o.adaptive && o.method != 0) return adaptive(tb, y);
+        int ns = std::max(1, o.nsub);
+        double h = o.dt / ns;
+        for (int k = 0; k < ns; ++k) {
+            int s = fixed_recursive(tb, y, h, 0);
+            if (s != ST_OK) return s;
+        }
+        return ST_OK;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Temperature recovery, eqs. temperature-nonlinear .. netwon_iteration_temperature.
+// Solves sum_i Y_i e_i(T) = e (e = u for CONV, h for CONP) with n Newton
+// iterations: T_k = T_{k-1} + (e - e(T_{k-1})) / c(T_{k-1}), where
+// c = sum Y_i c_v,i (or c_p,i). (The printed update carries the opposite sign
+// of the Newton step eq. netwons-method-temperature defines; the step is used.)
+double recover_T(const Mech& m, int reactor, double e, const double* Y, double T, int iters) {
+    for (int k = 0; k < iters; ++k) {
+        double ev = 0.0, c = 0.0;
+        for (int i = 0; i < m.ns; ++i) {
+            ev += Y[i] * (reactor == CONV ? u_i(m, i, T) : h_i(m, i, T));
+            c += Y[i] * (reactor == CONV ? cv_i(m, i, T) : cp_i(m, i, T));
+        }
+        T = T + (e - ev) / c;
+    }
+    return T;
+}
+
+template <class F> void parallel_for(long N, int nthreads, F fn) {
+    if (nthreads <= 1 || N < 2) {
+        for (long c = 0; c < N; ++c) fn(c);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nthreads; ++t)
+        th.emplace_back([&, t]() { for (long c = t; c < N; c += nthreads) fn(c); });
+    for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C entry points (host pointers; arrays of cells are cell-major: cell c's
+// state is y[c*n .. c*n+n-1]).
+
+extern "C" {
+
+void* cgref_mech_create(int ns, int nr, const double* W, const double* nasa7,
+                        const int* rtype, const int* reversible,
+                        const int* rf_idx, const int* rf_nu, const int* rr_idx, const int* rr_nu,
+                        const double* arr, const double* arr0, const double* troe,
+                        const int* eff_ptr, const int* eff_idx, const double* eff_val) {
+    Mech* m = new Mech();
+    m->ns = ns;
+    m->nr = nr;
+    m->W.assign(W, W + ns);
+    m->Ri.resize(ns);
+    m->a.resize(5 * ns); m->bc.resize(6 * ns); m->cc.resize(6 * ns);
+    m->dc.resize(5 * ns); m->fc.resize(6 * ns);
+    for (int i = 0; i < ns; ++i) {
+        double Ri = R_U / W[i];
+        m->Ri[i] = Ri;
+        const double* nc = nasa7 + 7 * i;
+        double* a = &m->a[5 * i];
+        for (int k = 0; k <= 4; ++k) a[k] = Ri * nc[k];        // c_p fit coefficients
+        double href = Ri * nc[5], sref = Ri * nc[6];
+        double* b = &m->bc[6 * i];                               // Table 1, h_i
+        b[0] = href;
+        for (int k = 1; k <= 5; ++k) b[k] = a[k - 1] / k;
+        double* c = &m->cc[6 * i];                               // Table 1, u_i
+        c[0] = href;
+        c[1] = a[0] - Ri;
+        for (int k = 2; k <= 5; ++k) c[k] = a[k - 1] / k;
+        double* d = &m->dc[5 * i];                               // Table 1, s_i^o
+        d[0] = sref;
+        for (int k = 1; k <= 4; ++k) d[k] = a[k] / k;
+        double* f = &m->fc[6 * i];                               // Table 1, g_i^o
+        f[0] = href;
+        f[1] = a[0] - sref;
+        for (int k = 2; k <= 5; ++k) f[k] = (1.0 / k - 1.0 / (k - 1)) * a[k - 1];
+    }
+    m->rx.resize(nr);
+    for (int j = 0; j < nr; ++j) {
+        Reaction& r = m->rx[j];
+        r.type = rtype[j];
+        r.reversible = reversible[j];
+        r.sum_nu = 0;
+        for (int s = 0; s < 3; ++s) {
+            r.f_idx[s] = rf_idx[3 * j + s]; r.f_nu[s] = rf_nu[3 * j + s];
+            r.r_idx[s] = rr_idx[3 * j + s]; r.r_nu[s] = rr_nu[3 * j + s];
+            if (r.f_idx[s] >= 0) r.sum_nu -= r.f_nu[s];
+            if (r.r_idx[s] >= 0) r.sum_nu += r.r_nu[s];
+        }
+        r.lnA = arr[3 * j]; r.b = arr[3 * j + 1]; r.Ea = arr[3 * j + 2];
+        r.lnA0 = arr0[3 * j]; r.b0 = arr0[3 * j + 1]; r.Ea0 = arr0[3 * j + 2];
+        r.alpha = troe[4 * j]; r.T3 = troe[4 * j + 1]; r.T1 = troe[4 * j + 2]; r.T2 = troe[4 * j + 3];
+        r.has_T2 = !std::isnan(r.T2);
+        for (int e = eff_ptr[j]; e < eff_ptr[j + 1]; ++e) {
+            r.eff_sp.push_back(eff_idx[e]);
+            r.eff_val.push_back(eff_val[e]);
+        }
+    }
+    return m;
+}
+
+void cgref_mech_destroy(void* h) { delete static_cast<Mech*>(h); }
+
+// Mass-specific thermo per species at one temperature: cp, h, u, s, g, cv.
+void cgref_thermo(const void* h, double T, double* cp, double* hh, double* u, double* s, double* g,
+                  double* cv) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    double lnT = std::log(T);
+    for (int i = 0; i < m.ns; ++i) {
+        cp[i] = cp_i(m, i, T); hh[i] = h_i(m, i, T); u[i] = u_i(m, i, T);
+        s[i] = s_i(m, i, T, lnT); g[i] = g_i(m, i, T, lnT); cv[i] = cv_i(m, i, T);
+    }
+}
+
+// Forward/reverse rate constants and rates of progress of one state.
+void cgref_rates(const void* h, double T, const double* C, double* kf, double* kr, double* q) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    progress_rates(m, T, C, kf, kr, q);
+}
+
+// S(y) for N cells, y cell-major [N][ns+1].
+void cgref_source(const void* h, int reactor, long N, const double* y, double* S) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    const int n = m.ns + 1;
+    for (long c = 0; c < N; ++c) source(m, reactor, y + c * n, S + c * n);
+}
+
+// S(y) with complex state (for complex-step differentiation).
+void cgref_source_complex(const void* h, int reactor, const double* y_re, const double* y_im,
+                          double* S_re, double* S_im) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    const int n = m.ns + 1;
+    std::vector<cplx> y(n), S(n);
+    for (int i = 0; i < n; ++i) y[i] = cplx(y_re[i], y_im[i]);
+    source(m, reactor, y.data(), S.data());
+    for (int i = 0; i < n; ++i) { S_re[i] = S[i].real(); S_im[i] = S[i].imag(); }
+}
+
+// J(y) for N cells, J cell-major [N][n][n] row-major.
+void cgref_jacobian(const void* h, int reactor, long N, const double* y, double* J) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    const int n = m.ns + 1;
+    for (long c = 0; c < N; ++c) jacobian(m, reactor, y + c * n, J + c * n * n);
+}
+
+// Solve A x = b with LU and partial pivoting; A, b overwritten (x in b). 0 if singular.
+int cgref_lu_solve(int n, double* A, double* b) {
+    std::vector<int> piv(n);
+    if (!lu_factor(n, A, piv.data())) return 0;
+    lu_solve(n, A, piv.data(), b);
+    return 1;
+}
+
+// Temperature from mass-specific energy (u for CONV, h otherwise) and Y.
+void cgref_temperature(const void* h, int reactor, long N, const double* e, const double* Y,
+                       const double* T0, int iters, double* T) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    for (long c = 0; c < N; ++c) T[c] = recover_T(m, reactor, e[c], Y + c * m.ns, T0[c], iters);
+}
+
+// Integrate N cells over dt. y in/out cell-major [N][ns+1] = (T, C).
+// status[N]; stats[N][4] = accepted steps, rejected/failed attempts, Newton
+// iterations, LU factorisations.
+void cgref_integrate(const void* h, const int* iopt, const double* dopt, const double* tab,
+                     long N, double* y, int* status, int* stats, int nthreads) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    Opts o;
+    o.method = iopt[0]; o.reactor = iopt[1]; o.adaptive = iopt[2]; o.nsub = iopt[3];
+    o.max_newton = iopt[4]; o.max_steps = iopt[5]; o.max_halvings = iopt[6]; o.err_filter = iopt[7];
+    o.dt = dopt[0]; o.rtol = dopt[1]; o.atol = dopt[2]; o.newton_tol = dopt[3];
+    o.h0 = dopt[4]; o.hmin = dopt[5]; o.neg_tol = dopt[6];
+    Tableau tb;
+    tb.s = (int)tab[0];
+    tb.err_order = (int)tab[1];
+    for (int i = 0; i < 5; ++i) {
+        for (int j = 0; j < 5; ++j) tb.A[i][j] = tab[2 + 5 * i + j];
+        tb.b[i] = tab[27 + i];
+        tb.bhat[i] = tab[32 + i];
+    }
+    const int n = m.ns + 1;
+    parallel_for(N, nthreads, [&](long c) {
+        Cell cell(m, o);
+        std::vector<double> yc(y + c * n, y + (c + 1) * n);
+        int s = cell.integrate(tb, yc);
+        if (s == ST_OK && !finite_vec(yc)) s = ST_NONFINITE;
+        std::copy(yc.begin(), yc.end(), y + c * n);
+        status[c] = s;
+        stats[4 * c + 0] = cell.st.steps;
+        stats[4 * c + 1] = cell.st.rejects;
+        stats[4 * c + 2] = cell.st.newton;
+        stats[4 * c + 3] = cell.st.lu;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,25 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
+
+
+@pytest.fixture(scope="session")
+def mechs():
+    from paper_2510_10005_gb300 import inputs
+    return {k: inputs.gen_mechanism(k) for k in ("h2", "ch4")}
+
+
+@pytest.fixture(scope="session")
+def ref(mechs):
+    import oracle
+    return {k: oracle.RefMech(m) for k, m in mechs.items()}

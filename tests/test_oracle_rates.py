@@ -1,0 +1,220 @@
+"""Pins of the oracle's reaction rates and source term (Section 2.2).
+
+Closed forms and limits: third-body with unit efficiencies, Lindemann low and
+high pressure limits, Troe at f1 = 0, the extreme Troe parameters of
+Appendix C.1, the reverse reaction's equilibrium constant, and conservation
+of mass and of every element by omega."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_10005_gb300 import inputs
+
+R = inputs.R_UNIV
+
+
+def edit(mech, j, rtype=None, effs=None, troe=None, reverse=False):
+    """Copy of mech with reaction j changed (type, efficiencies, Troe data)."""
+    m = mech.copy()
+    if rtype is not None:
+        m.rtype[j] = rtype
+    if troe is not None:
+        m.troe[j] = troe
+    if reverse:
+        m.rf_idx[j], m.rr_idx[j] = mech.rr_idx[j].copy(), mech.rf_idx[j].copy()
+        m.rf_nu[j], m.rr_nu[j] = mech.rr_nu[j].copy(), mech.rf_nu[j].copy()
+    if effs is not None:
+        idx, val, ptr = [], [], [0]
+        for k in range(m.nr):
+            if k == j:
+                pairs = effs
+            else:
+                pairs = list(zip(mech.eff_idx[mech.eff_ptr[k]:mech.eff_ptr[k + 1]],
+                                 mech.eff_val[mech.eff_ptr[k]:mech.eff_ptr[k + 1]]))
+            for s, v in pairs:
+                idx.append(int(s)); val.append(float(v))
+            ptr.append(len(idx))
+        m.eff_ptr = np.array(ptr, dtype=np.int32)
+        m.eff_idx = np.array(idx, dtype=np.int32)
+        m.eff_val = np.array(val)
+    return m
+
+
+def first(mech, t):
+    return int(np.nonzero(mech.rtype == t)[0][0])
+
+
+def test_third_body_unit_efficiencies(mechs):
+    m = mechs["ch4"]
+    j = first(m, inputs.RXN_THREE_BODY)
+    T, C, p = inputs.random_states(m, 4, seed=2)
+    tb = oracle.RefMech(edit(m, j, effs=[]))
+    el = oracle.RefMech(edit(m, j, rtype=inputs.RXN_ELEMENTARY, effs=[]))
+    for c in range(4):
+        kf_tb = tb.rates(T[c], C[c])[0][j]
+        kA = el.rates(T[c], C[c])[0][j]
+        assert kf_tb == pytest.approx(C[c].sum() * kA, rel=1e-14)
+    # with efficiencies: [M] = sum_i alpha_i C_i
+    effs = [(0, 2.5), (3, 0.5)]
+    tbe = oracle.RefMech(edit(m, j, effs=effs))
+    for c in range(4):
+        M = C[c].sum() + 1.5 * C[c][0] - 0.5 * C[c][3]
+        assert tbe.rates(T[c], C[c])[0][j] == pytest.approx(M * el.rates(T[c], C[c])[0][j], rel=1e-14)
+
+
+def _arrhenius(tr, T):
+    return math.exp(tr[0] + tr[1] * math.log(T) - tr[2] / (R * T))
+
+
+def test_lindemann_limits(mechs):
+    m = mechs["ch4"]
+    j = first(m, inputs.RXN_TROE)
+    lm = oracle.RefMech(edit(m, j, rtype=inputs.RXN_LINDEMANN, effs=[]))
+    T = 1300.0
+    kinf, k0 = _arrhenius(m.arr[j], T), _arrhenius(m.arr0[j], T)
+    X = np.full(m.ns, 1.0 / m.ns)
+    lo = X * 1e-12   # Pr -> 0: k_f -> k_0 [M]
+    hi = X * 1e12    # Pr -> infinity: k_f -> k_inf
+    assert lm.rates(T, lo)[0][j] == pytest.approx(k0 * lo.sum(), rel=1e-8)
+    assert lm.rates(T, hi)[0][j] == pytest.approx(kinf, rel=1e-8)
+    # in between: k_inf Pr/(1+Pr)
+    mid = X * 0.02
+    Pr = k0 * mid.sum() / kinf
+    assert lm.rates(T, mid)[0][j] == pytest.approx(kinf * Pr / (1 + Pr), rel=1e-13)
+
+
+def test_troe_at_f1_zero_gives_fcent(mechs):
+    """log10 Pr = -c makes f1 = 0, so F = F_cent exactly (eq. f_and_fcent)."""
+    m = mechs["ch4"]
+    j = first(m, inputs.RXN_TROE)
+    alpha, T3, T1, T2 = 0.6, 200.0, 2000.0, 5000.0
+    tm = oracle.RefMech(edit(m, j, effs=[], troe=[alpha, T3, T1, T2]))
+    T = 1100.0
+    Fc = (1 - alpha) * math.exp(-T / T3) + alpha * math.exp(-T / T1) + math.exp(-T2 / T)
+    c = -0.4 - 0.67 * math.log10(Fc)
+    kinf, k0 = _arrhenius(m.arr[j], T), _arrhenius(m.arr0[j], T)
+    Pr = 10.0 ** (-c)
+    Mtot = Pr * kinf / k0
+    C = np.full(m.ns, Mtot / m.ns)
+    kf = tm.rates(T, C)[0][j]
+    assert kf == pytest.approx(kinf * Pr / (1 + Pr) * Fc, rel=1e-12)
+
+
+def test_troe_extreme_parameters_and_missing_T2(mechs):
+    """T3 = 1e-30, T1 = 1e30 (Appendix C.1): first F_cent term 0, second alpha;
+    a missing T2 drops the third term."""
+    m = mechs["ch4"]
+    j = first(m, inputs.RXN_TROE)
+    alpha = 0.3
+    tm = oracle.RefMech(edit(m, j, effs=[], troe=[alpha, 1e-30, 1e30, np.nan]))
+    T = 1500.0
+    kinf, k0 = _arrhenius(m.arr[j], T), _arrhenius(m.arr0[j], T)
+    C = np.full(m.ns, 0.01 / m.ns)
+    Pr = k0 * C.sum() / kinf
+    L = math.log10(alpha)
+    c, n = -0.4 - 0.67 * L, 0.75 - 1.27 * L
+    P = math.log10(Pr)
+    f1 = (P + c) / (n - 0.14 * (P + c))
+    F = 10.0 ** (L / (1 + f1 * f1))
+    kf = tm.rates(T, C)[0][j]
+    assert np.isfinite(kf)
+    assert kf == pytest.approx(kinf * Pr / (1 + Pr) * F, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["h2", "ch4"])
+def test_reverse_reaction_inverts_equilibrium_constant(mechs, kind):
+    """Writing a reaction backwards inverts K: (kf/kr) * (kf'/kr') = 1."""
+    m = mechs[kind]
+    T, C, p = inputs.random_states(m, 3, seed=5)
+    base = oracle.RefMech(m)
+    for j in range(0, m.nr, max(1, m.nr // 12)):
+        rev = oracle.RefMech(edit(m, j, reverse=True))
+        for c in range(3):
+            kf, kr, _ = base.rates(T[c], C[c])
+            kf2, kr2, _ = rev.rates(T[c], C[c])
+            assert (kf[j] / kr[j]) * (kf2[j] / kr2[j]) == pytest.approx(1.0, rel=1e-11)
+
+
+def test_equilibrium_constant_from_gibbs(mechs, ref):
+    """K = kf/kr equals exp(-sum nu W g / RT) (p_ref/RT)^{sum nu} computed with
+    numpy's power on the oracle's own species Gibbs energies: pins the
+    integer-power expansion for sum(nu) = -1, 0, +1."""
+    m, r = mechs["ch4"], ref["ch4"]
+    T, C, p = inputs.random_states(m, 2, seed=7)
+    seen = set()
+    for c in range(2):
+        g = r.thermo(T[c])["g"]
+        kf, kr, _ = r.rates(T[c], C[c])
+        for j in range(m.nr):
+            nu = np.zeros(m.ns)
+            for s in range(3):
+                if m.rf_idx[j, s] >= 0:
+                    nu[m.rf_idx[j, s]] -= m.rf_nu[j, s]
+                if m.rr_idx[j, s] >= 0:
+                    nu[m.rr_idx[j, s]] += m.rr_nu[j, s]
+            dG = nu @ (m.W * g)
+            K = np.exp(-dG / (R * T[c])) * np.power(101325.0 / (R * T[c]), nu.sum())
+            assert kf[j] / kr[j] == pytest.approx(K, rel=1e-9)
+            seen.add(int(nu.sum()))
+    assert {-1, 0, 1} <= seen
+
+
+@pytest.mark.parametrize("kind", ["h2", "ch4"])
+@pytest.mark.parametrize("reactor", [oracle.CONV, oracle.CONP_LITERAL])
+def test_mass_and_element_conservation(mechs, ref, kind, reactor):
+    """sum_i W_i omega_i = 0 (eq. chemical-reaction-mass-conservation) and
+    sum_i e_ki omega_i = 0 for every element k, relative to the magnitudes."""
+    m, r = mechs[kind], ref[kind]
+    T, C, p = inputs.random_states(m, 64, seed=11)
+    S = r.source(T, C, reactor)
+    w = S[:, 1:]
+    mass = w * m.W
+    assert np.all(np.abs(mass.sum(1)) <= 1e-13 * np.abs(mass).sum(1))
+    for k in range(len(m.elements)):
+        el = w * m.comp[:, k]
+        assert np.all(np.abs(el.sum(1)) <= 1e-13 * np.abs(el).sum(1) + 1e-300)
+
+
+def test_production_rates_are_stoichiometric_sums(mechs, ref):
+    """omega_i = sum_j nu_ij q_j with the oracle's own q_j; omega_T from the
+    oracle's own mass-specific u and c_v (eq. temperature_source)."""
+    m, r = mechs["h2"], ref["h2"]
+    T, C, p = inputs.random_states(m, 4, seed=13)
+    nu = np.zeros((m.ns, m.nr))
+    for j in range(m.nr):
+        for s in range(3):
+            if m.rf_idx[j, s] >= 0:
+                nu[m.rf_idx[j, s], j] -= m.rf_nu[j, s]
+            if m.rr_idx[j, s] >= 0:
+                nu[m.rr_idx[j, s], j] += m.rr_nu[j, s]
+    S = r.source(T, C, oracle.CONV)
+    for c in range(4):
+        q = r.rates(T[c], C[c])[2]
+        w = nu @ q
+        np.testing.assert_allclose(S[c, 1:], w, rtol=1e-12, atol=1e-14 * np.abs(nu).dot(np.abs(q)).max())
+        th = r.thermo(T[c])
+        wT = -np.sum(m.W * th["u"] * w) / np.sum(m.W * C[c] * th["cv"])
+        assert S[c, 0] == pytest.approx(wT, rel=1e-10, abs=1e-12 * np.abs(m.W * th["u"] * w).sum())
+
+
+def test_conp_keeps_pressure_and_enthalpy_rates_zero(mechs, ref):
+    """Constant-pressure form: d(T sum C)/dt = 0 (p fixed), and with the
+    chemical production omega (the CONP_LITERAL rows) the parcel enthalpy
+    rate sum W_i h_i omega_i + rho c_p omega_T vanishes (Appendix B)."""
+    m, r = mechs["ch4"], ref["ch4"]
+    T, C, p = inputs.random_states(m, 16, seed=17)
+    S = r.source(T, C, oracle.CONP)
+    L = r.source(T, C, oracle.CONP_LITERAL)
+    for c in range(16):
+        th = r.thermo(T[c])
+        dpdt = S[c, 0] * C[c].sum() + T[c] * S[c, 1:].sum()
+        assert abs(dpdt) <= 1e-12 * (abs(S[c, 0] * C[c].sum()) + T[c] * np.abs(S[c, 1:]).sum())
+        w, wT = L[c, 1:], L[c, 0]
+        assert S[c, 0] == wT
+        s_dil = wT / T[c] + w.sum() / C[c].sum()
+        np.testing.assert_allclose(S[c, 1:], w - C[c] * s_dil, rtol=1e-12,
+                                   atol=1e-13 * np.abs(w).max())
+        dH = np.sum(m.W * th["h"] * w) + np.sum(m.W * C[c] * th["cp"]) * wT
+        assert abs(dH) <= 1e-12 * np.abs(m.W * th["h"] * w).sum()

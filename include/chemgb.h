@@ -1,0 +1,187 @@
+/*
+ * chemgb -- batched stiff chemistry integration on one GPU (C ABI).
+ *
+ * The library integrates the chemical source term of a reacting-flow solver
+ * cell by cell under operator splitting, following ChemGen (arXiv 2510.10005):
+ * the state of a cell is y = (T, C_1..C_ns) (Section 3, eq.
+ * extracted_problem-1), its right-hand side S(y) = (omega_T, dC/dt) is built
+ * from NASA-7 thermodynamics (Section 2.1, Table 1), Gibbs-based equilibrium
+ * constants and Arrhenius / third-body / Troe rates (Section 2.2), and a cell
+ * is advanced over dt with backward Euler + Newton (Section 3.2) or an SDIRK
+ * scheme in stage-derivative form (Appendix A), each Newton step solving
+ * (I - gamma h J) delta = -f with the analytical Jacobian J (Section 3.2) and
+ * a dense LU with partial pivoting (Section 3.4).
+ *
+ * Conventions shared by every entry point:
+ *   - Units are SI-kmol: C in kmol/m^3, T in K, p in Pa, rho in kg/m^3,
+ *     W in kg/kmol, Ea in J/kmol, R = 8314.46261815324 J/(kmol K),
+ *     p_ref = 101325 Pa.
+ *   - Per-cell arrays are caller-owned DEVICE pointers laid out
+ *     structure-of-arrays: component k of cell c is at [k * N + c].
+ *     (cg_integrate_host is the one exception: host pointers.)
+ *   - Work is enqueued on the CUDA stream `stream` (a cudaStream_t; NULL is
+ *     the legacy default stream) and returns before it completes, except
+ *     where a function says it synchronises.
+ *   - Return values: CG_OK, or an error code for invalid arguments, resource
+ *     or CUDA failures; cg_last_error() then describes the failure (per
+ *     calling thread). Numerical failures of individual cells are reported in
+ *     the per-cell status array, never as a process abort.
+ *   - A cg_mech is immutable after creation; concurrent calls with the same
+ *     mechanism on different streams are allowed.
+ */
+#ifndef CHEMGB_H
+#define CHEMGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cg_mech cg_mech;
+
+typedef enum {
+    CG_OK = 0,
+    CG_EINVAL = 1,        /* invalid argument or mechanism data            */
+    CG_ENOMEM = 2,        /* device or host allocation failed              */
+    CG_ECUDA = 3,         /* a CUDA runtime call failed                    */
+    CG_ECAPACITY = 4,     /* a size exceeds what the library supports      */
+    CG_EUNSUPPORTED = 5   /* option combination not implemented           */
+} cg_status;
+
+/* per-cell status written by cg_integrate */
+enum {
+    CG_CELL_OK = 0,
+    CG_CELL_NEWTON_FAIL = 1,      /* Newton failed at the deepest halving   */
+    CG_CELL_STEP_TOO_SMALL = 2,   /* adaptive step fell below hmin          */
+    CG_CELL_MAX_STEPS = 3,        /* more than max_steps step attempts      */
+    CG_CELL_NONFINITE = 4         /* input state not finite                 */
+};
+
+/* reaction types (Section 2.2) */
+enum { CG_RXN_ELEMENTARY = 0, CG_RXN_THREE_BODY = 1, CG_RXN_LINDEMANN = 2, CG_RXN_TROE = 3 };
+
+/* reactor forms: constant volume (Section 3, eq. temperature_source);
+ * constant pressure with the dilution of the cell's volume (the reading of
+ * Appendix B that keeps p = R T sum C fixed); Appendix B as printed
+ * (enthalpy form of omega_T, dC/dt = omega). */
+enum { CG_CONV = 0, CG_CONP = 1, CG_CONP_LITERAL = 2 };
+
+/* integrators: backward Euler (Section 3.2), SDIRK-2 (Appendix A.1),
+ * SDIRK-4 (Appendix A.2) */
+enum { CG_BE = 0, CG_SDIRK2 = 1, CG_SDIRK4 = 2 };
+
+/* arithmetic of the Newton matrix factorisation */
+enum { CG_FP64 = 0, CG_FP32LU = 1 };
+
+/*
+ * Mechanism description (host arrays, copied by cg_mech_create; the caller
+ * keeps ownership). Reactions are written sum nu^f_i A_i <=> sum nu^r_i A_i
+ * with at most three distinct species on each side.
+ *   W[ns]           molecular masses
+ *   nasa7[ns*7]     a1..a5 (c_p/R polynomial), a6 (h/R constant), a7 (s/R
+ *                   constant); one range used at every temperature
+ *   rxn_type[nr]    CG_RXN_*
+ *   reversible[nr]  0 or 1; reverse rate k_f / K_c (eq. reverse_rate)
+ *   rf_idx/rf_nu[nr*3]  reactant species and integer coefficients (-1 / 0 pad)
+ *   rr_idx/rr_nu[nr*3]  product species and coefficients
+ *   arr[nr*3]       ln A, b, Ea of k = A T^b exp(-Ea/(R T)) (k_inf of falloff)
+ *   arr0[nr*3]      ln A0, b0, Ea0 of the low-pressure limit (falloff only)
+ *   troe[nr*4]      alpha, T3, T1, T2 of eq. f_and_fcent; T2 = NaN: absent
+ *   eff_ptr[nr+1], eff_idx[], eff_val[]  CSR of third-body efficiencies
+ *                   that differ from 1 (eq. TB_optimization)
+ */
+typedef struct {
+    int n_species, n_reactions;
+    const double *W, *nasa7;
+    const int *rxn_type, *reversible;
+    const int *rf_idx, *rf_nu, *rr_idx, *rr_nu;
+    const double *arr, *arr0, *troe;
+    const int *eff_ptr, *eff_idx;
+    const double *eff_val;
+} cg_mech_desc;
+
+/* Validate the description (index ranges, coefficients, sizes), build the
+ * device copy and the assembly schedules of omega and J. Allocates device
+ * memory owned by the mechanism. Errors: CG_EINVAL (bad data; message names
+ * the first offending entry), CG_ECAPACITY (more species or reactions than
+ * one warp's shared memory holds), CG_ENOMEM, CG_ECUDA. */
+cg_status cg_mech_create(const cg_mech_desc *desc, cg_mech **out);
+/* Free a mechanism (NULL is ignored). No call using it may be in flight. */
+void cg_mech_destroy(cg_mech *mech);
+int cg_mech_n_species(const cg_mech *mech);
+int cg_mech_n_reactions(const cg_mech *mech);
+
+/* Source term S(y) = (omega_T, dC_1/dt .. dC_ns/dt) for N cells
+ * (Section 2.2, eqs. chemical-reaction-rate-of-progress, temperature_source;
+ * Appendix B). T[N], C[ns*N] in; S[(ns+1)*N] out, row 0 = omega_T. */
+cg_status cg_eval_rates(const cg_mech *mech, int reactor, int64_t N, const double *T,
+                        const double *C, double *S, void *stream);
+
+/* Analytical Jacobian J = dS/dy (Section 3.2, eq.
+ * derivative_matrices_temp_evol, T and C independent) for N cells.
+ * T[N], C[ns*N] in; J[N*n*n] out, n = ns+1, one row-major n x n block per
+ * cell (cell-major, the one non-SoA output), row/column 0 = T. */
+cg_status cg_eval_jacobian(const cg_mech *mech, int reactor, int64_t N, const double *T,
+                           const double *C, double *J, void *stream);
+
+/* Temperature from the mass-specific energy e (u for CG_CONV, h otherwise)
+ * and mass fractions Y[ns*N] by `iters` Newton iterations on
+ * sum_i Y_i e_i(T) = e (Section 2.1, eqs. temperature-nonlinear ..
+ * netwon_iteration_temperature; the paper uses 5). T[N] holds the initial
+ * guess on entry and the result on exit. */
+cg_status cg_temperature_from_energy(const cg_mech *mech, int reactor, int64_t N,
+                                     const double *e, const double *Y, double *T, int iters,
+                                     void *stream);
+
+/* Integration options (fill with cg_integrate_opts_default, then adjust). */
+typedef struct {
+    int method;        /* CG_BE, CG_SDIRK2, CG_SDIRK4                                 */
+    int reactor;       /* CG_CONV, CG_CONP, CG_CONP_LITERAL                           */
+    int adaptive;      /* 1: error-controlled steps (SDIRK only); 0: nsub fixed steps */
+    int precision;     /* CG_FP64 (CG_FP32LU reserved)                                */
+    int nsub;          /* fixed mode: number of equal steps over dt                   */
+    int max_newton;    /* Newton iterations per stage                                 */
+    int max_steps;     /* adaptive: step attempts before CG_CELL_MAX_STEPS            */
+    int max_halvings;  /* fixed mode: depth of step halving after a failed step       */
+    int err_filter;    /* adaptive: filter the error estimate by (I - gamma h J)^-1   */
+    int reserved;
+    double dt;         /* integration interval, s                                     */
+    double rtol, atol; /* weights w_i = atol + rtol max(|y_n,i|, |y_i|)               */
+    double newton_tol; /* Newton converged when WRMS(change of stage state) <= this   */
+    double h0;         /* adaptive: first step (0: dt)                                */
+    double hmin;       /* adaptive: smallest step                                     */
+    double neg_tol;    /* a step is rejected when some C_i < -neg_tol * sum C         */
+} cg_integrate_opts;
+
+void cg_integrate_opts_default(cg_integrate_opts *opts);
+
+/* Integrate N cells over opts->dt.
+ *   T[N], Y[ns*N]   in: initial temperature and mass fractions;
+ *                   out: final ones (overwritten in place)
+ *   p_or_rho[N]     pressure (CG_CONP, CG_CONP_LITERAL: C = rho Y / W with
+ *                   rho = p / (R T sum Y/W)) or density (CG_CONV)
+ *   cell_status[N]  CG_CELL_* per cell (may be NULL)
+ *   cell_stats[4*N] per cell: accepted steps, rejected or failed attempts,
+ *                   Newton iterations, LU factorisations (SoA; may be NULL)
+ * The work of a cell never depends on another cell. */
+cg_status cg_integrate(const cg_mech *mech, const cg_integrate_opts *opts, int64_t N, double *T,
+                       double *Y, const double *p_or_rho, int32_t *cell_status,
+                       int32_t *cell_stats, void *stream);
+
+/* Same as cg_integrate with HOST arrays: copies the inputs to device memory
+ * owned by the mechanism (grown on demand, freed with it), integrates,
+ * copies the results back and synchronises before returning. Not safe for
+ * concurrent calls on the same mechanism. */
+cg_status cg_integrate_host(const cg_mech *mech, const cg_integrate_opts *opts, int64_t N,
+                            double *T, double *Y, const double *p_or_rho, int32_t *cell_status,
+                            int32_t *cell_stats);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *cg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEMGB_H */

@@ -1,0 +1,205 @@
+"""Python binding of the chemgb C ABI (include/chemgb.h).
+
+Argument marshalling only: every function passes raw device pointers of
+torch tensors (float64 / int32, contiguous, on a CUDA device) and the
+current CUDA stream to the library, where all of the computation happens.
+The names are those of the C entry points. Importing this module does not
+need a GPU; calling into it needs the built library (see build.py) and
+fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ECAPACITY, CG_EUNSUPPORTED = range(6)
+CG_CELL_OK, CG_CELL_NEWTON_FAIL, CG_CELL_STEP_TOO_SMALL, CG_CELL_MAX_STEPS, CG_CELL_NONFINITE = range(5)
+CG_CONV, CG_CONP, CG_CONP_LITERAL = 0, 1, 2
+CG_BE, CG_SDIRK2, CG_SDIRK4 = 0, 1, 2
+CG_FP64, CG_FP32LU = 0, 1
+
+_lib = None
+
+
+class ChemgbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"chemgb error {code}: {msg}")
+        self.code = code
+
+
+class cg_mech_desc(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int), ("n_reactions", ctypes.c_int)] + [
+        (name, ctypes.c_void_p) for name in (
+            "W", "nasa7", "rxn_type", "reversible", "rf_idx", "rf_nu", "rr_idx", "rr_nu",
+            "arr", "arr0", "troe", "eff_ptr", "eff_idx", "eff_val")]
+
+
+class cg_integrate_opts(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in (
+        "method", "reactor", "adaptive", "precision", "nsub", "max_newton", "max_steps",
+        "max_halvings", "err_filter", "reserved")] + [(k, ctypes.c_double) for k in (
+            "dt", "rtol", "atol", "newton_tol", "h0", "hmin", "neg_tol")]
+
+
+EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n_reactions",
+            "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
+            "cg_integrate_opts_default", "cg_integrate", "cg_integrate_host", "cg_last_error")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libchemgb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"chemgb CUDA library not built ({_build.LIB}); run "
+                           "python -m paper_2510_10005_gb300.build")
+    lib = ctypes.CDLL(_build.LIB)
+    P, I, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.cg_mech_create.argtypes = [ctypes.POINTER(cg_mech_desc), ctypes.POINTER(P)]
+    lib.cg_mech_destroy.argtypes = [P]
+    lib.cg_mech_destroy.restype = None
+    lib.cg_mech_n_species.argtypes = [P]
+    lib.cg_mech_n_reactions.argtypes = [P]
+    lib.cg_eval_rates.argtypes = [P, I, L, P, P, P, P]
+    lib.cg_eval_jacobian.argtypes = [P, I, L, P, P, P, P]
+    lib.cg_temperature_from_energy.argtypes = [P, I, L, P, P, P, I, P]
+    lib.cg_integrate_opts_default.argtypes = [ctypes.POINTER(cg_integrate_opts)]
+    lib.cg_integrate_opts_default.restype = None
+    lib.cg_integrate.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, P]
+    lib.cg_integrate_host.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P]
+    lib.cg_last_error.restype = ctypes.c_char_p
+    lib.cg_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != CG_OK:
+        raise ChemgbError(code, load().cg_last_error().decode())
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _dev(t, dtype_name="float64"):
+    import torch
+    dt = {"float64": torch.float64, "int32": torch.int32}[dtype_name]
+    if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA {dtype_name} tensor, got {t.dtype} on {t.device}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# C entry points
+
+
+def cg_mech_create(mech) -> "MechHandle":
+    """Upload a paper_2510_10005_gb300.inputs.Mechanism (host arrays)."""
+    return MechHandle(mech)
+
+
+def cg_mech_destroy(handle: "MechHandle"):
+    handle.close()
+
+
+def cg_integrate_opts_default() -> cg_integrate_opts:
+    o = cg_integrate_opts()
+    load().cg_integrate_opts_default(ctypes.byref(o))
+    return o
+
+
+def make_opts(**kw) -> cg_integrate_opts:
+    o = cg_integrate_opts_default()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def cg_eval_rates(h, reactor, T, C, S, stream=None):
+    _check(load().cg_eval_rates(h.ptr, reactor, T.shape[0], _dev(T), _dev(C), _dev(S), _stream(stream)))
+
+
+def cg_eval_jacobian(h, reactor, T, C, J, stream=None):
+    _check(load().cg_eval_jacobian(h.ptr, reactor, T.shape[0], _dev(T), _dev(C), _dev(J), _stream(stream)))
+
+
+def cg_temperature_from_energy(h, reactor, e, Y, T, iters=5, stream=None):
+    _check(load().cg_temperature_from_energy(h.ptr, reactor, T.shape[0], _dev(e), _dev(Y), _dev(T),
+                                             iters, _stream(stream)))
+
+
+def cg_integrate(h, opts, T, Y, p_or_rho, status=None, stats=None, stream=None):
+    _check(load().cg_integrate(h.ptr, ctypes.byref(opts), T.shape[0], _dev(T), _dev(Y), _dev(p_or_rho),
+                               None if status is None else _dev(status, "int32"),
+                               None if stats is None else _dev(stats, "int32"), _stream(stream)))
+
+
+def cg_integrate_host(h, opts, T, Y, p_or_rho, status=None, stats=None):
+    """Host numpy arrays (float64 / int32, C-contiguous; Y as [ns, N])."""
+    for a in (T, Y, p_or_rho):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(load().cg_integrate_host(h.ptr, ctypes.byref(opts), T.shape[0], _ptr(T), _ptr(Y),
+                                    _ptr(p_or_rho), _ptr(status), _ptr(stats)))
+
+
+class MechHandle:
+    """Owns one cg_mech."""
+
+    def __init__(self, mech):
+        lib = load()
+        f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+        self._keep = dict(
+            W=f64(mech.W), nasa7=f64(mech.nasa7), rxn_type=i32(mech.rtype), reversible=i32(mech.reversible),
+            rf_idx=i32(mech.rf_idx), rf_nu=i32(mech.rf_nu), rr_idx=i32(mech.rr_idx), rr_nu=i32(mech.rr_nu),
+            arr=f64(mech.arr), arr0=f64(mech.arr0), troe=f64(mech.troe), eff_ptr=i32(mech.eff_ptr),
+            eff_idx=i32(mech.eff_idx) if len(mech.eff_idx) else np.zeros(1, np.int32),
+            eff_val=f64(mech.eff_val) if len(mech.eff_val) else np.zeros(1))
+        d = cg_mech_desc(mech.ns, mech.nr, *[self._keep[k].ctypes.data for k in (
+            "W", "nasa7", "rxn_type", "reversible", "rf_idx", "rf_nu", "rr_idx", "rr_nu", "arr", "arr0",
+            "troe", "eff_ptr", "eff_idx", "eff_val")])
+        h = ctypes.c_void_p()
+        _check(lib.cg_mech_create(ctypes.byref(d), ctypes.byref(h)))
+        self.ptr = h.value
+        self.ns, self.nr, self.n = mech.ns, mech.nr, mech.ns + 1
+        self.mech = mech
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().cg_mech_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

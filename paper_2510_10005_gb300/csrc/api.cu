@@ -1,0 +1,682 @@
+// C-ABI of chemgb (declared in include/chemgb.h): mechanism upload and the
+// host-side preparation of the kernels (reaction ordering, thermo table,
+// assembly schedules, shared-memory layout, Butcher tableaux).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "chemgb.h"
+#include "chem_internal.h"
+
+using cg::DevMech;
+using cg::IntParams;
+using cg::Layout;
+
+namespace {
+
+thread_local std::string g_err;
+
+cg_status fail(cg_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+cg_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+const double kR = 8314.46261815324;
+const double kPref = 101325.0;
+const size_t kMaxSmemPerBlock = 227 * 1024;
+
+// One term of an assembly schedule: out[dst] += fac * in[src].
+struct Term {
+    int dst, src;
+    double fac;
+    long order;   // accumulation order within one destination
+};
+
+struct Schedule {
+    int rounds = 0;
+    std::vector<int> dst, src;
+    std::vector<double> fac;
+};
+
+// Pack terms into rounds of 32 with pairwise distinct destinations; the terms
+// of one destination land in increasing rounds in their `order`.
+Schedule make_schedule(std::vector<Term> terms) {
+    std::stable_sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) {
+        return a.dst != b.dst ? a.dst < b.dst : a.order < b.order;
+    });
+    Schedule s;
+    std::vector<int> fill;
+    int last_dst = -1, last_round = -1;
+    for (const Term& t : terms) {
+        int r = (t.dst == last_dst) ? last_round + 1 : 0;
+        while (r < (int)fill.size() && fill[r] == 32) ++r;
+        if (r == (int)fill.size()) {
+            fill.push_back(0);
+            s.dst.resize(fill.size() * 32, -1);
+            s.src.resize(fill.size() * 32, 0);
+            s.fac.resize(fill.size() * 32, 0.0);
+        }
+        const int k = r * 32 + fill[r]++;
+        s.dst[k] = t.dst;
+        s.src[k] = t.src;
+        s.fac[k] = t.fac;
+        last_dst = t.dst;
+        last_round = r;
+    }
+    s.rounds = (int)fill.size();
+    if (s.rounds == 0) {   // keep a valid (empty) device pointer
+        s.dst.assign(32, -1);
+        s.src.assign(32, 0);
+        s.fac.assign(32, 0.0);
+    }
+    return s;
+}
+
+Layout make_layout(int ns, int nr) {
+    const int n = ns + 1;
+    Layout L;
+    L.ld = (n % 2) ? n : n + 1;   // odd stride: fewer bank conflicts on column walks
+    int o = 0;
+    L.G = o; o += n * L.ld;
+    L.RD = o; o += 9 * nr;
+    L.SP = o; o += 4 * ns;
+    L.V = o; o += ns;
+    L.yn = o; o += n;
+    L.Y = o; o += n;
+    L.base = o; o += n;
+    L.S = o; o += n;
+    L.S0 = o; o += n;
+    L.f = o; o += n;
+    L.err = o; o += n;
+    L.y1 = o; o += n;
+    L.colA = o; o += n;
+    L.colB = o; o += n;
+    L.rinv = o; o += n;
+    L.Gam = o; o += 5 * n;
+    L.piv = o; o += (n + 1) / 2;
+    L.total = (o + 1) & ~1;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Butcher tableaux (Appendix A), in stage-derivative form.
+
+struct Tab {
+    int s = 1, err_order = 0, start_zero = 0;
+    double A[5][5] = {}, b[5] = {}, bh[5] = {};
+};
+
+typedef long double ld_t;
+
+// order conditions up to order 4 of a 5-stage method with b = last row of A
+void sdirk4_residual(const ld_t x[9], ld_t res[9]) {
+    const ld_t g = (ld_t)4 / 15;
+    ld_t A[5][5] = {{g, 0, 0, 0, 0},
+                    {(ld_t)1 / 2, g, 0, 0, 0},
+                    {x[0], x[1], g, 0, 0},
+                    {x[2], x[3], x[4], g, 0},
+                    {x[5], x[6], x[7], x[8], g}};
+    ld_t c[5], Ac[5], Ac2[5], AAc[5];
+    for (int i = 0; i < 5; ++i) {
+        c[i] = 0;
+        for (int j = 0; j < 5; ++j) c[i] += A[i][j];
+    }
+    for (int i = 0; i < 5; ++i) {
+        Ac[i] = Ac2[i] = 0;
+        for (int j = 0; j < 5; ++j) { Ac[i] += A[i][j] * c[j]; Ac2[i] += A[i][j] * c[j] * c[j]; }
+    }
+    for (int i = 0; i < 5; ++i) {
+        AAc[i] = 0;
+        for (int j = 0; j < 5; ++j) AAc[i] += A[i][j] * Ac[j];
+    }
+    const ld_t* b = A[4];
+    ld_t s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0, s7 = 0, s8 = 0;
+    for (int i = 0; i < 5; ++i) {
+        s1 += b[i];
+        s2 += b[i] * c[i];
+        s3 += b[i] * c[i] * c[i];
+        s4 += b[i] * Ac[i];
+        s5 += b[i] * c[i] * c[i] * c[i];
+        s6 += b[i] * c[i] * Ac[i];
+        s7 += b[i] * Ac2[i];
+        s8 += b[i] * AAc[i];
+    }
+    res[0] = s1 - 1;
+    res[1] = s2 - (ld_t)1 / 2;
+    res[2] = s3 - (ld_t)1 / 3;
+    res[3] = s4 - (ld_t)1 / 6;
+    res[4] = s5 - (ld_t)1 / 4;
+    res[5] = s6 - (ld_t)1 / 8;
+    res[6] = s7 - (ld_t)1 / 12;
+    res[7] = s8 - (ld_t)1 / 24;
+    res[8] = x[0] + x[1] - (ld_t)3 / 10;   // c3 = 17/30 from the printed row sums
+}
+
+bool gauss_solve(int n, ld_t* M, ld_t* r) {   // M n x n row-major, r rhs -> solution
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (fabsl(M[i * n + k]) > fabsl(M[p * n + k])) p = i;
+        if (M[p * n + k] == 0) return false;
+        if (p != k) {
+            for (int j = 0; j < n; ++j) std::swap(M[k * n + j], M[p * n + j]);
+            std::swap(r[k], r[p]);
+        }
+        for (int i = k + 1; i < n; ++i) {
+            const ld_t f = M[i * n + k] / M[k * n + k];
+            for (int j = k; j < n; ++j) M[i * n + j] -= f * M[k * n + j];
+            r[i] -= f * r[k];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        for (int j = i + 1; j < n; ++j) r[i] -= M[i * n + j] * r[j];
+        r[i] /= M[i * n + i];
+    }
+    return true;
+}
+
+// SDIRK-4 of Appendix A.2: gamma = 4/15, a21 = 1/2, printed to seven digits
+// (a52 not printed; the scheme is stiffly accurate, so a52 = b2). The full
+// precision coefficients solve the order-4 conditions near the printed values.
+bool make_sdirk4(Tab& t) {
+    ld_t x[9] = {0.3541539L, -0.05415395L, 0.08515494L, -0.06484332L, 0.07915325L,
+                 2.100115L, -0.7677800L, 2.399816L, -2.998818L};
+    for (int it = 0; it < 60; ++it) {
+        ld_t r[9], Jm[81];
+        sdirk4_residual(x, r);
+        ld_t rmax = 0;
+        for (int i = 0; i < 9; ++i) rmax = std::max(rmax, fabsl(r[i]));
+        if (rmax < 1e-18L) break;
+        for (int k = 0; k < 9; ++k) {
+            ld_t xp[9], xm[9], rp[9], rm[9];
+            std::copy(x, x + 9, xp);
+            std::copy(x, x + 9, xm);
+            const ld_t hstep = 1e-7L;
+            xp[k] += hstep;
+            xm[k] -= hstep;
+            sdirk4_residual(xp, rp);
+            sdirk4_residual(xm, rm);
+            for (int i = 0; i < 9; ++i) Jm[i * 9 + k] = (rp[i] - rm[i]) / (2 * hstep);
+        }
+        for (int i = 0; i < 9; ++i) r[i] = -r[i];
+        if (!gauss_solve(9, Jm, r)) return false;
+        for (int i = 0; i < 9; ++i) x[i] += r[i];
+    }
+    ld_t r[9];
+    sdirk4_residual(x, r);
+    for (int i = 0; i < 9; ++i)
+        if (fabsl(r[i]) > 1e-15L) return false;
+    const ld_t g = (ld_t)4 / 15;
+    ld_t A[5][5] = {{g, 0, 0, 0, 0},
+                    {(ld_t)1 / 2, g, 0, 0, 0},
+                    {x[0], x[1], g, 0, 0},
+                    {x[2], x[3], x[4], g, 0},
+                    {x[5], x[6], x[7], x[8], g}};
+    // embedded third-order weights on stages 1-4
+    ld_t c[5], Ac[5];
+    for (int i = 0; i < 5; ++i) {
+        c[i] = 0;
+        for (int j = 0; j < 5; ++j) c[i] += A[i][j];
+    }
+    for (int i = 0; i < 5; ++i) {
+        Ac[i] = 0;
+        for (int j = 0; j < 5; ++j) Ac[i] += A[i][j] * c[j];
+    }
+    ld_t M[16], rhs[4] = {1, (ld_t)1 / 2, (ld_t)1 / 3, (ld_t)1 / 6};
+    for (int j = 0; j < 4; ++j) {
+        M[0 * 4 + j] = 1;
+        M[1 * 4 + j] = c[j];
+        M[2 * 4 + j] = c[j] * c[j];
+        M[3 * 4 + j] = Ac[j];
+    }
+    if (!gauss_solve(4, M, rhs)) return false;
+    t.s = 5;
+    t.err_order = 3;
+    t.start_zero = 0;
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) t.A[i][j] = (double)A[i][j];
+    for (int j = 0; j < 5; ++j) {
+        t.b[j] = (double)A[4][j];
+        t.bh[j] = j < 4 ? (double)rhs[j] : 0.0;
+    }
+    return true;
+}
+
+bool make_tableau(int method, Tab& t) {
+    t = Tab();
+    if (method == CG_BE) {
+        t.s = 1; t.A[0][0] = 1.0; t.b[0] = 1.0; t.err_order = 0; t.start_zero = 1;
+        return true;
+    }
+    if (method == CG_SDIRK2) {
+        const double g = 1.0 - std::sqrt(2.0) / 2.0;
+        t.s = 2; t.A[0][0] = g; t.A[1][0] = 1.0 - g; t.A[1][1] = g;
+        t.b[0] = 1.0 - g; t.b[1] = g; t.bh[0] = 1.0; t.bh[1] = 0.0; t.err_order = 1;
+        return true;
+    }
+    if (method == CG_SDIRK4) {
+        static Tab cached;
+        static bool ok = make_sdirk4(cached);
+        t = cached;
+        return ok;
+    }
+    return false;
+}
+
+template <class T> cg_status upload(std::vector<void*>& allocs, const std::vector<T>& h, const T** out) {
+    void* d = nullptr;
+    const size_t bytes = std::max<size_t>(1, h.size()) * sizeof(T);
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (mechanism)");
+    allocs.push_back(d);
+    if (!h.empty()) {
+        e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (mechanism)");
+    }
+    *out = static_cast<const T*>(d);
+    return CG_OK;
+}
+
+}  // namespace
+
+struct cg_mech {
+    DevMech dm;
+    Layout L;
+    int ns = 0, nr = 0;
+    std::vector<void*> allocs;
+    // device workspace of cg_integrate_host
+    int64_t cap = 0;
+    double *wT = nullptr, *wY = nullptr, *wP = nullptr;
+    int32_t *wStatus = nullptr, *wStats = nullptr;
+    cudaStream_t hstream = nullptr;
+};
+
+namespace {
+
+int warps_per_block(const Layout& L) {
+    const size_t per_warp = (size_t)L.total * sizeof(double);
+    if (per_warp > 24 * 1024) return 1;
+    int w = 4;
+    while (w > 1 && (size_t)w * per_warp > kMaxSmemPerBlock) --w;
+    return w;
+}
+
+cg_status validate(const cg_mech_desc* d) {
+    if (!d) return fail(CG_EINVAL, "desc is NULL");
+    const int ns = d->n_species, nr = d->n_reactions;
+    if (ns < 1 || nr < 0) return fail(CG_EINVAL, "n_species must be >= 1 and n_reactions >= 0");
+    if (!d->W || !d->nasa7) return fail(CG_EINVAL, "W and nasa7 are required");
+    for (int i = 0; i < ns; ++i) {
+        if (!(d->W[i] > 0.0) || !std::isfinite(d->W[i])) return fail(CG_EINVAL, "W[%d] must be positive", i);
+        for (int k = 0; k < 7; ++k)
+            if (!std::isfinite(d->nasa7[7 * i + k])) return fail(CG_EINVAL, "nasa7[%d][%d] not finite", i, k);
+    }
+    if (nr == 0) return CG_OK;
+    if (!d->rxn_type || !d->reversible || !d->rf_idx || !d->rf_nu || !d->rr_idx || !d->rr_nu ||
+        !d->arr || !d->arr0 || !d->troe || !d->eff_ptr)
+        return fail(CG_EINVAL, "reaction arrays are required when n_reactions > 0");
+    if (d->eff_ptr[0] != 0) return fail(CG_EINVAL, "eff_ptr[0] must be 0");
+    for (int j = 0; j < nr; ++j) {
+        const int t = d->rxn_type[j];
+        if (t < CG_RXN_ELEMENTARY || t > CG_RXN_TROE) return fail(CG_EINVAL, "reaction %d: bad type %d", j, t);
+        int nf = 0, nb = 0;
+        for (int s = 0; s < 3; ++s) {
+            const int a = d->rf_idx[3 * j + s], b = d->rr_idx[3 * j + s];
+            const int na = d->rf_nu[3 * j + s], nbv = d->rr_nu[3 * j + s];
+            if (a < -1 || a >= ns || b < -1 || b >= ns)
+                return fail(CG_EINVAL, "reaction %d: species index out of range", j);
+            if ((a >= 0) != (na > 0) || (b >= 0) != (nbv > 0) || na < 0 || nbv < 0 || na > 8 || nbv > 8)
+                return fail(CG_EINVAL, "reaction %d: coefficients must be 1..8 on used slots, 0 on empty", j);
+            for (int s2 = 0; s2 < s; ++s2) {
+                if (a >= 0 && d->rf_idx[3 * j + s2] == a) return fail(CG_EINVAL, "reaction %d: repeated reactant", j);
+                if (b >= 0 && d->rr_idx[3 * j + s2] == b) return fail(CG_EINVAL, "reaction %d: repeated product", j);
+            }
+            nf += a >= 0;
+            nb += b >= 0;
+        }
+        if (nf == 0 || nb == 0) return fail(CG_EINVAL, "reaction %d: needs reactants and products", j);
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(d->arr[3 * j + k])) return fail(CG_EINVAL, "reaction %d: arr not finite", j);
+        if (t == CG_RXN_LINDEMANN || t == CG_RXN_TROE)
+            for (int k = 0; k < 3; ++k)
+                if (!std::isfinite(d->arr0[3 * j + k])) return fail(CG_EINVAL, "reaction %d: arr0 not finite", j);
+        if (t == CG_RXN_TROE) {
+            const double* tr = d->troe + 4 * j;
+            if (!std::isfinite(tr[0]) || !(tr[1] != 0.0) || !(tr[2] != 0.0) || !std::isfinite(tr[1]) ||
+                !std::isfinite(tr[2]) || std::isinf(tr[3]))
+                return fail(CG_EINVAL, "reaction %d: Troe parameters invalid", j);
+        }
+        const int e0 = d->eff_ptr[j], e1 = d->eff_ptr[j + 1];
+        if (e1 < e0) return fail(CG_EINVAL, "eff_ptr must be non-decreasing (reaction %d)", j);
+        if (t == CG_RXN_ELEMENTARY && e1 != e0)
+            return fail(CG_EINVAL, "reaction %d: elementary reactions take no efficiencies", j);
+        for (int e = e0; e < e1; ++e) {
+            if (!d->eff_idx || !d->eff_val) return fail(CG_EINVAL, "eff_idx/eff_val required");
+            if (d->eff_idx[e] < 0 || d->eff_idx[e] >= ns)
+                return fail(CG_EINVAL, "reaction %d: efficiency species out of range", j);
+            if (!std::isfinite(d->eff_val[e])) return fail(CG_EINVAL, "reaction %d: efficiency not finite", j);
+        }
+    }
+    return CG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cg_last_error(void) { return g_err.c_str(); }
+
+void cg_mech_destroy(cg_mech* m) {
+    if (!m) return;
+    for (void* p : m->allocs) cudaFree(p);
+    cudaFree(m->wT);
+    cudaFree(m->wY);
+    cudaFree(m->wP);
+    cudaFree(m->wStatus);
+    cudaFree(m->wStats);
+    if (m->hstream) cudaStreamDestroy(m->hstream);
+    delete m;
+}
+
+int cg_mech_n_species(const cg_mech* m) { return m ? m->ns : -1; }
+int cg_mech_n_reactions(const cg_mech* m) { return m ? m->nr : -1; }
+
+cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
+    if (!out) return fail(CG_EINVAL, "out is NULL");
+    *out = nullptr;
+    cg_status st = validate(d);
+    if (st != CG_OK) return st;
+    const int ns = d->n_species, nr = d->n_reactions, n = ns + 1;
+    const Layout L = make_layout(ns, nr);
+    if ((size_t)L.total * sizeof(double) > kMaxSmemPerBlock)
+        return fail(CG_ECAPACITY, "mechanism with %d species and %d reactions needs %zu bytes of shared memory per cell (max %zu)",
+                    ns, nr, (size_t)L.total * sizeof(double), kMaxSmemPerBlock);
+
+    // internal reaction order: by type, stable
+    std::vector<int> perm(nr);
+    for (int j = 0; j < nr; ++j) perm[j] = j;
+    std::stable_sort(perm.begin(), perm.end(),
+                     [&](int a, int b) { return d->rxn_type[a] < d->rxn_type[b]; });
+
+    std::vector<double> th((size_t)cg::TH_ROWS * ns), W(ns), invW(ns);
+    for (int i = 0; i < ns; ++i) {
+        const double* a = d->nasa7 + 7 * i;
+        auto T = [&](int r) -> double& { return th[(size_t)r * ns + i]; };
+        T(cg::TH_A1) = a[0]; T(cg::TH_A2) = a[1]; T(cg::TH_A3) = a[2]; T(cg::TH_A4) = a[3]; T(cg::TH_A5) = a[4];
+        T(cg::TH_H2) = a[1] / 2; T(cg::TH_H3) = a[2] / 3; T(cg::TH_H4) = a[3] / 4; T(cg::TH_H5) = a[4] / 5;
+        T(cg::TH_A6) = a[5];
+        T(cg::TH_S3) = a[2] / 2; T(cg::TH_S4) = a[3] / 3; T(cg::TH_S5) = a[4] / 4;
+        T(cg::TH_A7) = a[6];
+        T(cg::TH_D3) = 2 * a[2]; T(cg::TH_D4) = 3 * a[3]; T(cg::TH_D5) = 4 * a[4];
+        W[i] = d->W[i];
+        invW[i] = 1.0 / d->W[i];
+    }
+
+    std::vector<int> rtype(nr), rev(nr), sumnu(nr), sidx(6 * (size_t)nr, -1), snu(6 * (size_t)nr, 0),
+        hasT2(nr, 0), eff_ptr(nr + 1, 0), eff_idx;
+    std::vector<double> lnA(nr), beta(nr), Ta(nr), dlnA0(nr, 0.0), dbeta0(nr, 0.0), dTa0(nr, 0.0),
+        talpha(nr, 0.0), tiT3(nr, 0.0), tiT1(nr, 0.0), tT2(nr, 0.0), eff_am1;
+    std::vector<Term> wterms, vterms, jterms;
+    std::vector<double> nu(ns);
+    for (int jj = 0; jj < nr; ++jj) {
+        const int j = perm[jj];
+        rtype[jj] = d->rxn_type[j];
+        rev[jj] = d->reversible[j] ? 1 : 0;
+        int sn = 0;
+        std::fill(nu.begin(), nu.end(), 0.0);
+        for (int s = 0; s < 3; ++s) {
+            const int a = d->rf_idx[3 * j + s], b = d->rr_idx[3 * j + s];
+            sidx[(size_t)s * nr + jj] = a;
+            snu[(size_t)s * nr + jj] = a >= 0 ? d->rf_nu[3 * j + s] : 0;
+            sidx[(size_t)(3 + s) * nr + jj] = b;
+            snu[(size_t)(3 + s) * nr + jj] = b >= 0 ? d->rr_nu[3 * j + s] : 0;
+            if (a >= 0) { sn -= d->rf_nu[3 * j + s]; nu[a] -= d->rf_nu[3 * j + s]; }
+            if (b >= 0) { sn += d->rr_nu[3 * j + s]; nu[b] += d->rr_nu[3 * j + s]; }
+        }
+        sumnu[jj] = sn;
+        lnA[jj] = d->arr[3 * j];
+        beta[jj] = d->arr[3 * j + 1];
+        Ta[jj] = d->arr[3 * j + 2] / kR;
+        const bool fall = rtype[jj] == CG_RXN_LINDEMANN || rtype[jj] == CG_RXN_TROE;
+        if (fall) {
+            dlnA0[jj] = d->arr0[3 * j] - d->arr[3 * j];
+            dbeta0[jj] = d->arr0[3 * j + 1] - d->arr[3 * j + 1];
+            dTa0[jj] = (d->arr0[3 * j + 2] - d->arr[3 * j + 2]) / kR;
+        }
+        if (rtype[jj] == CG_RXN_TROE) {
+            const double* tr = d->troe + 4 * j;
+            talpha[jj] = tr[0];
+            tiT3[jj] = 1.0 / tr[1];
+            tiT1[jj] = 1.0 / tr[2];
+            hasT2[jj] = std::isnan(tr[3]) ? 0 : 1;
+            tT2[jj] = hasT2[jj] ? tr[3] : 0.0;
+        }
+        std::vector<std::pair<int, double>> effs;
+        for (int e = d->eff_ptr[j]; e < d->eff_ptr[j + 1]; ++e) {
+            eff_idx.push_back(d->eff_idx[e]);
+            eff_am1.push_back(d->eff_val[e] - 1.0);
+            effs.push_back({d->eff_idx[e], d->eff_val[e] - 1.0});
+        }
+        eff_ptr[jj + 1] = (int)eff_idx.size();
+
+        // schedule terms of this reaction, in a fixed order per destination
+        const bool press = rtype[jj] != CG_RXN_ELEMENTARY;
+        for (int i = 0; i < ns; ++i) {
+            if (nu[i] == 0.0) continue;
+            const long base_order = (long)jj * 64;
+            wterms.push_back({1 + i, 0 * nr + jj, nu[i], base_order});
+            if (press) vterms.push_back({i, 2 * nr + jj, nu[i], base_order});
+            const int row = (1 + i) * L.ld;
+            jterms.push_back({row + 0, 1 * nr + jj, nu[i], base_order});
+            for (int s = 0; s < 6; ++s) {
+                const int sp = sidx[(size_t)s * nr + jj];
+                if (sp >= 0) jterms.push_back({row + 1 + sp, (3 + s) * nr + jj, nu[i], base_order + 1 + s});
+            }
+            if (press)
+                for (size_t e = 0; e < effs.size(); ++e)
+                    jterms.push_back({row + 1 + effs[e].first, 2 * nr + jj, nu[i] * effs[e].second,
+                                      base_order + 8 + (long)e});
+        }
+    }
+    const Schedule ws = make_schedule(wterms), vs = make_schedule(vterms), js = make_schedule(jterms);
+
+    cg_mech* m = new cg_mech();
+    m->ns = ns;
+    m->nr = nr;
+    m->L = L;
+    DevMech& dm = m->dm;
+    dm.ns = ns;
+    dm.nr = nr;
+    dm.n = n;
+    dm.ln_pref_R = std::log(kPref / kR);
+#define UP(vec, field)                                           \
+    if ((st = upload(m->allocs, vec, &dm.field)) != CG_OK) {     \
+        cg_mech_destroy(m);                                      \
+        return st;                                               \
+    }
+    UP(th, th) UP(W, W) UP(invW, invW) UP(rtype, rtype) UP(rev, rev) UP(sumnu, sumnu)
+    UP(sidx, sidx) UP(snu, snu) UP(lnA, lnA) UP(beta, beta) UP(Ta, Ta) UP(dlnA0, dlnA0)
+    UP(dbeta0, dbeta0) UP(dTa0, dTa0) UP(talpha, talpha) UP(tiT3, tiT3) UP(tiT1, tiT1)
+    UP(tT2, tT2) UP(hasT2, hasT2) UP(eff_ptr, eff_ptr) UP(eff_idx, eff_idx) UP(eff_am1, eff_am1)
+    UP(ws.dst, w_dst) UP(ws.src, w_src) UP(ws.fac, w_fac)
+    UP(vs.dst, v_dst) UP(vs.src, v_src) UP(vs.fac, v_fac)
+    UP(js.dst, j_dst) UP(js.src, j_src) UP(js.fac, j_fac)
+#undef UP
+    dm.w_rounds = ws.rounds;
+    dm.v_rounds = vs.rounds;
+    dm.j_rounds = js.rounds;
+    *out = m;
+    return CG_OK;
+}
+
+cg_status cg_eval_rates(const cg_mech* m, int reactor, int64_t N, const double* T, const double* C,
+                        double* S, void* stream) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    if (N < 0 || reactor < CG_CONV || reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad N or reactor");
+    if (N == 0) return CG_OK;
+    if (!T || !C || !S) return fail(CG_EINVAL, "NULL array");
+    cudaError_t e = cg::launch_eval_rates(m->dm, m->L, warps_per_block(m->L), reactor, N, T, C, S,
+                                          (cudaStream_t)stream);
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "eval_rates launch");
+}
+
+cg_status cg_eval_jacobian(const cg_mech* m, int reactor, int64_t N, const double* T, const double* C,
+                           double* J, void* stream) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    if (N < 0 || reactor < CG_CONV || reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad N or reactor");
+    if (N == 0) return CG_OK;
+    if (!T || !C || !J) return fail(CG_EINVAL, "NULL array");
+    cudaError_t e = cg::launch_eval_jacobian(m->dm, m->L, warps_per_block(m->L), reactor, N, T, C, J,
+                                             (cudaStream_t)stream);
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "eval_jacobian launch");
+}
+
+cg_status cg_temperature_from_energy(const cg_mech* m, int reactor, int64_t N, const double* e,
+                                     const double* Y, double* T, int iters, void* stream) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    if (N < 0 || iters < 0 || reactor < CG_CONV || reactor > CG_CONP_LITERAL)
+        return fail(CG_EINVAL, "bad N, iters or reactor");
+    if (N == 0) return CG_OK;
+    if (!e || !Y || !T) return fail(CG_EINVAL, "NULL array");
+    cudaError_t err = cg::launch_temperature(m->dm, reactor, N, e, Y, T, iters, (cudaStream_t)stream);
+    return err == cudaSuccess ? CG_OK : cuda_fail(err, "temperature launch");
+}
+
+void cg_integrate_opts_default(cg_integrate_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->method = CG_SDIRK4;
+    o->reactor = CG_CONP;
+    o->adaptive = 1;
+    o->precision = CG_FP64;
+    o->nsub = 1;
+    o->max_newton = 7;
+    o->max_steps = 100000;
+    o->max_halvings = 10;
+    o->err_filter = 1;
+    o->dt = 1e-6;
+    o->rtol = 1e-6;
+    o->atol = 1e-12;
+    o->newton_tol = 0.03;
+    o->h0 = 0.0;
+    o->hmin = 1e-20;
+    o->neg_tol = 1e-6;
+}
+
+static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
+    if (!o) return fail(CG_EINVAL, "opts is NULL");
+    if (o->method < CG_BE || o->method > CG_SDIRK4) return fail(CG_EINVAL, "bad method");
+    if (o->reactor < CG_CONV || o->reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad reactor");
+    if (o->precision != CG_FP64) return fail(CG_EUNSUPPORTED, "precision %d not available", o->precision);
+    if (!(o->dt > 0.0) || !std::isfinite(o->dt)) return fail(CG_EINVAL, "dt must be positive");
+    if (o->nsub < 1 || o->max_newton < 1 || o->max_steps < 1 || o->max_halvings < 0 || o->max_halvings > 40)
+        return fail(CG_EINVAL, "nsub, max_newton, max_steps >= 1 and 0 <= max_halvings <= 40 required");
+    if (!(o->rtol >= 0.0) || !(o->atol >= 0.0) || !(o->rtol + o->atol > 0.0) || !(o->newton_tol > 0.0) ||
+        !(o->hmin >= 0.0) || !(o->h0 >= 0.0) || !(o->neg_tol >= 0.0))
+        return fail(CG_EINVAL, "tolerances must be non-negative (rtol + atol and newton_tol positive)");
+    Tab t;
+    if (!make_tableau(o->method, t)) return fail(CG_EINVAL, "tableau construction failed");
+    P.method = o->method;
+    P.reactor = o->reactor;
+    P.adaptive = (o->adaptive && o->method != CG_BE) ? 1 : 0;
+    P.nsub = o->nsub;
+    P.max_newton = o->max_newton;
+    P.max_steps = o->max_steps;
+    P.max_halvings = o->max_halvings;
+    P.err_filter = o->err_filter;
+    P.dt = o->dt;
+    P.rtol = o->rtol;
+    P.atol = o->atol;
+    P.newton_tol = o->newton_tol;
+    P.h0 = o->h0;
+    P.hmin = o->hmin;
+    P.neg_tol = o->neg_tol;
+    P.s = t.s;
+    P.err_order = t.err_order;
+    P.start_zero = t.start_zero;
+    for (int i = 0; i < 5; ++i) {
+        for (int j = 0; j < 5; ++j) P.A[i][j] = t.A[i][j];
+        P.b[i] = t.b[i];
+        P.bh[i] = t.bh[i];
+    }
+    return CG_OK;
+}
+
+cg_status cg_integrate(const cg_mech* m, const cg_integrate_opts* o, int64_t N, double* T, double* Y,
+                       const double* p_or_rho, int32_t* cell_status, int32_t* cell_stats,
+                       void* stream) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    IntParams P;
+    cg_status st = make_params(o, P);
+    if (st != CG_OK) return st;
+    if (N < 0) return fail(CG_EINVAL, "N < 0");
+    if (N == 0) return CG_OK;
+    if (!T || !Y || !p_or_rho) return fail(CG_EINVAL, "NULL array");
+    cudaError_t e = cg::launch_integrate(m->dm, m->L, P, warps_per_block(m->L), N, T, Y, p_or_rho,
+                                         cell_status, cell_stats, (cudaStream_t)stream);
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch");
+}
+
+cg_status cg_integrate_host(const cg_mech* mc, const cg_integrate_opts* o, int64_t N, double* T,
+                            double* Y, const double* p_or_rho, int32_t* cell_status,
+                            int32_t* cell_stats) {
+    if (!mc) return fail(CG_EINVAL, "mech is NULL");
+    cg_mech* m = const_cast<cg_mech*>(mc);
+    IntParams P;
+    cg_status st = make_params(o, P);
+    if (st != CG_OK) return st;
+    if (N < 0) return fail(CG_EINVAL, "N < 0");
+    if (N == 0) return CG_OK;
+    if (!T || !Y || !p_or_rho) return fail(CG_EINVAL, "NULL array");
+    cudaError_t e;
+    if (!m->hstream && (e = cudaStreamCreateWithFlags(&m->hstream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    if (N > m->cap) {
+        cudaFree(m->wT); cudaFree(m->wY); cudaFree(m->wP); cudaFree(m->wStatus); cudaFree(m->wStats);
+        m->wT = m->wY = m->wP = nullptr;
+        m->wStatus = m->wStats = nullptr;
+        m->cap = 0;
+        if ((e = cudaMalloc(&m->wT, N * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&m->wY, N * m->ns * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&m->wP, N * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&m->wStatus, N * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&m->wStats, 4 * N * sizeof(int32_t))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc (host-call workspace)");
+        m->cap = N;
+    }
+    cudaStream_t s = m->hstream;
+    if ((e = cudaMemcpyAsync(m->wT, T, N * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(m->wY, Y, N * m->ns * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(m->wP, p_or_rho, N * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync H2D");
+    if ((e = cg::launch_integrate(m->dm, m->L, P, warps_per_block(m->L), N, m->wT, m->wY, m->wP,
+                                  m->wStatus, m->wStats, s)) != cudaSuccess)
+        return cuda_fail(e, "integrate launch");
+    if ((e = cudaMemcpyAsync(T, m->wT, N * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(Y, m->wY, N * m->ns * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync D2H");
+    if (cell_status &&
+        (e = cudaMemcpyAsync(cell_status, m->wStatus, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync D2H");
+    if (cell_stats &&
+        (e = cudaMemcpyAsync(cell_stats, m->wStats, 4 * N * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync D2H");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/chemgb.h declares; argument validation that happens
+before any CUDA call is exercised here (no compute call needs a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2510_10005_gb300 import build, chemgb, inputs
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "chemgb.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cg_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return chemgb.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(chemgb.EXPORTED) <= set(names)
+
+
+def test_opts_default(lib):
+    o = chemgb.cg_integrate_opts_default()
+    assert (o.method, o.reactor, o.adaptive, o.precision) == (chemgb.CG_SDIRK4, chemgb.CG_CONP, 1, 0)
+    assert o.rtol == 1e-6 and o.atol == 1e-12 and o.newton_tol == 0.03 and o.neg_tol == 1e-6
+    assert ctypes.sizeof(chemgb.cg_integrate_opts) == 10 * 4 + 7 * 8
+
+
+def _desc(mech):
+    keep = dict(W=mech.W.astype(np.float64), nasa7=mech.nasa7.astype(np.float64),
+                rxn_type=mech.rtype.astype(np.int32), reversible=mech.reversible.astype(np.int32),
+                rf_idx=mech.rf_idx.astype(np.int32), rf_nu=mech.rf_nu.astype(np.int32),
+                rr_idx=mech.rr_idx.astype(np.int32), rr_nu=mech.rr_nu.astype(np.int32),
+                arr=mech.arr.astype(np.float64), arr0=mech.arr0.astype(np.float64),
+                troe=mech.troe.astype(np.float64), eff_ptr=mech.eff_ptr.astype(np.int32),
+                eff_idx=mech.eff_idx.astype(np.int32), eff_val=mech.eff_val.astype(np.float64))
+    d = chemgb.cg_mech_desc(mech.ns, mech.nr, *[keep[k].ctypes.data for k in (
+        "W", "nasa7", "rxn_type", "reversible", "rf_idx", "rf_nu", "rr_idx", "rr_nu", "arr", "arr0",
+        "troe", "eff_ptr", "eff_idx", "eff_val")])
+    return d, keep
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("rf_idx", 99, "species index out of range"),
+    ("rf_nu", 0, "coefficients"),
+    ("rtype", 7, "bad type"),
+])
+def test_mech_create_rejects_bad_data(lib, field, value, needle):
+    m = inputs.gen_mechanism("h2").copy()
+    getattr(m, field).flat[0] = value
+    d, keep = _desc(m)
+    h = ctypes.c_void_p()
+    code = lib.cg_mech_create(ctypes.byref(d), ctypes.byref(h))
+    assert code == chemgb.CG_EINVAL and h.value is None
+    assert needle in lib.cg_last_error().decode()
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.cg_mech_create(None, ctypes.byref(h)) == chemgb.CG_EINVAL
+    o = chemgb.cg_integrate_opts_default()
+    assert lib.cg_integrate(None, ctypes.byref(o), 4, None, None, None, None, None, None) == chemgb.CG_EINVAL
+    assert "mech is NULL" in lib.cg_last_error().decode()
+    assert lib.cg_mech_n_species(None) == -1

@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (derived from the arithmetic, also in the design doc):
+  * omega: both sides sum the same terms nu_ij q_j in different orders, so
+    the difference is bounded by a few ulp of sum_j |nu_ij q_j|; the test
+    allows 1e-12 of that scale (the exps of rates and equilibrium constants
+    are evaluated differently and differ by ~1e-15 relative).
+  * J: 1e-10 of the entry plus 1e-12 of its row's largest entry.
+  * Fixed-step integration (backward Euler, Newton iterated to 1e-10 of the
+    state): relative 1e-10 on T and on every Y_k above 1e-12, absolute 1e-20
+    below (the benchmark spec's fixed-step bar, with the floor where a mass fraction
+    carries no more digits than the Newton tolerance leaves it).
+  * Adaptive integration: within the integrator's rtol (1e-6).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_10005_gb300 import chemgb, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def handles(mechs):
+    chemgb.load(build_if_missing=True)
+    return {k: chemgb.cg_mech_create(m) for k, m in mechs.items()}
+
+
+def d(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def gpu_rates(h, T, C, reactor):
+    Tt, Ct = d(T), d(C.T)                      # SoA [ns][N]
+    S = torch.empty((h.n, len(T)), dtype=torch.float64, device=DEV)
+    chemgb.cg_eval_rates(h, reactor, Tt, Ct, S)
+    torch.cuda.synchronize()
+    return S.cpu().numpy().T                   # [N][n]
+
+
+def nu_matrix(m):
+    nu = np.zeros((m.ns, m.nr))
+    for j in range(m.nr):
+        for s in range(3):
+            if m.rf_idx[j, s] >= 0:
+                nu[m.rf_idx[j, s], j] -= m.rf_nu[j, s]
+            if m.rr_idx[j, s] >= 0:
+                nu[m.rr_idx[j, s], j] += m.rr_nu[j, s]
+    return nu
+
+
+@pytest.mark.parametrize("kind", ["h2", "ch4"])
+@pytest.mark.parametrize("reactor", [chemgb.CG_CONV, chemgb.CG_CONP, chemgb.CG_CONP_LITERAL])
+def test_rates_parity(mechs, ref, handles, kind, reactor):
+    m, r, h = mechs[kind], ref[kind], handles[kind]
+    T, C, p = inputs.random_states(m, 200, seed=101)   # Section 5.1 recipe; 200 = 6 warps of 32 + tail
+    Sg = gpu_rates(h, T, C, reactor)
+    So = r.source(T, C, reactor)
+    nu = np.abs(nu_matrix(m))
+    for c in range(len(T)):
+        q = np.abs(r.rates(T[c], C[c])[2])
+        scale = nu @ q
+        if reactor == chemgb.CG_CONP:
+            scale = scale + C[c] * (np.abs(So[c, 0]) / T[c] + scale.sum() / C[c].sum())
+        th = r.thermo(T[c])
+        e = th["u"] if reactor == chemgb.CG_CONV else th["h"]
+        cv = th["cv"] if reactor == chemgb.CG_CONV else th["cp"]
+        tscale = np.sum(np.abs(m.W * e) * (nu @ q)) / np.sum(m.W * C[c] * cv)
+        assert abs(Sg[c, 0] - So[c, 0]) <= 1e-12 * tscale + 1e-12 * abs(So[c, 0])
+        np.testing.assert_array_less(np.abs(Sg[c, 1:] - So[c, 1:]), 1e-12 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("kind", ["h2", "ch4"])
+@pytest.mark.parametrize("reactor", [chemgb.CG_CONV, chemgb.CG_CONP])
+def test_jacobian_parity(mechs, ref, handles, kind, reactor):
+    m, r, h = mechs[kind], ref[kind], handles[kind]
+    N = 37   # a ragged count
+    T, C, p = inputs.random_states(m, N, seed=202)
+    J = torch.empty((N, h.n, h.n), dtype=torch.float64, device=DEV)
+    chemgb.cg_eval_jacobian(h, reactor, d(T), d(C.T), J)
+    torch.cuda.synchronize()
+    Jg = J.cpu().numpy()
+    Jo = r.jacobian(T, C, reactor)
+    rowmax = np.abs(Jo).max(axis=2, keepdims=True)
+    err = np.abs(Jg - Jo)
+    assert np.all(err <= 1e-10 * np.abs(Jo) + 1e-12 * rowmax)
+
+
+def test_temperature_recovery_parity(mechs, ref, handles):
+    m, r, h = mechs["ch4"], ref["ch4"], handles["ch4"]
+    T, Y, p = inputs.field_flames(m, 300, seed=5)
+    e = np.array([Y[c] @ r.thermo(T[c])["h"] for c in range(300)])
+    T0 = T + 250.0
+    To = r.temperature(e, Y, T0, iters=5, reactor=oracle.CONP)
+    Tg = d(T0)
+    chemgb.cg_temperature_from_energy(h, chemgb.CG_CONP, d(e), d(Y.T), Tg, 5)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(Tg.cpu().numpy(), To, rtol=1e-12)
+    np.testing.assert_allclose(Tg.cpu().numpy(), T, rtol=1e-8)
+
+
+def run_gpu(h, opts, T, Y, p):
+    N = len(T)
+    Tt, Yt, pt = d(T), d(Y.T), d(p)
+    st = torch.empty(N, dtype=torch.int32, device=DEV)
+    stats = torch.empty((4, N), dtype=torch.int32, device=DEV)
+    chemgb.cg_integrate(h, opts, Tt, Yt, pt, st, stats)
+    torch.cuda.synchronize()
+    return Tt.cpu().numpy(), Yt.cpu().numpy().T, st.cpu().numpy(), stats.cpu().numpy().T
+
+
+BE_OPTS = dict(method=oracle.BE, adaptive=0, dt=1e-5, rtol=1e-10, atol=1e-16, newton_tol=1.0,
+               max_newton=20, max_halvings=10, reactor=oracle.CONP)
+
+
+def assert_state_close(Tg, Yg, To, Yo, rel, floor):
+    np.testing.assert_allclose(Tg, To, rtol=rel, atol=0)
+    bad = np.abs(Yg - Yo) > rel * np.abs(Yo) + floor
+    assert not bad.any(), (np.argwhere(bad)[:5], np.abs(Yg - Yo)[bad][:5], Yo[bad][:5])
+
+
+def test_backward_euler_parity_full_config(mechs, ref, handles):
+    """9-species mechanism, constant pressure, one backward-Euler step of
+    1e-5 s (plus halvings) on 4096 cells: T0 in U[1000, 1500] K, 1 atm,
+    phi in U[0.5, 2]."""
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 4096, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=0)
+    To, Yo, so, sto = r.integrate(T, Y, p, BE_OPTS, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**BE_OPTS), T, Y, p)
+    assert np.all(so == 0)
+    np.testing.assert_array_equal(sg, so)
+    assert np.mean(np.all(stg == sto, axis=1)) > 0.99
+    assert_state_close(Tg, Yg, To, Yo, 1e-10, 1e-22)
+
+
+@pytest.mark.parametrize("method", [chemgb.CG_SDIRK2, chemgb.CG_SDIRK4])
+def test_fixed_step_sdirk_parity(mechs, ref, handles, method):
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 67, (1100, 1400), (1, 1), (0.5, 2), "H2", seed=3)
+    o = dict(BE_OPTS, method=method, dt=2e-6, nsub=4)
+    To, Yo, so, _ = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, _ = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    assert_state_close(Tg, Yg, To, Yo, 1e-10, 1e-22)
+
+
+ADAPT = dict(method=oracle.SDIRK4, adaptive=1, dt=1e-6, rtol=1e-6, atol=1e-12, newton_tol=0.03,
+             max_newton=7, reactor=oracle.CONP)
+
+
+def test_adaptive_sdirk4_parity_flame_field(mechs, ref, handles):
+    """53-species mechanism, 1-D flame-like field (unburnt, front, burnt),
+    SDIRK-4 with error control, rtol 1e-6: a stratified 128-cell sample."""
+    m, r, h = mechs["ch4"], ref["ch4"], handles["ch4"]
+    T, Y, p = inputs.field_flames(m, 4096, seed=0)
+    idx = np.arange(0, 4096, 32)
+    To, Yo, so, sto = r.integrate(T[idx], Y[idx], p[idx], ADAPT, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**ADAPT), T[idx], Y[idx], p[idx])
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    np.testing.assert_allclose(Tg, To, rtol=1e-6)
+    assert np.max(np.abs(Yg - Yo)) < 1e-6
+    # both sides take the same steps except where err sits at the threshold
+    assert np.mean(np.all(stg == sto, axis=1)) > 0.9
+
+
+def test_adaptive_sdirk4_parity_h2(mechs, ref, handles):
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 100, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=7)
+    o = dict(ADAPT, dt=1e-5)
+    To, Yo, so, _ = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, _ = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    np.testing.assert_allclose(Tg, To, rtol=1e-6)
+    assert np.max(np.abs(Yg - Yo)) < 1e-6
+
+
+def test_edge_cases(mechs, ref, handles):
+    m, h = mechs["h2"], handles["h2"]
+    o = chemgb.make_opts(**BE_OPTS)
+    # N = 0 is a no-op
+    e = torch.empty(0, dtype=torch.float64, device=DEV)
+    chemgb.cg_integrate(h, o, e, torch.empty((m.ns, 0), dtype=torch.float64, device=DEV), e)
+    # one cell, and a non-finite cell next to a good one
+    T, Y, p = inputs.field_reactor(m, 2, (1200, 1200), (1, 1), (1, 1), "H2", seed=1)
+    T[0] = np.nan
+    Tg, Yg, sg, stg = run_gpu(h, o, T, Y, p)
+    assert sg[0] == chemgb.CG_CELL_NONFINITE and sg[1] == chemgb.CG_CELL_OK
+    assert np.isnan(Tg[0]) and np.all(stg[0] == 0)
+    Tg1, Yg1, sg1, _ = run_gpu(h, o, T[1:], Y[1:], p[1:])
+    assert Tg1[0] == Tg[1] and np.array_equal(Yg1[0], Yg[1])   # cells are independent
+    # failure statuses, as the oracle's
+    r = ref["h2"]
+    T, Y, p = inputs.field_reactor(m, 3, (1400, 1400), (1, 1), (1, 1), "H2", seed=0)
+    for kw, want in ((dict(BE_OPTS, max_newton=1, max_halvings=0), 1),
+                     (dict(ADAPT, dt=1e-4, max_steps=3), 3),
+                     (dict(ADAPT, dt=1e-5, hmin=1e-3), 2)):
+        _, _, sg, _ = run_gpu(h, chemgb.make_opts(**kw), T, Y, p)
+        _, _, so, _ = r.integrate(T, Y, p, kw)
+        assert np.all(sg == want) and np.all(so == want)
+
+
+def test_host_entry_point_matches_device(mechs, handles):
+    m, h = mechs["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 513, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=9)
+    o = chemgb.make_opts(**BE_OPTS)
+    Tg, Yg, sg, stg = run_gpu(h, o, T, Y, p)
+    Th, Yh, ph = T.copy(), np.ascontiguousarray(Y.T), p.copy()
+    sh = np.zeros(513, np.int32)
+    sth = np.zeros((4, 513), np.int32)
+    chemgb.cg_integrate_host(h, o, Th, Yh, ph, sh, sth)
+    np.testing.assert_array_equal(Th, Tg)
+    np.testing.assert_array_equal(Yh.T, Yg)
+    np.testing.assert_array_equal(sh, sg)
+    np.testing.assert_array_equal(sth.T, stg)

@@ -184,7 +184,9 @@ def run_gpu(args):
 
     mech, T, Y, p = make_workload(seed=rank, cells=args.cells)
     h = chemgb.cg_mech_create(mech)
-    opts = chemgb.make_opts(**OPTS)
+    if args.team:
+        chemgb.cg_mech_set_launch(h, args.team, args.tpb)
+    opts = chemgb.make_opts(**OPTS, precision=args.precision)
     N = len(T)
     T0 = torch.tensor(T, dtype=torch.float64, device=dev)
     Y0 = torch.tensor(np.ascontiguousarray(Y.T), dtype=torch.float64, device=dev)
@@ -304,6 +306,9 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cells", type=int, default=CELLS, help="cells per GPU (default: the workload's)")
+    ap.add_argument("--team", type=int, default=0, help="threads per cell (default: the library's choice)")
+    ap.add_argument("--tpb", type=int, default=1, help="cells per block with --team 32")
+    ap.add_argument("--precision", type=int, default=0, help="0: FP64 Newton matrix, 1: FP32 LU")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -112,6 +112,19 @@ void cg_mech_destroy(cg_mech *mech);
 int cg_mech_n_species(const cg_mech *mech);
 int cg_mech_n_reactions(const cg_mech *mech);
 
+/* Launch shape of every kernel that uses this mechanism: `team` threads
+ * (32, 64, 128 or 256) cooperate on one cell and `teams_per_block` cells
+ * share a block (must be 1 when team > 32). The default is one warp per cell
+ * up to 24 unknowns and two warps per cell above. Changing the team size
+ * rebuilds the assembly schedules (synchronises the device); no call using
+ * the mechanism may run concurrently. Results do not depend on the shape
+ * beyond the summation order of team-wide reductions. Errors: CG_EINVAL
+ * (bad shape), CG_ECAPACITY (shared memory), CG_ENOMEM, CG_ECUDA. This is
+ * a launch-tuning hook, not part of the method of the paper. */
+cg_status cg_mech_set_launch(cg_mech *mech, int team, int teams_per_block);
+/* Current launch shape; returns 0, or -1 for a NULL mechanism. */
+int cg_mech_get_launch(const cg_mech *mech, int *team, int *teams_per_block);
+
 /* Source term S(y) = (omega_T, dC_1/dt .. dC_ns/dt) for N cells
  * (Section 2.2, eqs. chemical-reaction-rate-of-progress, temperature_source;
  * Appendix B). T[N], C[ns*N] in; S[(ns+1)*N] out, row 0 = omega_T. */

@@ -46,6 +46,7 @@ class cg_integrate_opts(ctypes.Structure):
 
 
 EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n_reactions",
+            "cg_mech_set_launch", "cg_mech_get_launch",
             "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_host", "cg_last_error")
 
@@ -71,6 +72,8 @@ def load(build_if_missing: bool = False):
     lib.cg_mech_destroy.restype = None
     lib.cg_mech_n_species.argtypes = [P]
     lib.cg_mech_n_reactions.argtypes = [P]
+    lib.cg_mech_set_launch.argtypes = [P, I, I]
+    lib.cg_mech_get_launch.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.cg_eval_rates.argtypes = [P, I, L, P, P, P, P]
     lib.cg_eval_jacobian.argtypes = [P, I, L, P, P, P, P]
     lib.cg_temperature_from_energy.argtypes = [P, I, L, P, P, P, I, P]
@@ -127,6 +130,16 @@ def cg_mech_create(mech) -> "MechHandle":
 
 def cg_mech_destroy(handle: "MechHandle"):
     handle.close()
+
+
+def cg_mech_set_launch(h, team: int, teams_per_block: int = 1):
+    _check(load().cg_mech_set_launch(h.ptr, team, teams_per_block))
+
+
+def cg_mech_get_launch(h):
+    t, b = ctypes.c_int(), ctypes.c_int()
+    load().cg_mech_get_launch(h.ptr, ctypes.byref(t), ctypes.byref(b))
+    return t.value, b.value
 
 
 def cg_integrate_opts_default() -> cg_integrate_opts:

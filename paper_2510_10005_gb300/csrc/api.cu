@@ -47,51 +47,66 @@ struct Term {
 };
 
 struct Schedule {
-    int rounds = 0;
+    int len = 0;   // terms per lane
     std::vector<int> dst, src;
     std::vector<double> fac;
 };
 
-// Pack terms into rounds of 32 with pairwise distinct destinations; the terms
-// of one destination land in increasing rounds in their `order`.
-Schedule make_schedule(std::vector<Term> terms) {
+// Lane-owned schedule: terms are grouped by destination (in their `order`
+// within a destination), destinations are dealt to the 32 lanes longest
+// first onto the least-loaded lane, and each lane's terms are laid out at
+// [t * lanes + lane]; the last term of a destination carries its index.
+Schedule make_schedule(std::vector<Term> terms, int lanes_n) {
     std::stable_sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) {
         return a.dst != b.dst ? a.dst < b.dst : a.order < b.order;
     });
-    Schedule s;
-    std::vector<int> fill;
-    int last_dst = -1, last_round = -1;
-    for (const Term& t : terms) {
-        int r = (t.dst == last_dst) ? last_round + 1 : 0;
-        while (r < (int)fill.size() && fill[r] == 32) ++r;
-        if (r == (int)fill.size()) {
-            fill.push_back(0);
-            s.dst.resize(fill.size() * 32, -1);
-            s.src.resize(fill.size() * 32, 0);
-            s.fac.resize(fill.size() * 32, 0.0);
-        }
-        const int k = r * 32 + fill[r]++;
-        s.dst[k] = t.dst;
-        s.src[k] = t.src;
-        s.fac[k] = t.fac;
-        last_dst = t.dst;
-        last_round = r;
+    struct Run { int dst; size_t b, e; };
+    std::vector<Run> runs;
+    for (size_t i = 0; i < terms.size();) {
+        size_t j = i;
+        while (j < terms.size() && terms[j].dst == terms[i].dst) ++j;
+        runs.push_back({terms[i].dst, i, j});
+        i = j;
     }
-    s.rounds = (int)fill.size();
-    if (s.rounds == 0) {   // keep a valid (empty) device pointer
-        s.dst.assign(32, -1);
-        s.src.assign(32, 0);
-        s.fac.assign(32, 0.0);
+    std::vector<Run> by_len = runs;
+    std::stable_sort(by_len.begin(), by_len.end(),
+                     [](const Run& a, const Run& b) { return a.e - a.b > b.e - b.b; });
+    std::vector<std::vector<Run>> lanes(lanes_n);
+    std::vector<size_t> load(lanes_n, 0);
+    for (const Run& r : by_len) {
+        int best = 0;
+        for (int l = 1; l < lanes_n; ++l)
+            if (load[l] < load[best]) best = l;
+        lanes[best].push_back(r);
+        load[best] += r.e - r.b;
+    }
+    Schedule s;
+    s.len = (int)*std::max_element(load.begin(), load.end());
+    const size_t slots = (size_t)std::max(1, s.len) * lanes_n;
+    s.dst.assign(slots, -1);
+    s.src.assign(slots, 0);
+    s.fac.assign(slots, 0.0);
+    for (int l = 0; l < lanes_n; ++l) {
+        std::sort(lanes[l].begin(), lanes[l].end(), [](const Run& a, const Run& b) { return a.dst < b.dst; });
+        size_t t = 0;
+        for (const Run& r : lanes[l])
+            for (size_t i = r.b; i < r.e; ++i, ++t) {
+                const size_t k = t * lanes_n + l;
+                s.src[k] = terms[i].src;
+                s.fac[k] = terms[i].fac;
+                s.dst[k] = (i + 1 == r.e) ? r.dst : -1;
+            }
     }
     return s;
 }
 
-Layout make_layout(int ns, int nr) {
+// mat_bytes: 8 for the FP64 Newton matrix, 4 for the FP32 one
+Layout make_layout(int ns, int nr, int mat_bytes = 8) {
     const int n = ns + 1;
     Layout L;
     L.ld = (n % 2) ? n : n + 1;   // odd stride: fewer bank conflicts on column walks
     int o = 0;
-    L.G = o; o += n * L.ld;
+    L.G = o; o += (n * L.ld * mat_bytes + 7) / 8;
     L.RD = o; o += 9 * nr;
     L.SP = o; o += 4 * ns;
     L.V = o; o += ns;
@@ -108,6 +123,7 @@ Layout make_layout(int ns, int nr) {
     L.rinv = o; o += n;
     L.Gam = o; o += 5 * n;
     L.piv = o; o += (n + 1) / 2;
+    L.red = o; o += 24;
     L.total = (o + 1) & ~1;
     return L;
 }
@@ -295,9 +311,13 @@ template <class T> cg_status upload(std::vector<void*>& allocs, const std::vecto
 
 struct cg_mech {
     DevMech dm;
-    Layout L;
+    Layout L;     // FP64 Newton matrix
+    Layout L32;   // FP32 Newton matrix (mixed precision)
     int ns = 0, nr = 0;
-    std::vector<void*> allocs;
+    int tpb = 1;                       // teams per block (team = dm.team threads)
+    std::vector<void*> allocs;         // mechanism data
+    std::vector<void*> sched_allocs;   // schedules (rebuilt when the team size changes)
+    std::vector<Term> wterms, vterms, jterms;
     // device workspace of cg_integrate_host
     int64_t cap = 0;
     double *wT = nullptr, *wY = nullptr, *wP = nullptr;
@@ -307,12 +327,42 @@ struct cg_mech {
 
 namespace {
 
-int warps_per_block(const Layout& L) {
-    const size_t per_warp = (size_t)L.total * sizeof(double);
-    if (per_warp > 24 * 1024) return 1;
+// Default launch shape: one warp per cell for small mechanisms (several
+// cells per block), two warps per cell from 24 unknowns on, so that every SM
+// sub-partition holds two instruction streams.
+int default_team(int n) { return n <= 24 ? 32 : 64; }
+
+int default_tpb(int team, const Layout& L) {
+    if (team > 32) return 1;
+    const size_t per = (size_t)L.total * sizeof(double);
+    if (per > 24 * 1024) return 1;
     int w = 4;
-    while (w > 1 && (size_t)w * per_warp > kMaxSmemPerBlock) --w;
+    while (w > 1 && (size_t)w * per > kMaxSmemPerBlock) --w;
     return w;
+}
+
+template <class T> cg_status upload_sched(cg_mech* m, const std::vector<T>& h, const T** out) {
+    return upload(m->sched_allocs, h, out);
+}
+
+cg_status build_schedules(cg_mech* m, int team) {
+    for (void* p : m->sched_allocs) cudaFree(p);
+    m->sched_allocs.clear();
+    const Schedule ws = make_schedule(m->wterms, team), vs = make_schedule(m->vterms, team),
+                   js = make_schedule(m->jterms, team);
+    DevMech& dm = m->dm;
+    cg_status st;
+    if ((st = upload_sched(m, ws.dst, &dm.w_dst)) || (st = upload_sched(m, ws.src, &dm.w_src)) ||
+        (st = upload_sched(m, ws.fac, &dm.w_fac)) || (st = upload_sched(m, vs.dst, &dm.v_dst)) ||
+        (st = upload_sched(m, vs.src, &dm.v_src)) || (st = upload_sched(m, vs.fac, &dm.v_fac)) ||
+        (st = upload_sched(m, js.dst, &dm.j_dst)) || (st = upload_sched(m, js.src, &dm.j_src)) ||
+        (st = upload_sched(m, js.fac, &dm.j_fac)))
+        return st;
+    dm.w_len = ws.len;
+    dm.v_len = vs.len;
+    dm.j_len = js.len;
+    dm.team = team;
+    return CG_OK;
 }
 
 cg_status validate(const cg_mech_desc* d) {
@@ -383,6 +433,7 @@ const char* cg_last_error(void) { return g_err.c_str(); }
 void cg_mech_destroy(cg_mech* m) {
     if (!m) return;
     for (void* p : m->allocs) cudaFree(p);
+    for (void* p : m->sched_allocs) cudaFree(p);
     cudaFree(m->wT);
     cudaFree(m->wY);
     cudaFree(m->wP);
@@ -394,6 +445,32 @@ void cg_mech_destroy(cg_mech* m) {
 
 int cg_mech_n_species(const cg_mech* m) { return m ? m->ns : -1; }
 int cg_mech_n_reactions(const cg_mech* m) { return m ? m->nr : -1; }
+
+cg_status cg_mech_set_launch(cg_mech* m, int team, int teams_per_block) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    if (team != 32 && team != 64 && team != 128 && team != 256)
+        return fail(CG_EINVAL, "team must be 32, 64, 128 or 256 threads");
+    if (teams_per_block < 1 || (team > 32 && teams_per_block != 1) || team * teams_per_block > 1024)
+        return fail(CG_EINVAL, "teams_per_block must be 1 for teams above one warp, and blocks <= 1024 threads");
+    if ((size_t)teams_per_block * m->L.total * sizeof(double) > kMaxSmemPerBlock)
+        return fail(CG_ECAPACITY, "%d cells per block need more than %zu bytes of shared memory",
+                    teams_per_block, kMaxSmemPerBlock);
+    if (team != m->dm.team) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+        cg_status st = build_schedules(m, team);
+        if (st != CG_OK) return st;
+    }
+    m->tpb = teams_per_block;
+    return CG_OK;
+}
+
+int cg_mech_get_launch(const cg_mech* m, int* team, int* teams_per_block) {
+    if (!m) return -1;
+    if (team) *team = m->dm.team;
+    if (teams_per_block) *teams_per_block = m->tpb;
+    return 0;
+}
 
 cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     if (!out) return fail(CG_EINVAL, "out is NULL");
@@ -492,12 +569,12 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
                                       base_order + 8 + (long)e});
         }
     }
-    const Schedule ws = make_schedule(wterms), vs = make_schedule(vterms), js = make_schedule(jterms);
 
     cg_mech* m = new cg_mech();
     m->ns = ns;
     m->nr = nr;
     m->L = L;
+    m->L32 = make_layout(ns, nr, 4);
     DevMech& dm = m->dm;
     dm.ns = ns;
     dm.nr = nr;
@@ -512,13 +589,16 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     UP(sidx, sidx) UP(snu, snu) UP(lnA, lnA) UP(beta, beta) UP(Ta, Ta) UP(dlnA0, dlnA0)
     UP(dbeta0, dbeta0) UP(dTa0, dTa0) UP(talpha, talpha) UP(tiT3, tiT3) UP(tiT1, tiT1)
     UP(tT2, tT2) UP(hasT2, hasT2) UP(eff_ptr, eff_ptr) UP(eff_idx, eff_idx) UP(eff_am1, eff_am1)
-    UP(ws.dst, w_dst) UP(ws.src, w_src) UP(ws.fac, w_fac)
-    UP(vs.dst, v_dst) UP(vs.src, v_src) UP(vs.fac, v_fac)
-    UP(js.dst, j_dst) UP(js.src, j_src) UP(js.fac, j_fac)
 #undef UP
-    dm.w_rounds = ws.rounds;
-    dm.v_rounds = vs.rounds;
-    dm.j_rounds = js.rounds;
+    m->wterms.swap(wterms);
+    m->vterms.swap(vterms);
+    m->jterms.swap(jterms);
+    const int team = default_team(n);
+    if ((st = build_schedules(m, team)) != CG_OK) {
+        cg_mech_destroy(m);
+        return st;
+    }
+    m->tpb = default_tpb(team, L);
     *out = m;
     return CG_OK;
 }
@@ -529,7 +609,7 @@ cg_status cg_eval_rates(const cg_mech* m, int reactor, int64_t N, const double* 
     if (N < 0 || reactor < CG_CONV || reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad N or reactor");
     if (N == 0) return CG_OK;
     if (!T || !C || !S) return fail(CG_EINVAL, "NULL array");
-    cudaError_t e = cg::launch_eval_rates(m->dm, m->L, warps_per_block(m->L), reactor, N, T, C, S,
+    cudaError_t e = cg::launch_eval_rates(m->dm, m->L, m->tpb, reactor, N, T, C, S,
                                           (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "eval_rates launch");
 }
@@ -540,7 +620,7 @@ cg_status cg_eval_jacobian(const cg_mech* m, int reactor, int64_t N, const doubl
     if (N < 0 || reactor < CG_CONV || reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad N or reactor");
     if (N == 0) return CG_OK;
     if (!T || !C || !J) return fail(CG_EINVAL, "NULL array");
-    cudaError_t e = cg::launch_eval_jacobian(m->dm, m->L, warps_per_block(m->L), reactor, N, T, C, J,
+    cudaError_t e = cg::launch_eval_jacobian(m->dm, m->L, m->tpb, reactor, N, T, C, J,
                                              (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "eval_jacobian launch");
 }
@@ -581,7 +661,8 @@ static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
     if (!o) return fail(CG_EINVAL, "opts is NULL");
     if (o->method < CG_BE || o->method > CG_SDIRK4) return fail(CG_EINVAL, "bad method");
     if (o->reactor < CG_CONV || o->reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad reactor");
-    if (o->precision != CG_FP64) return fail(CG_EUNSUPPORTED, "precision %d not available", o->precision);
+    if (o->precision != CG_FP64 && o->precision != CG_FP32LU)
+        return fail(CG_EINVAL, "bad precision %d", o->precision);
     if (!(o->dt > 0.0) || !std::isfinite(o->dt)) return fail(CG_EINVAL, "dt must be positive");
     if (o->nsub < 1 || o->max_newton < 1 || o->max_steps < 1 || o->max_halvings < 0 || o->max_halvings > 40)
         return fail(CG_EINVAL, "nsub, max_newton, max_steps >= 1 and 0 <= max_halvings <= 40 required");
@@ -598,6 +679,7 @@ static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
     P.max_steps = o->max_steps;
     P.max_halvings = o->max_halvings;
     P.err_filter = o->err_filter;
+    P.precision = o->precision;
     P.dt = o->dt;
     P.rtol = o->rtol;
     P.atol = o->atol;
@@ -626,7 +708,7 @@ cg_status cg_integrate(const cg_mech* m, const cg_integrate_opts* o, int64_t N, 
     if (N < 0) return fail(CG_EINVAL, "N < 0");
     if (N == 0) return CG_OK;
     if (!T || !Y || !p_or_rho) return fail(CG_EINVAL, "NULL array");
-    cudaError_t e = cg::launch_integrate(m->dm, m->L, P, warps_per_block(m->L), N, T, Y, p_or_rho,
+    cudaError_t e = cg::launch_integrate(m->dm, P.precision ? m->L32 : m->L, P, m->tpb, N, T, Y, p_or_rho,
                                          cell_status, cell_stats, (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch");
 }
@@ -663,7 +745,7 @@ cg_status cg_integrate_host(const cg_mech* mc, const cg_integrate_opts* o, int64
         (e = cudaMemcpyAsync(m->wY, Y, N * m->ns * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(m->wP, p_or_rho, N * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync H2D");
-    if ((e = cg::launch_integrate(m->dm, m->L, P, warps_per_block(m->L), N, m->wT, m->wY, m->wP,
+    if ((e = cg::launch_integrate(m->dm, P.precision ? m->L32 : m->L, P, m->tpb, N, m->wT, m->wY, m->wP,
                                   m->wStatus, m->wStats, s)) != cudaSuccess)
         return cuda_fail(e, "integrate launch");
     if ((e = cudaMemcpyAsync(T, m->wT, N * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||

@@ -1,6 +1,7 @@
-// Device side of chemgb: per-cell chemistry and implicit integration, one
-// warp per cell, everything a cell touches during a Newton iteration staged
-// in that warp's slice of shared memory.
+// Device side of chemgb: per-cell chemistry and implicit integration. One
+// team of TEAM threads (a warp, or a whole block of 2-8 warps) owns one cell;
+// everything the cell touches during a Newton iteration is staged in the
+// team's slice of shared memory.
 //
 // Method (arXiv 2510.10005): thermodynamics of Section 2.1 (NASA-7 form,
 // molar, in units of R and R T), rates of Section 2.2 (Arrhenius,
@@ -11,12 +12,15 @@
 // (T, C) independent, Newton on (I - gamma h J) (Section 3.2, Appendix A)
 // and a dense LU with partial pivoting (Section 3.4).
 //
-// GB300 notes that shape the code: FP64 runs at 2 lanes per clock per SM and
-// a warp instruction costs the same whether 1 or 32 lanes are active, so
-// every FP64 loop is flattened across all 32 lanes; omega and J are
-// assembled by host-scheduled rounds in which the 32 lanes add 32 terms into
-// 32 distinct entries (no atomics, deterministic order); reactions are
-// sorted by type so that lanes of a warp take the same branch.
+// GB300 notes that shape the code: each SM sub-partition has its own FP64
+// unit retiring half a lane per clock, and a warp instruction costs the same
+// whatever its active-lane count. So every FP64 loop is flattened across
+// the whole team, a team of two warps keeps two instruction streams per
+// sub-partition, and omega and J are assembled by host-built schedules in
+// which every thread owns a set of destination entries and accumulates their
+// terms in a register (no atomics, no synchronisation, deterministic order);
+// reactions are sorted by type so that neighbouring threads take the same
+// branch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -46,6 +50,7 @@ enum {
 // Reactions are in the library's internal order (sorted by type).
 struct DevMech {
     int ns, nr, n;               // species, reactions, n = ns + 1
+    int team;                    // threads per cell the schedules were built for
     double ln_pref_R;            // ln(p_ref / R)
     const double *th;            // [TH_ROWS][ns]
     const double *W, *invW;      // [ns]
@@ -57,13 +62,13 @@ struct DevMech {
     const int *hasT2;
     const int *eff_ptr, *eff_idx;
     const double *eff_am1;       // alpha - 1
-    // assembly schedules: rounds of 32 (dst, src, factor) terms
-    int w_rounds, v_rounds, j_rounds;
+    // thread-owned assembly schedules: len terms per thread, (dst, src, factor)
+    int w_len, v_len, j_len;
     const int *w_dst, *w_src, *v_dst, *v_src, *j_dst, *j_src;
     const double *w_fac, *v_fac, *j_fac;
 };
 
-// Offsets (in doubles) of the arrays in one warp's shared-memory slice.
+// Offsets (in doubles) of the arrays in one team's shared-memory slice.
 struct Layout {
     int ld;                  // row stride of the n x n matrix (odd)
     int G;                   // n x ld: Newton matrix / LU factors
@@ -73,19 +78,30 @@ struct Layout {
     int yn, Y, base, S, S0, f, err, y1, colA, colB, rinv;   // n each
     int Gam;                 // 5 n: stage derivatives
     int piv;                 // ints, n of them (in ceil(n/2) doubles)
-    int total;               // doubles per warp
+    int red;                 // 24: cross-warp reduction scratch
+    int total;               // doubles per team
 };
 
 // Integration parameters and the Butcher tableau (stage-derivative form).
 struct IntParams {
     int method, reactor, adaptive, nsub, max_newton, max_steps, max_halvings, err_filter;
+    int precision;                  // 0: FP64 Newton matrix, 1: FP32 Newton matrix
     double dt, rtol, atol, newton_tol, h0, hmin, neg_tol;
     int s, err_order, start_zero;   // stages; embedded order; BE starts Newton at y_n
     double A[5][5], b[5], bh[5];
 };
 
 // ---------------------------------------------------------------------------
-// warp helpers
+// team helpers (TEAM = 32: one warp; TEAM > 32: the whole block)
+
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+    if constexpr (TEAM == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <int TEAM>
+__device__ __forceinline__ int team_lane() { return threadIdx.x & (TEAM - 1); }
 
 static __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -93,14 +109,50 @@ static __device__ __forceinline__ double warp_sum(double v) {
     return __shfl_sync(kFull, v, 0);   // one value for every lane
 }
 
-// Walks a rows x ncol row-major index space with stride 32 from `lane`.
+// Sum over the team, the same value in every thread (fixed order).
+template <int TEAM>
+__device__ __forceinline__ double team_sum(double v, double* red) {
+    v = warp_sum(v);
+    if constexpr (TEAM == 32) {
+        return v;
+    } else {
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) red[w] = v;
+        __syncthreads();
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < TEAM / 32; ++k) s += red[k];
+        __syncthreads();
+        return s;
+    }
+}
+
+template <int TEAM>
+__device__ __forceinline__ bool team_any(bool b, double* red) {
+    b = __any_sync(kFull, b);
+    if constexpr (TEAM == 32) {
+        return b;
+    } else {
+        int* ri = reinterpret_cast<int*>(red + 16);
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) ri[w] = b ? 1 : 0;
+        __syncthreads();
+        int r = 0;
+#pragma unroll
+        for (int k = 0; k < TEAM / 32; ++k) r |= ri[k];
+        __syncthreads();
+        return r != 0;
+    }
+}
+
+// Walks a rows x ncol row-major index space with stride S from `lane`.
 struct Flat2D {
     int r, c, dr, dc, ncol;
-    __device__ __forceinline__ Flat2D(int lane, int ncol_) : ncol(ncol_) {
+    __device__ __forceinline__ Flat2D(int lane, int ncol_, int S) : ncol(ncol_) {
         r = lane / ncol;
         c = lane - r * ncol;
-        dr = 32 / ncol;
-        dc = 32 - dr * ncol;
+        dr = S / ncol;
+        dc = S - dr * ncol;
     }
     __device__ __forceinline__ void next() {
         r += dr;
@@ -109,17 +161,75 @@ struct Flat2D {
     }
 };
 
-// out[dst] += fac * in[src], one round of 32 distinct destinations at a time.
-static __device__ __forceinline__ void run_schedule(int rounds, const int* __restrict__ dst,
+// Thread-owned assembly schedule: term t of thread l is at [t * TEAM + l];
+// each thread owns a set of destinations and walks their terms in a fixed
+// order, accumulating in a register; the last term of a destination carries
+// its index (dst >= 0) and flushes out[dst] += acc. Padding terms have fac 0,
+// src 0, dst -1. No two threads share a destination, so no synchronisation
+// is needed inside the walk. `in` is read-only while the schedule runs.
+// The sum is formed in FP64 and added to the destination in its own type.
+template <int TEAM, class OT>
+__device__ __forceinline__ void run_schedule(int len, const int* __restrict__ dst,
                                              const int* __restrict__ src,
-                                             const double* __restrict__ fac, double* out,
+                                             const double* __restrict__ fac, OT* out,
                                              const double* in, int lane) {
-    for (int r = 0; r < rounds; ++r) {
-        const int k = r * 32 + lane;
-        const int d = __ldg(dst + k);
-        if (d >= 0) out[d] = fma(__ldg(fac + k), in[__ldg(src + k)], out[d]);
-        __syncwarp();
+    double acc = 0.0;
+    int t = 0;
+    for (; t + 4 <= len; t += 4) {
+        int d[4], s[4];
+        double f[4], x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = (t + u) * TEAM + lane;
+            d[u] = __ldg(dst + k);
+            s[u] = __ldg(src + k);
+            f[u] = __ldg(fac + k);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = in[s[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            acc = fma(f[u], x[u], acc);
+            if (d[u] >= 0) {
+                out[d[u]] = static_cast<OT>(static_cast<double>(out[d[u]]) + acc);
+                acc = 0.0;
+            }
+        }
     }
+    for (; t < len; ++t) {
+        const int k = t * TEAM + lane;
+        const int d = __ldg(dst + k);
+        acc = fma(__ldg(fac + k), in[__ldg(src + k)], acc);
+        if (d >= 0) {
+            out[d] = static_cast<OT>(static_cast<double>(out[d]) + acc);
+            acc = 0.0;
+        }
+    }
+    team_sync<TEAM>();
+}
+
+// 1/x by two Newton-Raphson steps r <- r + r (1 - x r) (quadratic
+// convergence) from the hardware's approximate single-precision reciprocal
+// of x truncated to 20 mantissa bits; the conversions between the formats
+// are done on the bit patterns. Falls back to division outside the
+// single-precision exponent range. Within 1 ulp of the correctly rounded
+// reciprocal (checked against 1.0/x in the tests).
+static __device__ __forceinline__ double rcp_nr(double x) {
+    const int hi = __double2hiint(x);
+    const int e = ((hi >> 20) & 0x7ff) - 1023;
+    if (e < -125 || e > 125) return 1.0 / x;
+    const int fbits = (hi & 0x80000000) | ((e + 127) << 23) | ((hi & 0xfffff) << 3);
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float(fbits)));
+    const int rb = __float_as_int(rf);
+    const int re = ((rb >> 23) & 0xff) - 127;
+    const int rhi = (rb & 0x80000000) | ((re + 1023) << 20) | ((rb & 0x7fffff) >> 3);
+    const int rlo = (rb & 0x7) << 29;
+    double r = __hiloint2double(rhi, rlo);
+    double t = fma(-x, r, 1.0);
+    r = fma(r, t, r);
+    t = fma(-x, r, 1.0);
+    return fma(r, t, r);
 }
 
 // ---------------------------------------------------------------------------
@@ -127,8 +237,9 @@ static __device__ __forceinline__ void run_schedule(int rounds, const int* __res
 
 // Fills SP (species thermo) and RD (q_j and, with deriv, dq_j/dT, the
 // third-body weight w_j and the mass-action partials). Returns sum C.
-static __device__ double rates(const DevMech& M, const Layout& L, double* sm, const double* y,
-                        bool deriv, int lane) {
+template <int TEAM>
+__device__ double rates(const DevMech& M, const Layout& L, double* sm, const double* y, bool deriv,
+                        int lane) {
     const int ns = M.ns, nr = M.nr;
     const double T = y[0];
     const double* C = y + 1;
@@ -139,7 +250,7 @@ static __device__ double rates(const DevMech& M, const Layout& L, double* sm, co
     double* cpR = gRT + ns;
     double* dcpR = cpR + ns;
     double csum = 0.0;
-    for (int i = lane; i < ns; i += 32) {
+    for (int i = lane; i < ns; i += TEAM) {
         const double* th = M.th + i;
 #define TH(k) __ldg(th + (k) * ns)
         const double cp = TH(TH_A1) + T * (TH(TH_A2) + T * (TH(TH_A3) + T * (TH(TH_A4) + T * TH(TH_A5))));
@@ -155,14 +266,14 @@ static __device__ double rates(const DevMech& M, const Layout& L, double* sm, co
         dcpR[i] = dcp;
         csum += C[i];
     }
-    const double Mc = warp_sum(csum);
-    __syncwarp();
+    const double Mc = team_sum<TEAM>(csum, sm + L.red);
+    team_sync<TEAM>();   // SP visible to the whole team
     const double lnPRT = M.ln_pref_R - lnT;   // ln(p_ref / (R T))
     double* q = sm + L.RD;
     double* dqdT = q + nr;
     double* wv = dqdT + nr;
     double* dd = wv + nr;
-    for (int j = lane; j < nr; j += 32) {
+    for (int j = lane; j < nr; j += TEAM) {
         const int type = __ldg(M.rtype + j);
         const double bj = __ldg(M.beta + j), Taj = __ldg(M.Ta + j);
         const double kA = exp(__ldg(M.lnA + j) + bj * lnT - Taj * invT);
@@ -271,7 +382,7 @@ static __device__ double rates(const DevMech& M, const Layout& L, double* sm, co
             if (sp[5] >= 0) dd[5 * nr + j] = -kr * p[3] * p[4] * dp[5];
         }
     }
-    __syncwarp();
+    team_sync<TEAM>();
     return Mc;
 }
 
@@ -280,21 +391,23 @@ struct SrcInfo {
 };
 
 // S = (omega_T, dC/dt) into sm[L.S..]; y = (T, C).
-static __device__ SrcInfo assemble_source(const DevMech& M, const Layout& L, double* sm, const double* y,
+template <int TEAM>
+__device__ SrcInfo assemble_source(const DevMech& M, const Layout& L, double* sm, const double* y,
                                    int reactor, double Mc, int lane) {
     const int ns = M.ns;
     double* S = sm + L.S;
+    double* red = sm + L.red;
     const double* hRT = sm + L.SP;
     const double* cpR = hRT + 2 * ns;
     const double* dcpR = cpR + ns;
     const double T = y[0];
     const double* C = y + 1;
-    for (int i = lane; i < ns; i += 32) S[1 + i] = 0.0;
-    __syncwarp();
-    run_schedule(M.w_rounds, M.w_dst, M.w_src, M.w_fac, S, sm + L.RD, lane);
+    for (int i = lane; i < ns; i += TEAM) S[1 + i] = 0.0;
+    team_sync<TEAM>();
+    run_schedule<TEAM>(M.w_len, M.w_dst, M.w_src, M.w_fac, S, sm + L.RD, lane);
     const double sub = reactor == R_CONV ? 1.0 : 0.0;   // u/RT = h/RT - 1, c_v/R = c_p/R - 1
     double qe = 0.0, den = 0.0, ws = 0.0, cw = 0.0, cdc = 0.0;
-    for (int i = lane; i < ns; i += 32) {
+    for (int i = lane; i < ns; i += TEAM) {
         const double w = S[1 + i];
         const double c = cpR[i] - sub;
         qe = fma(hRT[i] - sub, w, qe);
@@ -305,29 +418,31 @@ static __device__ SrcInfo assemble_source(const DevMech& M, const Layout& L, dou
     }
     SrcInfo si;
     si.Mc = Mc;
-    const double Qt = warp_sum(qe);
-    si.Dt = warp_sum(den);
-    si.Ws = warp_sum(ws);
-    si.cw = warp_sum(cw);
-    si.cdc = warp_sum(cdc);
+    const double Qt = team_sum<TEAM>(qe, red);
+    si.Dt = team_sum<TEAM>(den, red);
+    si.Ws = team_sum<TEAM>(ws, red);
+    si.cw = team_sum<TEAM>(cw, red);
+    si.cdc = team_sum<TEAM>(cdc, red);
     si.wT = -T * Qt / si.Dt;   // -sum e_i omega_i / (rho c), volumetric c
     si.sdil = 0.0;
     if (reactor == R_CONP) {
         si.sdil = si.wT / T + si.Ws / Mc;
-        for (int i = lane; i < ns; i += 32) S[1 + i] = fma(-C[i], si.sdil, S[1 + i]);
+        for (int i = lane; i < ns; i += TEAM) S[1 + i] = fma(-C[i], si.sdil, S[1 + i]);
     }
     if (lane == 0) S[0] = si.wT;
-    __syncwarp();
+    team_sync<TEAM>();
     return si;
 }
 
 // Analytical Jacobian. With out == nullptr, writes the Newton matrix
-// G = I - gh J into sm[L.G] (row stride L.ld); otherwise writes J to out
-// (row-major n x n, global memory).
-static __device__ void assemble_jacobian(const DevMech& M, const Layout& L, double* sm, const double* y,
+// G = I - gh J into sm[L.G] (row stride L.ld) in the matrix type MT (FP64,
+// or FP32 for the mixed-precision Newton); otherwise writes J to out
+// (row-major n x n, global memory, MT = double).
+template <int TEAM, class MT>
+__device__ void assemble_jacobian(const DevMech& M, const Layout& L, double* sm, const double* y,
                                   int reactor, const SrcInfo& si, double gh, double* out, int lane) {
     const int ns = M.ns, n = M.n, ld = L.ld;
-    double* G = sm + L.G;
+    MT* G = reinterpret_cast<MT*>(sm + L.G);
     double* V = sm + L.V;
     const double* hRT = sm + L.SP;
     const double* cpR = hRT + 2 * ns;
@@ -337,14 +452,14 @@ static __device__ void assemble_jacobian(const DevMech& M, const Layout& L, doub
     const double sub = reactor == R_CONV ? 1.0 : 0.0;
 
     // dense part of d omega / d C from third-body and falloff reactions
-    for (int i = lane; i < ns; i += 32) V[i] = 0.0;
-    __syncwarp();
-    run_schedule(M.v_rounds, M.v_dst, M.v_src, M.v_fac, V, RD, lane);
-    for (Flat2D it(lane, n); it.r < ns; it.next())
-        G[(1 + it.r) * ld + it.c] = it.c == 0 ? 0.0 : V[it.r];
-    __syncwarp();
+    for (int i = lane; i < ns; i += TEAM) V[i] = 0.0;
+    team_sync<TEAM>();
+    run_schedule<TEAM>(M.v_len, M.v_dst, M.v_src, M.v_fac, V, RD, lane);
+    for (Flat2D it(lane, n, TEAM); it.r < ns; it.next())
+        G[(1 + it.r) * ld + it.c] = static_cast<MT>(it.c == 0 ? 0.0 : V[it.r]);
+    team_sync<TEAM>();
     // sparse part, reaction by reaction in a fixed order
-    run_schedule(M.j_rounds, M.j_dst, M.j_src, M.j_fac, G, RD, lane);
+    run_schedule<TEAM>(M.j_len, M.j_dst, M.j_src, M.j_fac, G, RD, lane);
 
     // temperature row: J_T,m = -(T A_m + omega_T c_m) / D (m > 0),
     // J_T,0 = -(sum c_i omega_i + T A_0 + omega_T sum C_i dc_i/dT) / D,
@@ -352,10 +467,10 @@ static __device__ void assemble_jacobian(const DevMech& M, const Layout& L, doub
     double* JT = sm + L.colA;
     double* ds = sm + L.colB;
     const double invD = 1.0 / si.Dt;
-    for (int m = lane; m < n; m += 32) {
+    for (int m = lane; m < n; m += TEAM) {
         double a = 0.0, b = 0.0;
         for (int i = 0; i < ns; ++i) {
-            const double g = G[(1 + i) * ld + m];
+            const double g = static_cast<double>(G[(1 + i) * ld + m]);
             a = fma(hRT[i] - sub, g, a);
             b += g;
         }
@@ -371,38 +486,49 @@ static __device__ void assemble_jacobian(const DevMech& M, const Layout& L, doub
             ds[m] = d;
         }
     }
-    __syncwarp();
+    team_sync<TEAM>();
     const bool conp = reactor == R_CONP;
-    for (Flat2D it(lane, n); it.r < n; it.next()) {
+    for (Flat2D it(lane, n, TEAM); it.r < n; it.next()) {
         const int r = it.r, c = it.c;
         double J;
         if (r == 0) {
             J = JT[c];
         } else {
-            J = G[r * ld + c];
+            J = static_cast<double>(G[r * ld + c]);
             if (conp) {
                 J = fma(-C[r - 1], ds[c], J);
                 if (c == r) J -= si.sdil;
             }
         }
         if (out) out[r * n + c] = J;
-        else G[r * ld + c] = fma(-gh, J, r == c ? 1.0 : 0.0);
+        else G[r * ld + c] = static_cast<MT>(fma(-gh, J, r == c ? 1.0 : 0.0));
     }
-    __syncwarp();
+    team_sync<TEAM>();
 }
 
 // ---------------------------------------------------------------------------
-// dense LU with partial pivoting (Section 3.4), in place, warp-cooperative
+// dense LU with partial pivoting (Section 3.4), in place, team-cooperative
 
-static __device__ bool lu_factor(double* G, int n, int ld, int* piv, double* rinv, int lane) {
+// |x| as an unsigned integer with the order of |x| (non-negative IEEE values
+// order like their bit patterns)
+static __device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+static __device__ __forceinline__ unsigned long long abs_key(float x) {
+    return (unsigned long long)((unsigned)__float_as_int(x) & 0x7fffffffu);
+}
+
+// MT = double: the FP64 factorisation; MT = float: the FP32 factorisation
+// of the mixed-precision Newton (inverse pivots kept in FP64 for the solves).
+template <int TEAM, class MT>
+__device__ bool lu_factor(MT* G, int n, int ld, int* piv, double* rinv, double* red, int lane) {
     for (int k = 0; k < n; ++k) {
         // pivot: largest |G_ik|, i >= k; ties to the lowest row (non-negative
         // doubles order like their bit patterns)
         unsigned long long best = 0ull;
         int bi = n;
-        for (int i = k + lane; i < n; i += 32) {
-            const unsigned long long b =
-                (unsigned long long)__double_as_longlong(G[i * ld + k]) & 0x7fffffffffffffffull;
+        for (int i = k + lane; i < n; i += TEAM) {
+            const unsigned long long b = abs_key(G[i * ld + k]);
             if (bi == n || b > best) { best = b; bi = i; }
         }
 #pragma unroll
@@ -411,66 +537,106 @@ static __device__ bool lu_factor(double* G, int n, int ld, int* piv, double* rin
             const int oi = __shfl_xor_sync(kFull, bi, o);
             if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
         }
+        if constexpr (TEAM > 32) {
+            unsigned long long* rb = reinterpret_cast<unsigned long long*>(red + 8);
+            int* ri = reinterpret_cast<int*>(red + 16);
+            const int w = threadIdx.x >> 5;
+            if ((threadIdx.x & 31) == 0) { rb[w] = best; ri[w] = bi; }
+            __syncthreads();
+            best = rb[0];
+            bi = ri[0];
+#pragma unroll
+            for (int v = 1; v < TEAM / 32; ++v) {
+                const unsigned long long ob = rb[v];
+                const int oi = ri[v];
+                if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+            }
+        }
         if (lane == 0) piv[k] = bi;
-        if (bi != k)
-            for (int j = lane; j < n; j += 32) {
-                const double t = G[k * ld + j];
+        if (bi != k) {
+            for (int j = lane; j < n; j += TEAM) {
+                const MT t = G[k * ld + j];
                 G[k * ld + j] = G[bi * ld + j];
                 G[bi * ld + j] = t;
             }
-        __syncwarp();
-        const double pv = G[k * ld + k];
-        if (pv == 0.0) return false;
-        const double r = 1.0 / pv;
+        }
+        team_sync<TEAM>();
+        const MT pv = G[k * ld + k];
+        if (pv == MT(0)) return false;
+        const double r = rcp_nr(static_cast<double>(pv));
         if (lane == 0) rinv[k] = r;
-        for (int i = k + 1 + lane; i < n; i += 32) G[i * ld + k] *= r;
-        __syncwarp();
+        const MT rm = static_cast<MT>(r);
+        for (int i = k + 1 + lane; i < n; i += TEAM) G[i * ld + k] *= rm;
+        team_sync<TEAM>();
         const int m = n - k - 1;
         if (m > 0) {
             const int k1 = k + 1;
-            for (Flat2D it(lane, m); it.r < m; it.next()) {
-                const int i = k1 + it.r, j = k1 + it.c;
-                G[i * ld + j] = fma(-G[i * ld + k], G[k * ld + j], G[i * ld + j]);
+            const MT* Uk = G + k * ld + k1;   // pivot row, right of the pivot
+            MT* B = G + k1 * ld;              // trailing block, rows k+1 .. n-1
+            Flat2D it(lane, m, TEAM);
+            while (it.r < m) {   // four elements per thread per pass, loads first
+                int o[4], c[4];
+                bool v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    v[u] = it.r < m;
+                    o[u] = v[u] ? it.r * ld : 0;
+                    c[u] = v[u] ? it.c : 0;
+                    it.next();
+                }
+                MT l[4], uu[4], a[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    l[u] = B[o[u] + k];
+                    uu[u] = Uk[c[u]];
+                    a[u] = B[o[u] + c[u] + k1];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (v[u]) B[o[u] + c[u] + k1] = fma(-l[u], uu[u], a[u]);
             }
         }
-        __syncwarp();
+        team_sync<TEAM>();
     }
     return true;
 }
 
-// x <- G^{-1} x with the factors of lu_factor.
-static __device__ void lu_solve(const double* G, int n, int ld, const int* piv, const double* rinv,
+// x <- G^{-1} x with the factors of lu_factor (FP64 arithmetic on x).
+template <int TEAM, class MT>
+__device__ void lu_solve(const MT* G, int n, int ld, const int* piv, const double* rinv,
                          double* x, int lane) {
     if (lane == 0)
         for (int k = 0; k < n; ++k) {
             const int p = piv[k];
             if (p != k) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
         }
-    __syncwarp();
+    team_sync<TEAM>();
     for (int j = 0; j < n - 1; ++j) {           // unit lower triangle, by columns
         const double xj = x[j];
-        for (int i = j + 1 + lane; i < n; i += 32) x[i] = fma(-G[i * ld + j], xj, x[i]);
-        __syncwarp();
+        for (int i = j + 1 + lane; i < n; i += TEAM)
+            x[i] = fma(-static_cast<double>(G[i * ld + j]), xj, x[i]);
+        team_sync<TEAM>();
     }
     for (int j = n - 1; j >= 0; --j) {          // upper triangle, by columns
         const double xj = x[j] * rinv[j];
-        __syncwarp();
+        team_sync<TEAM>();
         if (lane == 0) x[j] = xj;
-        for (int i = lane; i < j; i += 32) x[i] = fma(-G[i * ld + j], xj, x[i]);
-        __syncwarp();
+        for (int i = lane; i < j; i += TEAM) x[i] = fma(-static_cast<double>(G[i * ld + j]), xj, x[i]);
+        team_sync<TEAM>();
     }
 }
 
 // weighted RMS norm with w_i = atol + rtol max(|a_i|, |b_i|)
-static __device__ __forceinline__ double wrms(const double* v, const double* a, const double* b, int n,
-                                       double rtol, double atol, int lane) {
+template <int TEAM>
+__device__ __forceinline__ double wrms(const double* v, const double* a, const double* b, int n,
+                                       double rtol, double atol, double* red, int lane) {
     double s = 0.0;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = lane; i < n; i += TEAM) {
         const double w = atol + rtol * fmax(fabs(a[i]), fabs(b[i]));
         const double r = v[i] / w;
         s = fma(r, r, s);
     }
-    return sqrt(warp_sum(s) / n);
+    return sqrt(team_sum<TEAM>(s, red) / n);
 }
 
 }  // namespace cg

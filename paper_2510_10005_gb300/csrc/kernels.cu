@@ -1,4 +1,5 @@
-// Kernels of chemgb: one warp per cell.
+// Kernels of chemgb: one team of TEAM threads per cell (TEAM = 32: one warp,
+// several teams per block; TEAM = 64..256: one team per block).
 //
 //   eval_rates_kernel      S(y) for N cells (Section 2.2, Section 3, App. B)
 //   eval_jacobian_kernel   dS/dy for N cells (Section 3.2)
@@ -11,48 +12,57 @@ namespace cg {
 
 constexpr double kR = 8314.46261815324;   // J/(kmol K)
 
-__device__ __forceinline__ double* warp_smem(const Layout& L) {
+template <int TEAM>
+__device__ __forceinline__ double* team_smem(const Layout& L) {
     extern __shared__ double smem_all[];
-    return smem_all + (size_t)(threadIdx.x >> 5) * L.total;
+    return smem_all + (size_t)(threadIdx.x / TEAM) * L.total;
+}
+
+template <int TEAM>
+__device__ __forceinline__ int64_t team_cell() {
+    return (int64_t)blockIdx.x * (blockDim.x / TEAM) + threadIdx.x / TEAM;
 }
 
 // ---------------------------------------------------------------------------
 
+template <int TEAM>
 __global__ void eval_rates_kernel(DevMech M, Layout L, int reactor, int64_t N,
                                   const double* __restrict__ T, const double* __restrict__ C,
                                   double* __restrict__ S) {
-    const int lane = threadIdx.x & 31;
-    const int64_t cell = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (cell >= N) return;
-    double* sm = warp_smem(L);
+    const int lane = team_lane<TEAM>();
+    const int64_t cell = team_cell<TEAM>();
+    if (cell >= N) return;   // whole team (a team never straddles this bound)
+    double* sm = team_smem<TEAM>(L);
     double* y = sm + L.Y;
     if (lane == 0) y[0] = T[cell];
-    for (int i = lane; i < M.ns; i += 32) y[1 + i] = C[(int64_t)i * N + cell];
-    __syncwarp();
-    const double Mc = rates(M, L, sm, y, false, lane);
-    assemble_source(M, L, sm, y, reactor, Mc, lane);
+    for (int i = lane; i < M.ns; i += TEAM) y[1 + i] = C[(int64_t)i * N + cell];
+    team_sync<TEAM>();
+    const double Mc = rates<TEAM>(M, L, sm, y, false, lane);
+    assemble_source<TEAM>(M, L, sm, y, reactor, Mc, lane);
     const double* Sv = sm + L.S;
-    for (int i = lane; i < M.n; i += 32) S[(int64_t)i * N + cell] = Sv[i];
+    for (int i = lane; i < M.n; i += TEAM) S[(int64_t)i * N + cell] = Sv[i];
 }
 
+template <int TEAM>
 __global__ void eval_jacobian_kernel(DevMech M, Layout L, int reactor, int64_t N,
                                      const double* __restrict__ T, const double* __restrict__ C,
                                      double* __restrict__ J) {
-    const int lane = threadIdx.x & 31;
-    const int64_t cell = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = team_lane<TEAM>();
+    const int64_t cell = team_cell<TEAM>();
     if (cell >= N) return;
-    double* sm = warp_smem(L);
+    double* sm = team_smem<TEAM>(L);
     double* y = sm + L.Y;
     if (lane == 0) y[0] = T[cell];
-    for (int i = lane; i < M.ns; i += 32) y[1 + i] = C[(int64_t)i * N + cell];
-    __syncwarp();
-    const double Mc = rates(M, L, sm, y, true, lane);
-    const SrcInfo si = assemble_source(M, L, sm, y, reactor, Mc, lane);
-    assemble_jacobian(M, L, sm, y, reactor, si, 0.0, J + cell * (int64_t)M.n * M.n, lane);
+    for (int i = lane; i < M.ns; i += TEAM) y[1 + i] = C[(int64_t)i * N + cell];
+    team_sync<TEAM>();
+    const double Mc = rates<TEAM>(M, L, sm, y, true, lane);
+    const SrcInfo si = assemble_source<TEAM>(M, L, sm, y, reactor, Mc, lane);
+    assemble_jacobian<TEAM, double>(M, L, sm, y, reactor, si, 0.0, J + cell * (int64_t)M.n * M.n, lane);
 }
 
 // Newton on sum_i Y_i e_i(T) = e, e = u (constant volume) or h (otherwise),
 // molar e_i = R T h/RT (minus R T for u), mass-specific = molar / W_i.
+// One warp per cell.
 __global__ void temperature_kernel(DevMech M, int reactor, int64_t N, const double* __restrict__ e,
                                    const double* __restrict__ Y, double* __restrict__ Tio,
                                    int iters) {
@@ -94,6 +104,9 @@ struct Counters {
 // One step of size h from sm[yn]: stages of the tableau in stage-derivative
 // form (Appendix A), each by full Newton with G = I - a_pp h J(Y_p). On
 // success y1 holds the new state and err the (filtered) embedded estimate.
+// MT = float: G is assembled and factored in FP32 (an inexact Newton whose
+// residual, update and convergence test stay in FP64).
+template <int TEAM, class MT>
 __device__ bool rk_step(const DevMech& M, const Layout& L, const IntParams& P, double* sm, double h,
                         Counters& cnt, int lane) {
     const int n = M.n;
@@ -103,46 +116,47 @@ __device__ bool rk_step(const DevMech& M, const Layout& L, const IntParams& P, d
     double* S = sm + L.S;
     double* S0 = sm + L.S0;
     double* f = sm + L.f;
-    double* G = sm + L.G;
+    MT* G = reinterpret_cast<MT*>(sm + L.G);
     double* rinv = sm + L.rinv;
+    double* red = sm + L.red;
     int* piv = reinterpret_cast<int*>(sm + L.piv);
     if (!P.start_zero) {   // first Newton iterate of every stage: Gamma = S(y_n)
-        const double Mc = rates(M, L, sm, yn, false, lane);
-        assemble_source(M, L, sm, yn, P.reactor, Mc, lane);
-        for (int i = lane; i < n; i += 32) S0[i] = S[i];
-        __syncwarp();
+        const double Mc = rates<TEAM>(M, L, sm, yn, false, lane);
+        assemble_source<TEAM>(M, L, sm, yn, P.reactor, Mc, lane);
+        for (int i = lane; i < n; i += TEAM) S0[i] = S[i];
+        team_sync<TEAM>();
     }
     for (int p = 0; p < P.s; ++p) {
         const double gh = P.A[p][p] * h;
         double* Gp = sm + L.Gam + p * n;
-        for (int i = lane; i < n; i += 32) {
+        for (int i = lane; i < n; i += TEAM) {
             double b = yn[i];
             for (int j = 0; j < p; ++j) b = fma(h * P.A[p][j], sm[L.Gam + j * n + i], b);
             base[i] = b;
             Gp[i] = P.start_zero ? 0.0 : S0[i];
         }
-        __syncwarp();
+        team_sync<TEAM>();
         bool conv = false;
         for (int k = 0; k < P.max_newton; ++k) {
-            for (int i = lane; i < n; i += 32) Y[i] = fma(gh, Gp[i], base[i]);
-            __syncwarp();
-            const double Mc = rates(M, L, sm, Y, true, lane);
-            const SrcInfo si = assemble_source(M, L, sm, Y, P.reactor, Mc, lane);
-            assemble_jacobian(M, L, sm, Y, P.reactor, si, gh, nullptr, lane);
-            for (int i = lane; i < n; i += 32) f[i] = S[i] - Gp[i];   // -f(Gamma)
-            __syncwarp();
+            for (int i = lane; i < n; i += TEAM) Y[i] = fma(gh, Gp[i], base[i]);
+            team_sync<TEAM>();
+            const double Mc = rates<TEAM>(M, L, sm, Y, true, lane);
+            const SrcInfo si = assemble_source<TEAM>(M, L, sm, Y, P.reactor, Mc, lane);
+            assemble_jacobian<TEAM, MT>(M, L, sm, Y, P.reactor, si, gh, nullptr, lane);
+            for (int i = lane; i < n; i += TEAM) f[i] = S[i] - Gp[i];   // -f(Gamma)
+            team_sync<TEAM>();
             cnt.newton++;
             cnt.lu++;
-            if (!lu_factor(G, n, L.ld, piv, rinv, lane)) return false;
-            lu_solve(G, n, L.ld, piv, rinv, f, lane);
-            for (int i = lane; i < n; i += 32) {
+            if (!lu_factor<TEAM, MT>(G, n, L.ld, piv, rinv, red, lane)) return false;
+            lu_solve<TEAM, MT>(G, n, L.ld, piv, rinv, f, lane);
+            for (int i = lane; i < n; i += TEAM) {
                 const double g = Gp[i] + f[i];
                 Gp[i] = g;
                 f[i] *= gh;                  // change of the stage state
                 Y[i] = fma(gh, g, base[i]);
             }
-            __syncwarp();
-            const double nrm = wrms(f, yn, Y, n, P.rtol, P.atol, lane);
+            team_sync<TEAM>();
+            const double nrm = wrms<TEAM>(f, yn, Y, n, P.rtol, P.atol, red, lane);
             if (!isfinite(nrm)) return false;
             if (nrm <= P.newton_tol) { conv = true; break; }
         }
@@ -151,7 +165,7 @@ __device__ bool rk_step(const DevMech& M, const Layout& L, const IntParams& P, d
     double* y1 = sm + L.y1;
     double* err = sm + L.err;
     bool bad = false;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = lane; i < n; i += TEAM) {
         double v = yn[i], e = 0.0;
         for (int p = 0; p < P.s; ++p) {
             const double g = sm[L.Gam + p * n + i];
@@ -162,27 +176,29 @@ __device__ bool rk_step(const DevMech& M, const Layout& L, const IntParams& P, d
         err[i] = e;
         bad |= !isfinite(v);
     }
-    __syncwarp();
-    if (__any_sync(kFull, bad)) return false;
-    if (P.adaptive && P.err_filter) lu_solve(G, n, L.ld, piv, rinv, err, lane);
+    team_sync<TEAM>();
+    if (team_any<TEAM>(bad, red)) return false;
+    if (P.adaptive && P.err_filter) lu_solve<TEAM, MT>(G, n, L.ld, piv, rinv, err, lane);
     // admissible: T > 0 and C_i >= -neg_tol sum C
     double cs = 0.0;
-    for (int i = 1 + lane; i < n; i += 32) cs += y1[i];
-    cs = warp_sum(cs);
+    for (int i = 1 + lane; i < n; i += TEAM) cs += y1[i];
+    cs = team_sum<TEAM>(cs, red);
     bool neg = false;
-    for (int i = 1 + lane; i < n; i += 32) neg |= y1[i] < -P.neg_tol * cs;
-    neg = __any_sync(kFull, neg) || !(y1[0] > 0.0);
+    for (int i = 1 + lane; i < n; i += TEAM) neg |= y1[i] < -P.neg_tol * cs;
+    neg = team_any<TEAM>(neg, red) || !(y1[0] > 0.0);
     return !neg;
 }
 
+template <int TEAM>
 __device__ __forceinline__ void copy_vec(double* dst, const double* src, int n, int lane) {
-    for (int i = lane; i < n; i += 32) dst[i] = src[i];
-    __syncwarp();
+    for (int i = lane; i < n; i += TEAM) dst[i] = src[i];
+    team_sync<TEAM>();
 }
 
 // Fixed steps with deterministic halving: a failed step of level d is
 // replaced by two steps of level d+1 (recursively, at most max_halvings
 // deep), walked iteratively with a position counter.
+template <int TEAM, class MT>
 __device__ int integrate_fixed(const DevMech& M, const Layout& L, const IntParams& P, double* sm,
                                Counters& cnt, int lane) {
     const int D = P.max_halvings;
@@ -193,8 +209,8 @@ __device__ int integrate_fixed(const DevMech& M, const Layout& L, const IntParam
         int d = 0;
         while (pos < total) {
             const double h = ldexp(hsub, -d);
-            if (rk_step(M, L, P, sm, h, cnt, lane)) {
-                copy_vec(sm + L.yn, sm + L.y1, M.n, lane);
+            if (rk_step<TEAM, MT>(M, L, P, sm, h, cnt, lane)) {
+                copy_vec<TEAM>(sm + L.yn, sm + L.y1, M.n, lane);
                 cnt.steps++;
                 pos += 1ull << (D - d);
                 while (d > 0 && ((pos >> (D - d)) & 1ull) == 0ull) --d;
@@ -210,6 +226,7 @@ __device__ int integrate_fixed(const DevMech& M, const Layout& L, const IntParam
 
 // Error-controlled steps: accept when WRMS(err) <= 1; next step
 // h min(5, max(0.2, 0.9 err^(-1/(q+1)))); Newton failure: h / 4.
+template <int TEAM, class MT>
 __device__ int integrate_adaptive(const DevMech& M, const Layout& L, const IntParams& P, double* sm,
                                   Counters& cnt, int lane) {
     const double expo = -1.0 / (P.err_order + 1.0);
@@ -221,16 +238,16 @@ __device__ int integrate_adaptive(const DevMech& M, const Layout& L, const IntPa
         if (h < P.hmin) return CELL_STEP_TOO_SMALL;
         const bool last = t + h >= P.dt;
         const double hh = last ? P.dt - t : h;
-        if (!rk_step(M, L, P, sm, hh, cnt, lane)) {
+        if (!rk_step<TEAM, MT>(M, L, P, sm, hh, cnt, lane)) {
             cnt.rejects++;
             h = 0.25 * hh;
             continue;
         }
-        const double e = wrms(sm + L.err, sm + L.yn, sm + L.y1, M.n, P.rtol, P.atol, lane);
+        const double e = wrms<TEAM>(sm + L.err, sm + L.yn, sm + L.y1, M.n, P.rtol, P.atol, sm + L.red, lane);
         double fac = e > 0.0 ? 0.9 * pow(e, expo) : 5.0;
         fac = fmin(5.0, fmax(0.2, fac));
         if (e <= 1.0) {
-            copy_vec(sm + L.yn, sm + L.y1, M.n, lane);
+            copy_vec<TEAM>(sm + L.yn, sm + L.y1, M.n, lane);
             t = last ? P.dt : t + hh;
             cnt.steps++;
         } else {
@@ -241,52 +258,54 @@ __device__ int integrate_adaptive(const DevMech& M, const Layout& L, const IntPa
     return CELL_OK;
 }
 
+template <int TEAM, class MT>
 __global__ void integrate_kernel(DevMech M, Layout L, IntParams P, int64_t N, double* __restrict__ T,
                                  double* __restrict__ Yio, const double* __restrict__ p_or_rho,
                                  int32_t* __restrict__ status, int32_t* __restrict__ stats) {
-    const int lane = threadIdx.x & 31;
-    const int64_t cell = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = team_lane<TEAM>();
+    const int64_t cell = team_cell<TEAM>();
     if (cell >= N) return;
     const int ns = M.ns, n = M.n;
-    double* sm = warp_smem(L);
+    double* sm = team_smem<TEAM>(L);
     double* yn = sm + L.yn;
+    double* red = sm + L.red;
     // load and unpack: C_i = rho Y_i / W_i
     const double T0 = T[cell];
     const double pr = p_or_rho[cell];
     double ysum = 0.0;
-    for (int i = lane; i < ns; i += 32) {
+    for (int i = lane; i < ns; i += TEAM) {
         const double Yi = Yio[(int64_t)i * N + cell];
         yn[1 + i] = Yi;
         ysum = fma(Yi, __ldg(M.invW + i), ysum);
     }
-    ysum = warp_sum(ysum);
+    ysum = team_sum<TEAM>(ysum, red);
     const double rho = P.reactor == R_CONV ? pr : pr / (kR * T0 * ysum);
     bool fin = isfinite(T0);
-    for (int i = lane; i < ns; i += 32) {
+    for (int i = lane; i < ns; i += TEAM) {
         const double c = rho * yn[1 + i] * __ldg(M.invW + i);
         yn[1 + i] = c;
         fin &= isfinite(c);
     }
     if (lane == 0) yn[0] = T0;
-    __syncwarp();
-    fin = __all_sync(kFull, fin);
+    team_sync<TEAM>();
+    fin = !team_any<TEAM>(!fin, red);
     Counters cnt = {0, 0, 0, 0};
     int st;
     if (!fin) {
         st = CELL_NONFINITE;
     } else {
-        st = P.adaptive ? integrate_adaptive(M, L, P, sm, cnt, lane)
-                        : integrate_fixed(M, L, P, sm, cnt, lane);
-        bool f2 = true;
-        for (int i = lane; i < n; i += 32) f2 &= isfinite(yn[i]);
-        if (st == CELL_OK && !__all_sync(kFull, f2)) st = CELL_NONFINITE;
+        st = P.adaptive ? integrate_adaptive<TEAM, MT>(M, L, P, sm, cnt, lane)
+                        : integrate_fixed<TEAM, MT>(M, L, P, sm, cnt, lane);
+        bool bad = false;
+        for (int i = lane; i < n; i += TEAM) bad |= !isfinite(yn[i]);
+        if (team_any<TEAM>(bad, red) && st == CELL_OK) st = CELL_NONFINITE;
     }
     // store: T, Y_i = W_i C_i / sum W_j C_j (the input is kept for non-finite cells)
     if (st != CELL_NONFINITE) {
         double ms = 0.0;
-        for (int i = lane; i < ns; i += 32) ms = fma(__ldg(M.W + i), yn[1 + i], ms);
-        const double inv = 1.0 / warp_sum(ms);
-        for (int i = lane; i < ns; i += 32) Yio[(int64_t)i * N + cell] = __ldg(M.W + i) * yn[1 + i] * inv;
+        for (int i = lane; i < ns; i += TEAM) ms = fma(__ldg(M.W + i), yn[1 + i], ms);
+        const double inv = 1.0 / team_sum<TEAM>(ms, red);
+        for (int i = lane; i < ns; i += TEAM) Yio[(int64_t)i * N + cell] = __ldg(M.W + i) * yn[1 + i] * inv;
         if (lane == 0) T[cell] = yn[0];
     }
     if (lane == 0) {
@@ -301,7 +320,7 @@ __global__ void integrate_kernel(DevMech M, Layout L, IntParams P, int64_t N, do
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// launchers: teams_per_block teams of TEAM threads (TEAM > 32: one per block)
 
 static cudaError_t prepare(const void* fn, size_t smem) {
     if (smem > 48 * 1024)
@@ -309,24 +328,40 @@ static cudaError_t prepare(const void* fn, size_t smem) {
     return cudaSuccess;
 }
 
-cudaError_t launch_eval_rates(const DevMech& M, const Layout& L, int wpb, int reactor, int64_t N,
-                              const double* T, const double* C, double* S, cudaStream_t st) {
-    const size_t smem = (size_t)wpb * L.total * sizeof(double);
-    cudaError_t e = prepare((const void*)eval_rates_kernel, smem);
+template <int TEAM, class K, class... Args>
+static cudaError_t launch_team(K kernel, const Layout& L, int tpb, int64_t N, cudaStream_t st,
+                               Args... args) {
+    if (TEAM > 32) tpb = 1;
+    const size_t smem = (size_t)tpb * L.total * sizeof(double);
+    cudaError_t e = prepare((const void*)kernel, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (N + wpb - 1) / wpb;
-    eval_rates_kernel<<<(unsigned)blocks, 32 * wpb, smem, st>>>(M, L, reactor, N, T, C, S);
+    const int64_t blocks = (N + tpb - 1) / tpb;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    kernel<<<(unsigned)blocks, TEAM * tpb, smem, st>>>(args...);
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval_jacobian(const DevMech& M, const Layout& L, int wpb, int reactor, int64_t N,
+#define CG_DISPATCH_TEAM(team, CALL)                         \
+    switch (team) {                                          \
+        case 32: return CALL(32);                            \
+        case 64: return CALL(64);                            \
+        case 128: return CALL(128);                          \
+        case 256: return CALL(256);                          \
+        default: return cudaErrorInvalidValue;               \
+    }
+
+cudaError_t launch_eval_rates(const DevMech& M, const Layout& L, int tpb, int reactor, int64_t N,
+                              const double* T, const double* C, double* S, cudaStream_t st) {
+#define CALL(TM) launch_team<TM>(eval_rates_kernel<TM>, L, tpb, N, st, M, L, reactor, N, T, C, S)
+    CG_DISPATCH_TEAM(M.team, CALL)
+#undef CALL
+}
+
+cudaError_t launch_eval_jacobian(const DevMech& M, const Layout& L, int tpb, int reactor, int64_t N,
                                  const double* T, const double* C, double* J, cudaStream_t st) {
-    const size_t smem = (size_t)wpb * L.total * sizeof(double);
-    cudaError_t e = prepare((const void*)eval_jacobian_kernel, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = (N + wpb - 1) / wpb;
-    eval_jacobian_kernel<<<(unsigned)blocks, 32 * wpb, smem, st>>>(M, L, reactor, N, T, C, J);
-    return cudaGetLastError();
+#define CALL(TM) launch_team<TM>(eval_jacobian_kernel<TM>, L, tpb, N, st, M, L, reactor, N, T, C, J)
+    CG_DISPATCH_TEAM(M.team, CALL)
+#undef CALL
 }
 
 cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const double* e,
@@ -337,16 +372,19 @@ cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const d
     return cudaGetLastError();
 }
 
-cudaError_t launch_integrate(const DevMech& M, const Layout& L, const IntParams& P, int wpb,
+cudaError_t launch_integrate(const DevMech& M, const Layout& L, const IntParams& P, int tpb,
                              int64_t N, double* T, double* Y, const double* p_or_rho,
                              int32_t* status, int32_t* stats, cudaStream_t st) {
-    const size_t smem = (size_t)wpb * L.total * sizeof(double);
-    cudaError_t e = prepare((const void*)integrate_kernel, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = (N + wpb - 1) / wpb;
-    integrate_kernel<<<(unsigned)blocks, 32 * wpb, smem, st>>>(M, L, P, N, T, Y, p_or_rho, status,
-                                                              stats);
-    return cudaGetLastError();
+    if (P.precision == 1) {
+#define CALL(TM) \
+    launch_team<TM>(integrate_kernel<TM, float>, L, tpb, N, st, M, L, P, N, T, Y, p_or_rho, status, stats)
+        CG_DISPATCH_TEAM(M.team, CALL)
+#undef CALL
+    }
+#define CALL(TM) \
+    launch_team<TM>(integrate_kernel<TM, double>, L, tpb, N, st, M, L, P, N, T, Y, p_or_rho, status, stats)
+    CG_DISPATCH_TEAM(M.team, CALL)
+#undef CALL
 }
 
 }  // namespace cg

@@ -205,6 +205,32 @@ def test_edge_cases(mechs, ref, handles):
         assert np.all(sg == want) and np.all(so == want)
 
 
+@pytest.mark.parametrize("kind,shapes", [("h2", [(32, 1), (32, 4), (64, 1)]),
+                                         ("ch4", [(64, 1), (32, 1), (128, 1), (256, 1)])])
+def test_launch_shapes_agree(mechs, kind, shapes):
+    """Every team size / cells-per-block gives the same integration up to the
+    summation order of team-wide reductions."""
+    m = mechs[kind]
+    h = chemgb.cg_mech_create(m)
+    if kind == "h2":
+        T, Y, p = inputs.field_reactor(m, 77, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=12)
+        o = chemgb.make_opts(**BE_OPTS)
+    else:
+        T, Y, p = inputs.field_flames(m, 4096, seed=2)
+        idx = np.arange(2400, 2400 + 67)   # front cells: many steps
+        T, Y, p = T[idx], Y[idx], p[idx]
+        o = chemgb.make_opts(**ADAPT)
+    res = []
+    for team, tpb in shapes:
+        chemgb.cg_mech_set_launch(h, team, tpb)
+        assert chemgb.cg_mech_get_launch(h) == (team, tpb)
+        res.append(run_gpu(h, o, T, Y, p))
+    for Tg, Yg, sg, _ in res[1:]:
+        np.testing.assert_array_equal(sg, res[0][2])
+        np.testing.assert_allclose(Tg, res[0][0], rtol=1e-9)
+        assert np.max(np.abs(Yg - res[0][1])) < 1e-9
+
+
 def test_host_entry_point_matches_device(mechs, handles):
     m, h = mechs["h2"], handles["h2"]
     T, Y, p = inputs.field_reactor(m, 513, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=9)
@@ -218,3 +244,47 @@ def test_host_entry_point_matches_device(mechs, handles):
     np.testing.assert_array_equal(Yh.T, Yg)
     np.testing.assert_array_equal(sh, sg)
     np.testing.assert_array_equal(sth.T, stg)
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP32 Newton matrix and LU, FP64 residual/rates/updates
+
+
+def test_mixed_precision_backward_euler(mechs, ref, handles):
+    """The inexact Newton with an FP32 LU converges to the FP64 root: with the
+    Newton change required below 1e-10 of the state, T and Y agree with the
+    FP64 oracle to 1e-8 relative. Steps of 1e-6 s: at 1e-5 s across ignition
+    the backward-Euler equations have several admissible roots, and which one
+    a Newton iteration reaches depends on its first iterates (both the exact
+    and the inexact iteration are correct there)."""
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 1024, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=0)
+    o = dict(BE_OPTS, dt=1e-6)
+    To, Yo, so, sto = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**o, precision=chemgb.CG_FP32LU), T, Y, p)
+    assert np.all(sg == 0) and np.all(so == 0)
+    same = np.all(stg[:, :2] == sto[:, :2], axis=1)
+    assert same.mean() > 0.99
+    assert_state_close(Tg[same], Yg[same], To[same], Yo[same], 1e-8, 1e-18)
+
+
+def test_mixed_precision_fixed_sdirk4(mechs, ref, handles):
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 67, (1100, 1400), (1, 1), (0.5, 2), "H2", seed=3)
+    o = dict(BE_OPTS, method=chemgb.CG_SDIRK4, dt=2e-6, nsub=4)
+    To, Yo, so, _ = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, _ = run_gpu(h, chemgb.make_opts(**o, precision=chemgb.CG_FP32LU), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    assert_state_close(Tg, Yg, To, Yo, 1e-8, 1e-18)
+
+
+def test_mixed_precision_adaptive_flame(mechs, ref, handles):
+    m, r, h = mechs["ch4"], ref["ch4"], handles["ch4"]
+    T, Y, p = inputs.field_flames(m, 4096, seed=0)
+    idx = np.arange(0, 4096, 32)
+    To, Yo, so, _ = r.integrate(T[idx], Y[idx], p[idx], ADAPT, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**ADAPT, precision=chemgb.CG_FP32LU),
+                              T[idx], Y[idx], p[idx])
+    np.testing.assert_array_equal(sg, so)
+    np.testing.assert_allclose(Tg, To, rtol=1e-6)
+    assert np.max(np.abs(Yg - Yo)) < 1e-6

@@ -122,6 +122,16 @@ int cg_mech_n_reactions(const cg_mech *mech);
  * (bad shape), CG_ECAPACITY (shared memory), CG_ENOMEM, CG_ECUDA. This is
  * a launch-tuning hook, not part of the method of the paper. */
 cg_status cg_mech_set_launch(cg_mech *mech, int team, int teams_per_block);
+/* Shared memory a cell may use (bytes, 1 KiB .. 227 KiB; default 227 KiB).
+ * A cell's arrays are placed hottest first (Newton matrix, state vectors,
+ * thermo, stage derivatives, per-reaction data); those beyond the limit go
+ * to a per-team slot of global scratch that the library allocates
+ * stream-ordered for each launch (mechanisms whose Newton matrix alone
+ * nears the limit, such as 160 species in FP64, always spill). A lower
+ * limit trades L2 traffic for more cells per SM. Same concurrency rule as
+ * cg_mech_set_launch. Launch tuning, not part of the paper's method. */
+cg_status cg_mech_set_smem_limit(cg_mech *mech, int64_t bytes);
+
 /* Current launch shape; returns 0, or -1 for a NULL mechanism. */
 int cg_mech_get_launch(const cg_mech *mech, int *team, int *teams_per_block);
 
@@ -158,7 +168,9 @@ typedef struct {
     int max_steps;     /* adaptive: step attempts before CG_CELL_MAX_STEPS            */
     int max_halvings;  /* fixed mode: depth of step halving after a failed step       */
     int err_filter;    /* adaptive: filter the error estimate by (I - gamma h J)^-1   */
-    int reserved;
+    int persistent;    /* 1: resident grid whose teams take cells from a shared work
+                          counter (work stealing; always used when a cell's arrays
+                          spill to global scratch); 0: one launch slot per cell    */
     double dt;         /* integration interval, s                                     */
     double rtol, atol; /* weights w_i = atol + rtol max(|y_n,i|, |y_i|)               */
     double newton_tol; /* Newton converged when WRMS(change of stage state) <= this   */
@@ -181,6 +193,20 @@ void cg_integrate_opts_default(cg_integrate_opts *opts);
 cg_status cg_integrate(const cg_mech *mech, const cg_integrate_opts *opts, int64_t N, double *T,
                        double *Y, const double *p_or_rho, int32_t *cell_status,
                        int32_t *cell_stats, void *stream);
+
+/* Integrate the cells of up to 4 mechanisms in ONE persistent launch: the
+ * cells of all mechanisms form one index space (mechanism 0 first) from
+ * which resident teams take cells through a shared work counter, so cheap
+ * and expensive cells of either mechanism balance across the GPU. Array
+ * k-th entries are those of cg_integrate for mechanism k (cell_status and
+ * cell_stats may be NULL, or hold NULL entries). All mechanisms must use the
+ * same team size (cg_mech_set_launch); the same options apply to all.
+ * Allocates its work counter and any global scratch stream-ordered
+ * (cudaMallocAsync) and releases them on the same stream. */
+cg_status cg_integrate_batch(int n_mech, const cg_mech *const *mechs, const int64_t *N,
+                             double *const *T, double *const *Y, const double *const *p_or_rho,
+                             int32_t *const *cell_status, int32_t *const *cell_stats,
+                             const cg_integrate_opts *opts, void *stream);
 
 /* Same as cg_integrate with HOST arrays: copies the inputs to device memory
  * owned by the mechanism (grown on demand, freed with it), integrates,

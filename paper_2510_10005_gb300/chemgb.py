@@ -41,14 +41,15 @@ class cg_mech_desc(ctypes.Structure):
 class cg_integrate_opts(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in (
         "method", "reactor", "adaptive", "precision", "nsub", "max_newton", "max_steps",
-        "max_halvings", "err_filter", "reserved")] + [(k, ctypes.c_double) for k in (
+        "max_halvings", "err_filter", "persistent")] + [(k, ctypes.c_double) for k in (
             "dt", "rtol", "atol", "newton_tol", "h0", "hmin", "neg_tol")]
 
 
 EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n_reactions",
-            "cg_mech_set_launch", "cg_mech_get_launch",
+            "cg_mech_set_launch", "cg_mech_get_launch", "cg_mech_set_smem_limit",
             "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
-            "cg_integrate_opts_default", "cg_integrate", "cg_integrate_host", "cg_last_error")
+            "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
+            "cg_last_error")
 
 
 def library_path() -> str:
@@ -74,6 +75,8 @@ def load(build_if_missing: bool = False):
     lib.cg_mech_n_reactions.argtypes = [P]
     lib.cg_mech_set_launch.argtypes = [P, I, I]
     lib.cg_mech_get_launch.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.cg_mech_set_smem_limit.argtypes = [P, L]
+    lib.cg_integrate_batch.argtypes = [I, P, P, P, P, P, P, P, ctypes.POINTER(cg_integrate_opts), P]
     lib.cg_eval_rates.argtypes = [P, I, L, P, P, P, P]
     lib.cg_eval_jacobian.argtypes = [P, I, L, P, P, P, P]
     lib.cg_temperature_from_energy.argtypes = [P, I, L, P, P, P, I, P]
@@ -174,6 +177,24 @@ def cg_integrate(h, opts, T, Y, p_or_rho, status=None, stats=None, stream=None):
     _check(load().cg_integrate(h.ptr, ctypes.byref(opts), T.shape[0], _dev(T), _dev(Y), _dev(p_or_rho),
                                None if status is None else _dev(status, "int32"),
                                None if stats is None else _dev(stats, "int32"), _stream(stream)))
+
+
+def cg_mech_set_smem_limit(h, nbytes: int):
+    _check(load().cg_mech_set_smem_limit(h.ptr, int(nbytes)))
+
+
+def cg_integrate_batch(handles, opts, Ts, Ys, ps, statuses=None, stats=None, stream=None):
+    """One persistent launch over the cells of several mechanisms; the k-th
+    tensors belong to handles[k]."""
+    k = len(handles)
+    P = ctypes.c_void_p
+    arr = lambda vals: (P * k)(*vals)
+    Ns = (ctypes.c_int64 * k)(*[t.shape[0] for t in Ts])
+    st = arr([_dev(s, "int32") for s in statuses]) if statuses is not None else None
+    sa = arr([_dev(s, "int32") for s in stats]) if stats is not None else None
+    _check(load().cg_integrate_batch(k, arr([h.ptr for h in handles]), Ns, arr([_dev(t) for t in Ts]),
+                                     arr([_dev(y) for y in Ys]), arr([_dev(p) for p in ps]), st, sa,
+                                     ctypes.byref(opts), _stream(stream)))
 
 
 def cg_integrate_host(h, opts, T, Y, p_or_rho, status=None, stats=None):

@@ -100,31 +100,45 @@ Schedule make_schedule(std::vector<Term> terms, int lanes_n) {
     return s;
 }
 
-// mat_bytes: 8 for the FP64 Newton matrix, 4 for the FP32 one
-Layout make_layout(int ns, int nr, int mat_bytes = 8) {
+// Place one cell's arrays: hottest first into shared memory (at most
+// smem_limit bytes per cell), the rest into the cell's global scratch slot.
+// mat_bytes: 8 for the FP64 Newton matrix, 4 for the FP32 one.
+Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit) {
+    using namespace cg;
     const int n = ns + 1;
     Layout L;
     L.ld = (n % 2) ? n : n + 1;   // odd stride: fewer bank conflicts on column walks
-    int o = 0;
-    L.G = o; o += (n * L.ld * mat_bytes + 7) / 8;
-    L.RD = o; o += 9 * nr;
-    L.SP = o; o += 4 * ns;
-    L.V = o; o += ns;
-    L.yn = o; o += n;
-    L.Y = o; o += n;
-    L.base = o; o += n;
-    L.S = o; o += n;
-    L.S0 = o; o += n;
-    L.f = o; o += n;
-    L.err = o; o += n;
-    L.y1 = o; o += n;
-    L.colA = o; o += n;
-    L.colB = o; o += n;
-    L.rinv = o; o += n;
-    L.Gam = o; o += 5 * n;
-    L.piv = o; o += (n + 1) / 2;
-    L.red = o; o += 24;
-    L.total = (o + 1) & ~1;
+    int size[A_COUNT];
+    size[A_G] = (n * L.ld * mat_bytes + 7) / 8;
+    size[A_RD] = 9 * nr;
+    size[A_SP] = 4 * ns;
+    size[A_V] = ns;
+    for (int a : {A_YN, A_Y, A_BASE, A_S, A_S0, A_F, A_ERR, A_Y1, A_COLA, A_COLB, A_RINV}) size[a] = n;
+    size[A_GAM] = 5 * n;
+    size[A_PIV] = (n + 1) / 2;
+    size[A_RED] = 24;
+    const int order[A_COUNT] = {A_RED, A_PIV, A_G, A_RINV, A_YN, A_Y, A_F, A_S, A_BASE, A_S0,
+                                A_ERR, A_Y1, A_COLA, A_COLB, A_SP, A_V, A_GAM, A_RD};
+    // 1 KiB of the block's shared memory stays free for the kernels' static variables
+    const long budget = (long)((smem_limit > 2048 ? smem_limit - 1024 : 1024) / sizeof(double));
+    int so = 0, go = 0;
+    L.gmask = 0;
+    bool spill = false;
+    for (int k = 0; k < A_COUNT; ++k) {
+        const int a = order[k];
+        const int sz = (size[a] + 1) & ~1;   // 16-byte aligned arrays
+        if (a == A_RED || (!spill && so + sz <= budget)) {
+            L.off[a] = so;
+            so += sz;
+        } else {
+            spill = true;   // keep the priority order: once one array spills, the rest follow
+            L.off[a] = go;
+            go += sz;
+            L.gmask |= 1u << a;
+        }
+    }
+    L.stotal = so;
+    L.gtotal = go;
     return L;
 }
 
@@ -315,6 +329,7 @@ struct cg_mech {
     Layout L32;   // FP32 Newton matrix (mixed precision)
     int ns = 0, nr = 0;
     int tpb = 1;                       // teams per block (team = dm.team threads)
+    size_t smem_limit = 0;             // shared memory per cell before arrays spill to scratch
     std::vector<void*> allocs;         // mechanism data
     std::vector<void*> sched_allocs;   // schedules (rebuilt when the team size changes)
     std::vector<Term> wterms, vterms, jterms;
@@ -334,7 +349,7 @@ int default_team(int n) { return n <= 24 ? 32 : 64; }
 
 int default_tpb(int team, const Layout& L) {
     if (team > 32) return 1;
-    const size_t per = (size_t)L.total * sizeof(double);
+    const size_t per = (size_t)L.stotal * sizeof(double);
     if (per > 24 * 1024) return 1;
     int w = 4;
     while (w > 1 && (size_t)w * per > kMaxSmemPerBlock) --w;
@@ -363,6 +378,21 @@ cg_status build_schedules(cg_mech* m, int team) {
     dm.j_len = js.len;
     dm.team = team;
     return CG_OK;
+}
+
+cg::Task make_task(const cg_mech* m, const IntParams& P, int64_t N, int64_t first, double* T, double* Y,
+                   const double* p, int32_t* status, int32_t* stats) {
+    cg::Task t;
+    t.M = m->dm;
+    t.L = P.precision ? m->L32 : m->L;
+    t.N = N;
+    t.first = first;
+    t.T = T;
+    t.Y = Y;
+    t.p = p;
+    t.status = status;
+    t.stats = stats;
+    return t;
 }
 
 cg_status validate(const cg_mech_desc* d) {
@@ -452,7 +482,7 @@ cg_status cg_mech_set_launch(cg_mech* m, int team, int teams_per_block) {
         return fail(CG_EINVAL, "team must be 32, 64, 128 or 256 threads");
     if (teams_per_block < 1 || (team > 32 && teams_per_block != 1) || team * teams_per_block > 1024)
         return fail(CG_EINVAL, "teams_per_block must be 1 for teams above one warp, and blocks <= 1024 threads");
-    if ((size_t)teams_per_block * m->L.total * sizeof(double) > kMaxSmemPerBlock)
+    if ((size_t)teams_per_block * m->L.stotal * sizeof(double) > kMaxSmemPerBlock)
         return fail(CG_ECAPACITY, "%d cells per block need more than %zu bytes of shared memory",
                     teams_per_block, kMaxSmemPerBlock);
     if (team != m->dm.team) {
@@ -462,6 +492,19 @@ cg_status cg_mech_set_launch(cg_mech* m, int team, int teams_per_block) {
         if (st != CG_OK) return st;
     }
     m->tpb = teams_per_block;
+    return CG_OK;
+}
+
+cg_status cg_mech_set_smem_limit(cg_mech* m, int64_t bytes) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    if (bytes < 1024 || bytes > (int64_t)kMaxSmemPerBlock)
+        return fail(CG_EINVAL, "limit must be 1 KiB .. %zu bytes", kMaxSmemPerBlock);
+    const cg::Layout L = make_layout(m->ns, m->nr, 8, (size_t)bytes);
+    const cg::Layout L32 = make_layout(m->ns, m->nr, 4, (size_t)bytes);
+    if ((size_t)m->tpb * L.stotal * sizeof(double) > kMaxSmemPerBlock) m->tpb = 1;
+    m->L = L;
+    m->L32 = L32;
+    m->smem_limit = (size_t)bytes;
     return CG_OK;
 }
 
@@ -478,10 +521,8 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     cg_status st = validate(d);
     if (st != CG_OK) return st;
     const int ns = d->n_species, nr = d->n_reactions, n = ns + 1;
-    const Layout L = make_layout(ns, nr);
-    if ((size_t)L.total * sizeof(double) > kMaxSmemPerBlock)
-        return fail(CG_ECAPACITY, "mechanism with %d species and %d reactions needs %zu bytes of shared memory per cell (max %zu)",
-                    ns, nr, (size_t)L.total * sizeof(double), kMaxSmemPerBlock);
+    if (n > 1024) return fail(CG_ECAPACITY, "at most 1023 species are supported (got %d)", ns);
+    const Layout L = make_layout(ns, nr, 8, kMaxSmemPerBlock);
 
     // internal reaction order: by type, stable
     std::vector<int> perm(nr);
@@ -574,7 +615,8 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     m->ns = ns;
     m->nr = nr;
     m->L = L;
-    m->L32 = make_layout(ns, nr, 4);
+    m->L32 = make_layout(ns, nr, 4, kMaxSmemPerBlock);
+    m->smem_limit = kMaxSmemPerBlock;
     DevMech& dm = m->dm;
     dm.ns = ns;
     dm.nr = nr;
@@ -708,8 +750,44 @@ cg_status cg_integrate(const cg_mech* m, const cg_integrate_opts* o, int64_t N, 
     if (N < 0) return fail(CG_EINVAL, "N < 0");
     if (N == 0) return CG_OK;
     if (!T || !Y || !p_or_rho) return fail(CG_EINVAL, "NULL array");
-    cudaError_t e = cg::launch_integrate(m->dm, P.precision ? m->L32 : m->L, P, m->tpb, N, T, Y, p_or_rho,
-                                         cell_status, cell_stats, (cudaStream_t)stream);
+    cg::Tasks tasks;
+    tasks.count = 1;
+    tasks.total = N;
+    tasks.t[0] = make_task(m, P, N, 0, T, Y, p_or_rho, cell_status, cell_stats);
+    cudaError_t e = cg::launch_integrate(tasks, P, m->dm.team, m->tpb, o->persistent != 0,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch");
+}
+
+cg_status cg_integrate_batch(int n_mech, const cg_mech* const* mechs, const int64_t* N,
+                             double* const* T, double* const* Y, const double* const* p_or_rho,
+                             int32_t* const* cell_status, int32_t* const* cell_stats,
+                             const cg_integrate_opts* o, void* stream) {
+    if (n_mech < 1 || n_mech > cg::kMaxTasks)
+        return fail(CG_EINVAL, "n_mech must be 1..%d", cg::kMaxTasks);
+    if (!mechs || !N || !T || !Y || !p_or_rho) return fail(CG_EINVAL, "NULL array");
+    IntParams P;
+    cg_status st = make_params(o, P);
+    if (st != CG_OK) return st;
+    cg::Tasks tasks;
+    tasks.count = n_mech;
+    tasks.total = 0;
+    const int team = mechs[0] ? mechs[0]->dm.team : 0;
+    for (int k = 0; k < n_mech; ++k) {
+        const cg_mech* m = mechs[k];
+        if (!m) return fail(CG_EINVAL, "mechs[%d] is NULL", k);
+        if (m->dm.team != team)
+            return fail(CG_EINVAL, "all mechanisms of a batch need the same team size (cg_mech_set_launch)");
+        if (N[k] < 0) return fail(CG_EINVAL, "N[%d] < 0", k);
+        if (N[k] > 0 && (!T[k] || !Y[k] || !p_or_rho[k])) return fail(CG_EINVAL, "NULL array for mechanism %d", k);
+        tasks.t[k] = make_task(m, P, N[k], tasks.total, T[k], Y[k], p_or_rho[k],
+                               cell_status ? cell_status[k] : nullptr, cell_stats ? cell_stats[k] : nullptr);
+        tasks.total += N[k];
+    }
+    if (tasks.total == 0) return CG_OK;
+    int tpb = mechs[0]->tpb;
+    for (int k = 1; k < n_mech; ++k) tpb = std::min(tpb, mechs[k]->tpb);
+    cudaError_t e = cg::launch_integrate(tasks, P, team, tpb, true, (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch");
 }
 
@@ -745,8 +823,11 @@ cg_status cg_integrate_host(const cg_mech* mc, const cg_integrate_opts* o, int64
         (e = cudaMemcpyAsync(m->wY, Y, N * m->ns * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(m->wP, p_or_rho, N * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync H2D");
-    if ((e = cg::launch_integrate(m->dm, P.precision ? m->L32 : m->L, P, m->tpb, N, m->wT, m->wY, m->wP,
-                                  m->wStatus, m->wStats, s)) != cudaSuccess)
+    cg::Tasks tasks;
+    tasks.count = 1;
+    tasks.total = N;
+    tasks.t[0] = make_task(m, P, N, 0, m->wT, m->wY, m->wP, m->wStatus, m->wStats);
+    if ((e = cg::launch_integrate(tasks, P, m->dm.team, m->tpb, o->persistent != 0, s)) != cudaSuccess)
         return cuda_fail(e, "integrate launch");
     if ((e = cudaMemcpyAsync(T, m->wT, N * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(Y, m->wY, N * m->ns * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

@@ -68,19 +68,48 @@ struct DevMech {
     const double *w_fac, *v_fac, *j_fac;
 };
 
-// Offsets (in doubles) of the arrays in one team's shared-memory slice.
+// Working arrays of one cell. Each lives in the team's slice of shared
+// memory or, when the cell's arrays do not fit there (large mechanisms), in
+// the team's slot of a global scratch buffer (L2-resident).
+enum {
+    A_G = 0,    // n x ld Newton matrix / LU factors (FP64 or FP32)
+    A_RD,       // 9 nr: q, dq/dT, w, d[6] per reaction
+    A_SP,       // 4 ns: h/RT, g/RT, c_p/R, d(c_p/R)/dT
+    A_V,        // ns: dense third-body column of dOmega/dC
+    A_YN, A_Y, A_BASE, A_S, A_S0, A_F, A_ERR, A_Y1, A_COLA, A_COLB, A_RINV,   // n each
+    A_GAM,      // 5 n: stage derivatives
+    A_PIV,      // n ints
+    A_RED,      // 24 doubles: cross-warp reduction scratch (always shared)
+    A_COUNT
+};
+
 struct Layout {
     int ld;                  // row stride of the n x n matrix (odd)
-    int G;                   // n x ld: Newton matrix / LU factors
-    int RD;                  // 9 nr: q, dq/dT, w, d[6] per reaction
-    int SP;                  // 4 ns: h/RT, g/RT, c_p/R, d(c_p/R)/dT
-    int V;                   // ns: dense third-body column of dOmega/dC
-    int yn, Y, base, S, S0, f, err, y1, colA, colB, rinv;   // n each
-    int Gam;                 // 5 n: stage derivatives
-    int piv;                 // ints, n of them (in ceil(n/2) doubles)
-    int red;                 // 24: cross-warp reduction scratch
-    int total;               // doubles per team
+    int off[A_COUNT];        // offset in doubles within shared or global slot
+    unsigned gmask;          // bit a set: array a is in global scratch
+    int stotal;              // doubles of shared memory per team
+    int gtotal;              // doubles of global scratch per team
 };
+
+struct Ws {
+    int ld;
+    double *G, *RD, *SP, *V, *yn, *Y, *base, *S, *S0, *f, *err, *y1, *colA, *colB, *rinv, *Gam, *red;
+    int* piv;
+};
+
+__device__ __forceinline__ Ws make_ws(const Layout& L, double* sbase, double* gbase) {
+    double* p[A_COUNT];
+#pragma unroll
+    for (int a = 0; a < A_COUNT; ++a) p[a] = ((L.gmask >> a) & 1u ? gbase : sbase) + L.off[a];
+    Ws w;
+    w.ld = L.ld;
+    w.G = p[A_G]; w.RD = p[A_RD]; w.SP = p[A_SP]; w.V = p[A_V];
+    w.yn = p[A_YN]; w.Y = p[A_Y]; w.base = p[A_BASE]; w.S = p[A_S]; w.S0 = p[A_S0];
+    w.f = p[A_F]; w.err = p[A_ERR]; w.y1 = p[A_Y1]; w.colA = p[A_COLA]; w.colB = p[A_COLB];
+    w.rinv = p[A_RINV]; w.Gam = p[A_GAM]; w.red = p[A_RED];
+    w.piv = reinterpret_cast<int*>(p[A_PIV]);
+    return w;
+}
 
 // Integration parameters and the Butcher tableau (stage-derivative form).
 struct IntParams {
@@ -238,14 +267,14 @@ static __device__ __forceinline__ double rcp_nr(double x) {
 // Fills SP (species thermo) and RD (q_j and, with deriv, dq_j/dT, the
 // third-body weight w_j and the mass-action partials). Returns sum C.
 template <int TEAM>
-__device__ double rates(const DevMech& M, const Layout& L, double* sm, const double* y, bool deriv,
+__device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deriv,
                         int lane) {
     const int ns = M.ns, nr = M.nr;
     const double T = y[0];
     const double* C = y + 1;
     const double lnT = log(T);
     const double invT = 1.0 / T;
-    double* hRT = sm + L.SP;
+    double* hRT = W.SP;
     double* gRT = hRT + ns;
     double* cpR = gRT + ns;
     double* dcpR = cpR + ns;
@@ -266,10 +295,10 @@ __device__ double rates(const DevMech& M, const Layout& L, double* sm, const dou
         dcpR[i] = dcp;
         csum += C[i];
     }
-    const double Mc = team_sum<TEAM>(csum, sm + L.red);
+    const double Mc = team_sum<TEAM>(csum, W.red);
     team_sync<TEAM>();   // SP visible to the whole team
     const double lnPRT = M.ln_pref_R - lnT;   // ln(p_ref / (R T))
-    double* q = sm + L.RD;
+    double* q = W.RD;
     double* dqdT = q + nr;
     double* wv = dqdT + nr;
     double* dd = wv + nr;
@@ -390,21 +419,21 @@ struct SrcInfo {
     double wT, Dt, Ws, Mc, sdil, cw, cdc;
 };
 
-// S = (omega_T, dC/dt) into sm[L.S..]; y = (T, C).
+// S = (omega_T, dC/dt) into W.S; y = (T, C).
 template <int TEAM>
-__device__ SrcInfo assemble_source(const DevMech& M, const Layout& L, double* sm, const double* y,
+__device__ SrcInfo assemble_source(const DevMech& M, const Ws& W,const double* y,
                                    int reactor, double Mc, int lane) {
     const int ns = M.ns;
-    double* S = sm + L.S;
-    double* red = sm + L.red;
-    const double* hRT = sm + L.SP;
+    double* S = W.S;
+    double* red = W.red;
+    const double* hRT = W.SP;
     const double* cpR = hRT + 2 * ns;
     const double* dcpR = cpR + ns;
     const double T = y[0];
     const double* C = y + 1;
     for (int i = lane; i < ns; i += TEAM) S[1 + i] = 0.0;
     team_sync<TEAM>();
-    run_schedule<TEAM>(M.w_len, M.w_dst, M.w_src, M.w_fac, S, sm + L.RD, lane);
+    run_schedule<TEAM>(M.w_len, M.w_dst, M.w_src, M.w_fac, S, W.RD, lane);
     const double sub = reactor == R_CONV ? 1.0 : 0.0;   // u/RT = h/RT - 1, c_v/R = c_p/R - 1
     double qe = 0.0, den = 0.0, ws = 0.0, cw = 0.0, cdc = 0.0;
     for (int i = lane; i < ns; i += TEAM) {
@@ -435,18 +464,18 @@ __device__ SrcInfo assemble_source(const DevMech& M, const Layout& L, double* sm
 }
 
 // Analytical Jacobian. With out == nullptr, writes the Newton matrix
-// G = I - gh J into sm[L.G] (row stride L.ld) in the matrix type MT (FP64,
+// G = I - gh J into W.G (row stride W.ld) in the matrix type MT (FP64,
 // or FP32 for the mixed-precision Newton); otherwise writes J to out
 // (row-major n x n, global memory, MT = double).
 template <int TEAM, class MT>
-__device__ void assemble_jacobian(const DevMech& M, const Layout& L, double* sm, const double* y,
+__device__ void assemble_jacobian(const DevMech& M, const Ws& W,const double* y,
                                   int reactor, const SrcInfo& si, double gh, double* out, int lane) {
-    const int ns = M.ns, n = M.n, ld = L.ld;
-    MT* G = reinterpret_cast<MT*>(sm + L.G);
-    double* V = sm + L.V;
-    const double* hRT = sm + L.SP;
+    const int ns = M.ns, n = M.n, ld = W.ld;
+    MT* G = reinterpret_cast<MT*>(W.G);
+    double* V = W.V;
+    const double* hRT = W.SP;
     const double* cpR = hRT + 2 * ns;
-    const double* RD = sm + L.RD;
+    const double* RD = W.RD;
     const double T = y[0];
     const double* C = y + 1;
     const double sub = reactor == R_CONV ? 1.0 : 0.0;
@@ -464,8 +493,8 @@ __device__ void assemble_jacobian(const DevMech& M, const Layout& L, double* sm,
     // temperature row: J_T,m = -(T A_m + omega_T c_m) / D (m > 0),
     // J_T,0 = -(sum c_i omega_i + T A_0 + omega_T sum C_i dc_i/dT) / D,
     // A_m = sum_i e_i dOmega_i/dy_m (e = u/RT or h/RT, c = c_v/R or c_p/R)
-    double* JT = sm + L.colA;
-    double* ds = sm + L.colB;
+    double* JT = W.colA;
+    double* ds = W.colB;
     const double invD = 1.0 / si.Dt;
     for (int m = lane; m < n; m += TEAM) {
         double a = 0.0, b = 0.0;

@@ -4,20 +4,40 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <vector>
-
 #include "chem_device.cuh"
 
 namespace cg {
 
-cudaError_t launch_eval_rates(const DevMech& M, const Layout& L, int wpb, int reactor, int64_t N,
+// One mechanism's share of an integration launch: cells [first, first + N)
+// of the launch's cell index space are cells [0, N) of these arrays.
+struct Task {
+    DevMech M;
+    Layout L;
+    int64_t N, first;
+    double* T;
+    double* Y;
+    const double* p;
+    int32_t* status;
+    int32_t* stats;
+};
+
+constexpr int kMaxTasks = 4;
+
+struct Tasks {
+    Task t[kMaxTasks];
+    int count;
+    int64_t total;
+};
+
+cudaError_t launch_eval_rates(const DevMech& M, const Layout& L, int tpb, int reactor, int64_t N,
                               const double* T, const double* C, double* S, cudaStream_t st);
-cudaError_t launch_eval_jacobian(const DevMech& M, const Layout& L, int wpb, int reactor, int64_t N,
+cudaError_t launch_eval_jacobian(const DevMech& M, const Layout& L, int tpb, int reactor, int64_t N,
                                  const double* T, const double* C, double* J, cudaStream_t st);
 cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const double* e,
                                const double* Y, double* T, int iters, cudaStream_t st);
-cudaError_t launch_integrate(const DevMech& M, const Layout& L, const IntParams& P, int wpb,
-                             int64_t N, double* T, double* Y, const double* p_or_rho,
-                             int32_t* status, int32_t* stats, cudaStream_t st);
+// All tasks share one team size; `persistent` selects the resident grid with
+// the work counter (always used when a cell needs global scratch).
+cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, int tpb, bool persistent,
+                             cudaStream_t st);
 
 }  // namespace cg

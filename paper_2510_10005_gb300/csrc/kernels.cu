@@ -1,10 +1,17 @@
 // Kernels of chemgb: one team of TEAM threads per cell (TEAM = 32: one warp,
-// several teams per block; TEAM = 64..256: one team per block).
+// several teams per block; TEAM = 64..256: one team per block). Every
+// kernel walks the cells in a loop: a team takes cell `team id` and then
+// either the next cell of a fixed stride or, in the persistent form, the
+// next cell of an atomic work counter shared by the whole launch (work
+// stealing: a team that finishes a cheap cell takes the next one at once).
+// Arrays of a cell that do not fit in shared memory live in the team's slot
+// of a global scratch buffer.
 //
 //   eval_rates_kernel      S(y) for N cells (Section 2.2, Section 3, App. B)
 //   eval_jacobian_kernel   dS/dy for N cells (Section 3.2)
 //   temperature_kernel     T from (e, Y) by Newton (Section 2.1)
-//   integrate_kernel       backward Euler / SDIRK over dt (Section 3.2, App. A)
+//   integrate_kernel       backward Euler / SDIRK over dt (Section 3.2, App. A),
+//                          for up to kMaxTasks mechanisms in one launch
 #include "chem_device.cuh"
 #include "chem_internal.h"
 
@@ -12,15 +19,42 @@ namespace cg {
 
 constexpr double kR = 8314.46261815324;   // J/(kmol K)
 
+// Position of this team in the launch.
 template <int TEAM>
-__device__ __forceinline__ double* team_smem(const Layout& L) {
-    extern __shared__ double smem_all[];
-    return smem_all + (size_t)(threadIdx.x / TEAM) * L.total;
+struct TeamPos {
+    int lane, tib, tpb;
+    int64_t id, count;
+    __device__ __forceinline__ TeamPos() {
+        lane = team_lane<TEAM>();
+        tpb = blockDim.x / TEAM;
+        tib = threadIdx.x / TEAM;
+        id = (int64_t)blockIdx.x * tpb + tib;
+        count = (int64_t)gridDim.x * tpb;
+    }
+};
+
+// Next global cell index: from the work counter (every thread of the team
+// gets the same value) or the fixed stride.
+template <int TEAM>
+__device__ __forceinline__ int64_t next_cell(unsigned long long* counter, int64_t prev, int64_t stride,
+                                             int lane) {
+    if (!counter) return prev + stride;
+    if constexpr (TEAM == 32) {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(counter, 1ull);
+        return (int64_t)__shfl_sync(kFull, v, 0);
+    } else {
+        __shared__ unsigned long long slot;
+        __syncthreads();
+        if (lane == 0) slot = atomicAdd(counter, 1ull);
+        __syncthreads();
+        return (int64_t)slot;
+    }
 }
 
 template <int TEAM>
-__device__ __forceinline__ int64_t team_cell() {
-    return (int64_t)blockIdx.x * (blockDim.x / TEAM) + threadIdx.x / TEAM;
+__device__ __forceinline__ int64_t first_cell(unsigned long long* counter, int64_t id, int lane) {
+    return counter ? next_cell<TEAM>(counter, 0, 0, lane) : id;
 }
 
 // ---------------------------------------------------------------------------
@@ -28,36 +62,42 @@ __device__ __forceinline__ int64_t team_cell() {
 template <int TEAM>
 __global__ void eval_rates_kernel(DevMech M, Layout L, int reactor, int64_t N,
                                   const double* __restrict__ T, const double* __restrict__ C,
-                                  double* __restrict__ S) {
-    const int lane = team_lane<TEAM>();
-    const int64_t cell = team_cell<TEAM>();
-    if (cell >= N) return;   // whole team (a team never straddles this bound)
-    double* sm = team_smem<TEAM>(L);
-    double* y = sm + L.Y;
-    if (lane == 0) y[0] = T[cell];
-    for (int i = lane; i < M.ns; i += TEAM) y[1 + i] = C[(int64_t)i * N + cell];
-    team_sync<TEAM>();
-    const double Mc = rates<TEAM>(M, L, sm, y, false, lane);
-    assemble_source<TEAM>(M, L, sm, y, reactor, Mc, lane);
-    const double* Sv = sm + L.S;
-    for (int i = lane; i < M.n; i += TEAM) S[(int64_t)i * N + cell] = Sv[i];
+                                  double* __restrict__ S, double* gscratch, int64_t gstride) {
+    extern __shared__ double smem_all[];
+    const TeamPos<TEAM> tp;
+    const Ws W = make_ws(L, smem_all + (size_t)tp.tib * L.stotal,
+                         gscratch ? gscratch + tp.id * gstride : nullptr);
+    const int lane = tp.lane;
+    for (int64_t cell = tp.id; cell < N; cell += tp.count) {
+        double* y = W.Y;
+        if (lane == 0) y[0] = T[cell];
+        for (int i = lane; i < M.ns; i += TEAM) y[1 + i] = C[(int64_t)i * N + cell];
+        team_sync<TEAM>();
+        const double Mc = rates<TEAM>(M, W, y, false, lane);
+        assemble_source<TEAM>(M, W, y, reactor, Mc, lane);
+        for (int i = lane; i < M.n; i += TEAM) S[(int64_t)i * N + cell] = W.S[i];
+        team_sync<TEAM>();
+    }
 }
 
 template <int TEAM>
 __global__ void eval_jacobian_kernel(DevMech M, Layout L, int reactor, int64_t N,
                                      const double* __restrict__ T, const double* __restrict__ C,
-                                     double* __restrict__ J) {
-    const int lane = team_lane<TEAM>();
-    const int64_t cell = team_cell<TEAM>();
-    if (cell >= N) return;
-    double* sm = team_smem<TEAM>(L);
-    double* y = sm + L.Y;
-    if (lane == 0) y[0] = T[cell];
-    for (int i = lane; i < M.ns; i += TEAM) y[1 + i] = C[(int64_t)i * N + cell];
-    team_sync<TEAM>();
-    const double Mc = rates<TEAM>(M, L, sm, y, true, lane);
-    const SrcInfo si = assemble_source<TEAM>(M, L, sm, y, reactor, Mc, lane);
-    assemble_jacobian<TEAM, double>(M, L, sm, y, reactor, si, 0.0, J + cell * (int64_t)M.n * M.n, lane);
+                                     double* __restrict__ J, double* gscratch, int64_t gstride) {
+    extern __shared__ double smem_all[];
+    const TeamPos<TEAM> tp;
+    const Ws W = make_ws(L, smem_all + (size_t)tp.tib * L.stotal,
+                         gscratch ? gscratch + tp.id * gstride : nullptr);
+    const int lane = tp.lane;
+    for (int64_t cell = tp.id; cell < N; cell += tp.count) {
+        double* y = W.Y;
+        if (lane == 0) y[0] = T[cell];
+        for (int i = lane; i < M.ns; i += TEAM) y[1 + i] = C[(int64_t)i * N + cell];
+        team_sync<TEAM>();
+        const double Mc = rates<TEAM>(M, W, y, true, lane);
+        const SrcInfo si = assemble_source<TEAM>(M, W, y, reactor, Mc, lane);
+        assemble_jacobian<TEAM, double>(M, W, y, reactor, si, 0.0, J + cell * (int64_t)M.n * M.n, lane);
+    }
 }
 
 // Newton on sum_i Y_i e_i(T) = e, e = u (constant volume) or h (otherwise),
@@ -101,37 +141,34 @@ struct Counters {
     int steps, rejects, newton, lu;
 };
 
-// One step of size h from sm[yn]: stages of the tableau in stage-derivative
+// One step of size h from W.yn: stages of the tableau in stage-derivative
 // form (Appendix A), each by full Newton with G = I - a_pp h J(Y_p). On
 // success y1 holds the new state and err the (filtered) embedded estimate.
 // MT = float: G is assembled and factored in FP32 (an inexact Newton whose
 // residual, update and convergence test stay in FP64).
 template <int TEAM, class MT>
-__device__ bool rk_step(const DevMech& M, const Layout& L, const IntParams& P, double* sm, double h,
-                        Counters& cnt, int lane) {
+__device__ bool rk_step(const DevMech& M, const Ws& W, const IntParams& P, double h, Counters& cnt,
+                        int lane) {
     const int n = M.n;
-    double* yn = sm + L.yn;
-    double* Y = sm + L.Y;
-    double* base = sm + L.base;
-    double* S = sm + L.S;
-    double* S0 = sm + L.S0;
-    double* f = sm + L.f;
-    MT* G = reinterpret_cast<MT*>(sm + L.G);
-    double* rinv = sm + L.rinv;
-    double* red = sm + L.red;
-    int* piv = reinterpret_cast<int*>(sm + L.piv);
+    double* yn = W.yn;
+    double* Y = W.Y;
+    double* base = W.base;
+    double* S = W.S;
+    double* S0 = W.S0;
+    double* f = W.f;
+    MT* G = reinterpret_cast<MT*>(W.G);
     if (!P.start_zero) {   // first Newton iterate of every stage: Gamma = S(y_n)
-        const double Mc = rates<TEAM>(M, L, sm, yn, false, lane);
-        assemble_source<TEAM>(M, L, sm, yn, P.reactor, Mc, lane);
+        const double Mc = rates<TEAM>(M, W, yn, false, lane);
+        assemble_source<TEAM>(M, W, yn, P.reactor, Mc, lane);
         for (int i = lane; i < n; i += TEAM) S0[i] = S[i];
         team_sync<TEAM>();
     }
     for (int p = 0; p < P.s; ++p) {
         const double gh = P.A[p][p] * h;
-        double* Gp = sm + L.Gam + p * n;
+        double* Gp = W.Gam + p * n;
         for (int i = lane; i < n; i += TEAM) {
             double b = yn[i];
-            for (int j = 0; j < p; ++j) b = fma(h * P.A[p][j], sm[L.Gam + j * n + i], b);
+            for (int j = 0; j < p; ++j) b = fma(h * P.A[p][j], W.Gam[j * n + i], b);
             base[i] = b;
             Gp[i] = P.start_zero ? 0.0 : S0[i];
         }
@@ -140,15 +177,15 @@ __device__ bool rk_step(const DevMech& M, const Layout& L, const IntParams& P, d
         for (int k = 0; k < P.max_newton; ++k) {
             for (int i = lane; i < n; i += TEAM) Y[i] = fma(gh, Gp[i], base[i]);
             team_sync<TEAM>();
-            const double Mc = rates<TEAM>(M, L, sm, Y, true, lane);
-            const SrcInfo si = assemble_source<TEAM>(M, L, sm, Y, P.reactor, Mc, lane);
-            assemble_jacobian<TEAM, MT>(M, L, sm, Y, P.reactor, si, gh, nullptr, lane);
+            const double Mc = rates<TEAM>(M, W, Y, true, lane);
+            const SrcInfo si = assemble_source<TEAM>(M, W, Y, P.reactor, Mc, lane);
+            assemble_jacobian<TEAM, MT>(M, W, Y, P.reactor, si, gh, nullptr, lane);
             for (int i = lane; i < n; i += TEAM) f[i] = S[i] - Gp[i];   // -f(Gamma)
             team_sync<TEAM>();
             cnt.newton++;
             cnt.lu++;
-            if (!lu_factor<TEAM, MT>(G, n, L.ld, piv, rinv, red, lane)) return false;
-            lu_solve<TEAM, MT>(G, n, L.ld, piv, rinv, f, lane);
+            if (!lu_factor<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, W.red, lane)) return false;
+            lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, f, lane);
             for (int i = lane; i < n; i += TEAM) {
                 const double g = Gp[i] + f[i];
                 Gp[i] = g;
@@ -156,19 +193,19 @@ __device__ bool rk_step(const DevMech& M, const Layout& L, const IntParams& P, d
                 Y[i] = fma(gh, g, base[i]);
             }
             team_sync<TEAM>();
-            const double nrm = wrms<TEAM>(f, yn, Y, n, P.rtol, P.atol, red, lane);
+            const double nrm = wrms<TEAM>(f, yn, Y, n, P.rtol, P.atol, W.red, lane);
             if (!isfinite(nrm)) return false;
             if (nrm <= P.newton_tol) { conv = true; break; }
         }
         if (!conv) return false;
     }
-    double* y1 = sm + L.y1;
-    double* err = sm + L.err;
+    double* y1 = W.y1;
+    double* err = W.err;
     bool bad = false;
     for (int i = lane; i < n; i += TEAM) {
         double v = yn[i], e = 0.0;
         for (int p = 0; p < P.s; ++p) {
-            const double g = sm[L.Gam + p * n + i];
+            const double g = W.Gam[p * n + i];
             v = fma(h * P.b[p], g, v);
             e = fma(h * (P.b[p] - P.bh[p]), g, e);
         }
@@ -177,15 +214,15 @@ __device__ bool rk_step(const DevMech& M, const Layout& L, const IntParams& P, d
         bad |= !isfinite(v);
     }
     team_sync<TEAM>();
-    if (team_any<TEAM>(bad, red)) return false;
-    if (P.adaptive && P.err_filter) lu_solve<TEAM, MT>(G, n, L.ld, piv, rinv, err, lane);
+    if (team_any<TEAM>(bad, W.red)) return false;
+    if (P.adaptive && P.err_filter) lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, err, lane);
     // admissible: T > 0 and C_i >= -neg_tol sum C
     double cs = 0.0;
     for (int i = 1 + lane; i < n; i += TEAM) cs += y1[i];
-    cs = team_sum<TEAM>(cs, red);
+    cs = team_sum<TEAM>(cs, W.red);
     bool neg = false;
     for (int i = 1 + lane; i < n; i += TEAM) neg |= y1[i] < -P.neg_tol * cs;
-    neg = team_any<TEAM>(neg, red) || !(y1[0] > 0.0);
+    neg = team_any<TEAM>(neg, W.red) || !(y1[0] > 0.0);
     return !neg;
 }
 
@@ -199,8 +236,8 @@ __device__ __forceinline__ void copy_vec(double* dst, const double* src, int n, 
 // replaced by two steps of level d+1 (recursively, at most max_halvings
 // deep), walked iteratively with a position counter.
 template <int TEAM, class MT>
-__device__ int integrate_fixed(const DevMech& M, const Layout& L, const IntParams& P, double* sm,
-                               Counters& cnt, int lane) {
+__device__ int integrate_fixed(const DevMech& M, const Ws& W, const IntParams& P, Counters& cnt,
+                               int lane) {
     const int D = P.max_halvings;
     const double hsub = P.dt / P.nsub;
     for (int s = 0; s < P.nsub; ++s) {
@@ -209,8 +246,8 @@ __device__ int integrate_fixed(const DevMech& M, const Layout& L, const IntParam
         int d = 0;
         while (pos < total) {
             const double h = ldexp(hsub, -d);
-            if (rk_step<TEAM, MT>(M, L, P, sm, h, cnt, lane)) {
-                copy_vec<TEAM>(sm + L.yn, sm + L.y1, M.n, lane);
+            if (rk_step<TEAM, MT>(M, W, P, h, cnt, lane)) {
+                copy_vec<TEAM>(W.yn, W.y1, M.n, lane);
                 cnt.steps++;
                 pos += 1ull << (D - d);
                 while (d > 0 && ((pos >> (D - d)) & 1ull) == 0ull) --d;
@@ -227,8 +264,8 @@ __device__ int integrate_fixed(const DevMech& M, const Layout& L, const IntParam
 // Error-controlled steps: accept when WRMS(err) <= 1; next step
 // h min(5, max(0.2, 0.9 err^(-1/(q+1)))); Newton failure: h / 4.
 template <int TEAM, class MT>
-__device__ int integrate_adaptive(const DevMech& M, const Layout& L, const IntParams& P, double* sm,
-                                  Counters& cnt, int lane) {
+__device__ int integrate_adaptive(const DevMech& M, const Ws& W, const IntParams& P, Counters& cnt,
+                                  int lane) {
     const double expo = -1.0 / (P.err_order + 1.0);
     double t = 0.0;
     double h = P.h0 > 0.0 ? fmin(P.h0, P.dt) : P.dt;
@@ -238,16 +275,16 @@ __device__ int integrate_adaptive(const DevMech& M, const Layout& L, const IntPa
         if (h < P.hmin) return CELL_STEP_TOO_SMALL;
         const bool last = t + h >= P.dt;
         const double hh = last ? P.dt - t : h;
-        if (!rk_step<TEAM, MT>(M, L, P, sm, hh, cnt, lane)) {
+        if (!rk_step<TEAM, MT>(M, W, P, hh, cnt, lane)) {
             cnt.rejects++;
             h = 0.25 * hh;
             continue;
         }
-        const double e = wrms<TEAM>(sm + L.err, sm + L.yn, sm + L.y1, M.n, P.rtol, P.atol, sm + L.red, lane);
+        const double e = wrms<TEAM>(W.err, W.yn, W.y1, M.n, P.rtol, P.atol, W.red, lane);
         double fac = e > 0.0 ? 0.9 * pow(e, expo) : 5.0;
         fac = fmin(5.0, fmax(0.2, fac));
         if (e <= 1.0) {
-            copy_vec<TEAM>(sm + L.yn, sm + L.y1, M.n, lane);
+            copy_vec<TEAM>(W.yn, W.y1, M.n, lane);
             t = last ? P.dt : t + hh;
             cnt.steps++;
         } else {
@@ -258,27 +295,24 @@ __device__ int integrate_adaptive(const DevMech& M, const Layout& L, const IntPa
     return CELL_OK;
 }
 
+// Load, integrate and store one cell of one task.
 template <int TEAM, class MT>
-__global__ void integrate_kernel(DevMech M, Layout L, IntParams P, int64_t N, double* __restrict__ T,
-                                 double* __restrict__ Yio, const double* __restrict__ p_or_rho,
-                                 int32_t* __restrict__ status, int32_t* __restrict__ stats) {
-    const int lane = team_lane<TEAM>();
-    const int64_t cell = team_cell<TEAM>();
-    if (cell >= N) return;
+__device__ void integrate_cell(const Task& tk, const Ws& W, const IntParams& P, int64_t cell,
+                               int lane) {
+    const DevMech& M = tk.M;
+    const int64_t N = tk.N;
     const int ns = M.ns, n = M.n;
-    double* sm = team_smem<TEAM>(L);
-    double* yn = sm + L.yn;
-    double* red = sm + L.red;
+    double* yn = W.yn;
     // load and unpack: C_i = rho Y_i / W_i
-    const double T0 = T[cell];
-    const double pr = p_or_rho[cell];
+    const double T0 = tk.T[cell];
+    const double pr = tk.p[cell];
     double ysum = 0.0;
     for (int i = lane; i < ns; i += TEAM) {
-        const double Yi = Yio[(int64_t)i * N + cell];
+        const double Yi = tk.Y[(int64_t)i * N + cell];
         yn[1 + i] = Yi;
         ysum = fma(Yi, __ldg(M.invW + i), ysum);
     }
-    ysum = team_sum<TEAM>(ysum, red);
+    ysum = team_sum<TEAM>(ysum, W.red);
     const double rho = P.reactor == R_CONV ? pr : pr / (kR * T0 * ysum);
     bool fin = isfinite(T0);
     for (int i = lane; i < ns; i += TEAM) {
@@ -288,57 +322,131 @@ __global__ void integrate_kernel(DevMech M, Layout L, IntParams P, int64_t N, do
     }
     if (lane == 0) yn[0] = T0;
     team_sync<TEAM>();
-    fin = !team_any<TEAM>(!fin, red);
+    fin = !team_any<TEAM>(!fin, W.red);
     Counters cnt = {0, 0, 0, 0};
     int st;
     if (!fin) {
         st = CELL_NONFINITE;
     } else {
-        st = P.adaptive ? integrate_adaptive<TEAM, MT>(M, L, P, sm, cnt, lane)
-                        : integrate_fixed<TEAM, MT>(M, L, P, sm, cnt, lane);
+        st = P.adaptive ? integrate_adaptive<TEAM, MT>(M, W, P, cnt, lane)
+                        : integrate_fixed<TEAM, MT>(M, W, P, cnt, lane);
         bool bad = false;
         for (int i = lane; i < n; i += TEAM) bad |= !isfinite(yn[i]);
-        if (team_any<TEAM>(bad, red) && st == CELL_OK) st = CELL_NONFINITE;
+        if (team_any<TEAM>(bad, W.red) && st == CELL_OK) st = CELL_NONFINITE;
     }
     // store: T, Y_i = W_i C_i / sum W_j C_j (the input is kept for non-finite cells)
     if (st != CELL_NONFINITE) {
         double ms = 0.0;
         for (int i = lane; i < ns; i += TEAM) ms = fma(__ldg(M.W + i), yn[1 + i], ms);
-        const double inv = 1.0 / team_sum<TEAM>(ms, red);
-        for (int i = lane; i < ns; i += TEAM) Yio[(int64_t)i * N + cell] = __ldg(M.W + i) * yn[1 + i] * inv;
-        if (lane == 0) T[cell] = yn[0];
+        const double inv = 1.0 / team_sum<TEAM>(ms, W.red);
+        for (int i = lane; i < ns; i += TEAM) tk.Y[(int64_t)i * N + cell] = __ldg(M.W + i) * yn[1 + i] * inv;
+        if (lane == 0) tk.T[cell] = yn[0];
     }
     if (lane == 0) {
-        if (status) status[cell] = st;
-        if (stats) {
-            stats[cell] = cnt.steps;
-            stats[N + cell] = cnt.rejects;
-            stats[2 * N + cell] = cnt.newton;
-            stats[3 * N + cell] = cnt.lu;
+        if (tk.status) tk.status[cell] = st;
+        if (tk.stats) {
+            tk.stats[cell] = cnt.steps;
+            tk.stats[N + cell] = cnt.rejects;
+            tk.stats[2 * N + cell] = cnt.newton;
+            tk.stats[3 * N + cell] = cnt.lu;
         }
+    }
+    team_sync<TEAM>();
+}
+
+template <int TEAM, class MT>
+__global__ void integrate_kernel(Tasks tasks, IntParams P, int sstride, double* gscratch,
+                                 int64_t gstride, unsigned long long* counter) {
+    extern __shared__ double smem_all[];
+    const TeamPos<TEAM> tp;
+    double* sbase = smem_all + (size_t)tp.tib * sstride;
+    double* gbase = gscratch ? gscratch + tp.id * gstride : nullptr;
+    for (int64_t g = first_cell<TEAM>(counter, tp.id, tp.lane); g < tasks.total;
+         g = next_cell<TEAM>(counter, g, tp.count, tp.lane)) {
+        int k = 0;
+        while (k + 1 < tasks.count && g >= tasks.t[k + 1].first) ++k;
+        const Task& tk = tasks.t[k];
+        const Ws W = make_ws(tk.L, sbase, gbase);
+        integrate_cell<TEAM, MT>(tk, W, P, g - tk.first, tp.lane);
     }
 }
 
 // ---------------------------------------------------------------------------
-// launchers: teams_per_block teams of TEAM threads (TEAM > 32: one per block)
+// launchers
 
-static cudaError_t prepare(const void* fn, size_t smem) {
+static cudaError_t set_smem(const void* fn, size_t smem) {
     if (smem > 48 * 1024)
         return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return cudaSuccess;
 }
 
-template <int TEAM, class K, class... Args>
-static cudaError_t launch_team(K kernel, const Layout& L, int tpb, int64_t N, cudaStream_t st,
-                               Args... args) {
-    if (TEAM > 32) tpb = 1;
-    const size_t smem = (size_t)tpb * L.total * sizeof(double);
-    cudaError_t e = prepare((const void*)kernel, smem);
+// Blocks that keep every SM full (persistent launches).
+static cudaError_t resident_blocks(const void* fn, int threads, size_t smem, int64_t* out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (N + tpb - 1) / tpb;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    kernel<<<(unsigned)blocks, TEAM * tpb, smem, st>>>(args...);
-    return cudaGetLastError();
+    *out = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Global scratch slots (one per team) and the work counter, allocated
+// stream-ordered for this launch and released after it.
+struct LaunchMem {
+    double* gscratch = nullptr;
+    unsigned long long* counter = nullptr;
+};
+
+static cudaError_t get_mem(int64_t teams, int64_t gstride, bool need_counter, cudaStream_t st,
+                           LaunchMem& m) {
+    cudaError_t e;
+    if (gstride) {
+        void* p = nullptr;
+        if ((e = cudaMallocAsync(&p, (size_t)(teams * gstride) * sizeof(double), st)) != cudaSuccess)
+            return e;
+        m.gscratch = static_cast<double*>(p);
+    }
+    if (need_counter) {
+        void* p = nullptr;
+        if ((e = cudaMallocAsync(&p, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        m.counter = static_cast<unsigned long long*>(p);
+        return cudaMemsetAsync(m.counter, 0, sizeof(unsigned long long), st);
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t put_mem(LaunchMem& m, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (m.gscratch) e = cudaFreeAsync(m.gscratch, st);
+    if (m.counter && e == cudaSuccess) e = cudaFreeAsync(m.counter, st);
+    return e;
+}
+
+template <int TEAM, class K>
+static cudaError_t launch_eval(K kernel, const DevMech& M, const Layout& L, int tpb, int reactor,
+                               int64_t N, const double* T, const double* C, double* out,
+                               cudaStream_t st) {
+    if (TEAM > 32) tpb = 1;
+    const size_t smem = (size_t)tpb * L.stotal * sizeof(double);
+    cudaError_t e = set_smem((const void*)kernel, smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (N + tpb - 1) / tpb;
+    const int64_t gstride = round_up(L.gtotal, 32);
+    if (gstride) {
+        int64_t res = 0;
+        if ((e = resident_blocks((const void*)kernel, TEAM * tpb, smem, &res)) != cudaSuccess) return e;
+        blocks = blocks < res ? blocks : res;
+    }
+    if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;   // the cell loop covers the rest
+    LaunchMem mem;
+    if ((e = get_mem(blocks * tpb, gstride, false, st, mem)) != cudaSuccess) return e;
+    kernel<<<(unsigned)blocks, TEAM * tpb, smem, st>>>(M, L, reactor, N, T, C, out, mem.gscratch, gstride);
+    e = cudaGetLastError();
+    cudaError_t e2 = put_mem(mem, st);
+    return e != cudaSuccess ? e : e2;
 }
 
 #define CG_DISPATCH_TEAM(team, CALL)                         \
@@ -352,14 +460,14 @@ static cudaError_t launch_team(K kernel, const Layout& L, int tpb, int64_t N, cu
 
 cudaError_t launch_eval_rates(const DevMech& M, const Layout& L, int tpb, int reactor, int64_t N,
                               const double* T, const double* C, double* S, cudaStream_t st) {
-#define CALL(TM) launch_team<TM>(eval_rates_kernel<TM>, L, tpb, N, st, M, L, reactor, N, T, C, S)
+#define CALL(TM) launch_eval<TM>(eval_rates_kernel<TM>, M, L, tpb, reactor, N, T, C, S, st)
     CG_DISPATCH_TEAM(M.team, CALL)
 #undef CALL
 }
 
 cudaError_t launch_eval_jacobian(const DevMech& M, const Layout& L, int tpb, int reactor, int64_t N,
                                  const double* T, const double* C, double* J, cudaStream_t st) {
-#define CALL(TM) launch_team<TM>(eval_jacobian_kernel<TM>, L, tpb, N, st, M, L, reactor, N, T, C, J)
+#define CALL(TM) launch_eval<TM>(eval_jacobian_kernel<TM>, M, L, tpb, reactor, N, T, C, J, st)
     CG_DISPATCH_TEAM(M.team, CALL)
 #undef CALL
 }
@@ -368,22 +476,52 @@ cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const d
                                const double* Y, double* T, int iters, cudaStream_t st) {
     const int wpb = 4;
     const int64_t blocks = (N + wpb - 1) / wpb;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     temperature_kernel<<<(unsigned)blocks, 32 * wpb, 0, st>>>(M, reactor, N, e, Y, T, iters);
     return cudaGetLastError();
 }
 
-cudaError_t launch_integrate(const DevMech& M, const Layout& L, const IntParams& P, int tpb,
-                             int64_t N, double* T, double* Y, const double* p_or_rho,
-                             int32_t* status, int32_t* stats, cudaStream_t st) {
+template <int TEAM, class MT>
+static cudaError_t launch_integrate_t(const Tasks& tasks, const IntParams& P, int tpb, bool persistent,
+                                      cudaStream_t st) {
+    if (TEAM > 32) tpb = 1;
+    int sstride = 0;
+    int64_t gstride = 0;
+    for (int k = 0; k < tasks.count; ++k) {
+        sstride = sstride > tasks.t[k].L.stotal ? sstride : tasks.t[k].L.stotal;
+        gstride = gstride > tasks.t[k].L.gtotal ? gstride : tasks.t[k].L.gtotal;
+    }
+    gstride = round_up(gstride, 32);   // 256-byte aligned slots
+    const void* fn = (const void*)integrate_kernel<TEAM, MT>;
+    const size_t smem = (size_t)tpb * sstride * sizeof(double);
+    cudaError_t e = set_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (tasks.total + tpb - 1) / tpb;
+    const bool queue = persistent || gstride > 0;
+    if (queue) {
+        int64_t res = 0;
+        if ((e = resident_blocks(fn, TEAM * tpb, smem, &res)) != cudaSuccess) return e;
+        blocks = blocks < res ? blocks : res;
+    }
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    LaunchMem mem;
+    if ((e = get_mem(blocks * tpb, gstride, queue, st, mem)) != cudaSuccess) return e;
+    integrate_kernel<TEAM, MT><<<(unsigned)blocks, TEAM * tpb, smem, st>>>(tasks, P, sstride, mem.gscratch,
+                                                                           gstride, mem.counter);
+    e = cudaGetLastError();
+    cudaError_t e2 = put_mem(mem, st);
+    return e != cudaSuccess ? e : e2;
+}
+
+cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, int tpb, bool persistent,
+                             cudaStream_t st) {
     if (P.precision == 1) {
-#define CALL(TM) \
-    launch_team<TM>(integrate_kernel<TM, float>, L, tpb, N, st, M, L, P, N, T, Y, p_or_rho, status, stats)
-        CG_DISPATCH_TEAM(M.team, CALL)
+#define CALL(TM) launch_integrate_t<TM, float>(tasks, P, tpb, persistent, st)
+        CG_DISPATCH_TEAM(team, CALL)
 #undef CALL
     }
-#define CALL(TM) \
-    launch_team<TM>(integrate_kernel<TM, double>, L, tpb, N, st, M, L, P, N, T, Y, p_or_rho, status, stats)
-    CG_DISPATCH_TEAM(M.team, CALL)
+#define CALL(TM) launch_integrate_t<TM, double>(tasks, P, tpb, persistent, st)
+    CG_DISPATCH_TEAM(team, CALL)
 #undef CALL
 }
 

@@ -1,0 +1,151 @@
+"""GPU: work distribution, global-scratch placement, batched launches of
+several mechanisms, and the 160-species mechanism whose Newton matrix
+fills shared memory (its other arrays live in global scratch).
+
+Where the arithmetic of a cell is unchanged (persistent vs one slot per
+cell, shared vs global placement, batched vs separate launches) the results
+must be bit-identical."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_10005_gb300 import chemgb, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+BE = dict(method=chemgb.CG_BE, adaptive=0, dt=1e-5, rtol=1e-10, atol=1e-16, newton_tol=1.0,
+          max_newton=20, max_halvings=10, reactor=chemgb.CG_CONP)
+ADAPT = dict(method=chemgb.CG_SDIRK4, adaptive=1, dt=1e-6, rtol=1e-6, atol=1e-12, newton_tol=0.03,
+             max_newton=7, reactor=chemgb.CG_CONP)
+
+
+def d(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def run(h, o, T, Y, p):
+    N = len(T)
+    Tt, Yt, pt = d(T), d(Y.T), d(p)
+    st = torch.empty(N, dtype=torch.int32, device=DEV)
+    stats = torch.empty((4, N), dtype=torch.int32, device=DEV)
+    chemgb.cg_integrate(h, o, Tt, Yt, pt, st, stats)
+    torch.cuda.synchronize()
+    return Tt.cpu().numpy(), Yt.cpu().numpy().T, st.cpu().numpy(), stats.cpu().numpy().T
+
+
+def same(a, b):
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+@pytest.fixture(scope="module")
+def flame_cells(mechs):
+    m = mechs["ch4"]
+    T, Y, p = inputs.field_flames(m, 4096, seed=4)
+    idx = np.concatenate([np.arange(0, 4096, 64), np.arange(2420, 2460)])   # all regions + front
+    return T[idx], Y[idx], p[idx]
+
+
+def test_persistent_queue_is_bit_identical(mechs, flame_cells):
+    h = chemgb.cg_mech_create(mechs["ch4"])
+    T, Y, p = flame_cells
+    a = run(h, chemgb.make_opts(**ADAPT, persistent=0), T, Y, p)
+    b = run(h, chemgb.make_opts(**ADAPT, persistent=1), T, Y, p)
+    same(a, b)
+
+
+@pytest.mark.parametrize("limit", [40 * 1024, 16 * 1024, 4 * 1024])
+def test_global_scratch_placement_is_bit_identical(mechs, flame_cells, limit):
+    """Arrays moved to the global scratch slot compute the same numbers."""
+    h = chemgb.cg_mech_create(mechs["ch4"])
+    T, Y, p = flame_cells
+    o = chemgb.make_opts(**ADAPT)
+    a = run(h, o, T, Y, p)
+    chemgb.cg_mech_set_smem_limit(h, limit)
+    b = run(h, o, T, Y, p)
+    same(a, b)
+    o32 = chemgb.make_opts(**ADAPT, precision=chemgb.CG_FP32LU)
+    c = run(h, o32, T, Y, p)
+    chemgb.cg_mech_set_smem_limit(h, 227 * 1024)
+    same(c, run(h, o32, T, Y, p))
+
+
+def test_batch_of_two_mechanisms_matches_separate_launches(mechs, flame_cells):
+    h9 = chemgb.cg_mech_create(mechs["h2"])
+    h53 = chemgb.cg_mech_create(mechs["ch4"])
+    chemgb.cg_mech_set_launch(h9, 64, 1)        # one team size for the batch
+    T9, Y9, p9 = inputs.field_reactor(mechs["h2"], 300, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=5)
+    T53, Y53, p53 = flame_cells
+    o = chemgb.make_opts(**ADAPT)
+    a9 = run(h9, o, T9, Y9, p9)
+    a53 = run(h53, o, T53, Y53, p53)
+    Ts = [d(T9), d(T53)]
+    Ys = [d(Y9.T), d(Y53.T)]
+    ps = [d(p9), d(p53)]
+    sts = [torch.empty(len(T9), dtype=torch.int32, device=DEV), torch.empty(len(T53), dtype=torch.int32, device=DEV)]
+    sas = [torch.empty((4, len(T9)), dtype=torch.int32, device=DEV),
+           torch.empty((4, len(T53)), dtype=torch.int32, device=DEV)]
+    chemgb.cg_integrate_batch([h9, h53], o, Ts, Ys, ps, sts, sas)
+    torch.cuda.synchronize()
+    same(a9, (Ts[0].cpu().numpy(), Ys[0].cpu().numpy().T, sts[0].cpu().numpy(), sas[0].cpu().numpy().T))
+    same(a53, (Ts[1].cpu().numpy(), Ys[1].cpu().numpy().T, sts[1].cpu().numpy(), sas[1].cpu().numpy().T))
+    with pytest.raises(chemgb.ChemgbError):
+        chemgb.cg_mech_set_launch(h9, 32, 4)
+        chemgb.cg_integrate_batch([h9, h53], o, Ts, Ys, ps)
+
+
+# ---------------------------------------------------------------------------
+# 160 species, 900 reactions
+
+
+@pytest.fixture(scope="module")
+def big():
+    m = inputs.gen_mechanism("c7")
+    return m, oracle.RefMech(m), chemgb.cg_mech_create(m)
+
+
+def test_big_mechanism_rates_and_jacobian(big):
+    m, r, h = big
+    T, C, p = inputs.random_states(m, 9, seed=31)
+    S = torch.empty((m.ns + 1, 9), dtype=torch.float64, device=DEV)
+    chemgb.cg_eval_rates(h, chemgb.CG_CONP, d(T), d(C.T), S)
+    J = torch.empty((9, m.ns + 1, m.ns + 1), dtype=torch.float64, device=DEV)
+    chemgb.cg_eval_jacobian(h, chemgb.CG_CONP, d(T), d(C.T), J)
+    torch.cuda.synchronize()
+    So = r.source(T, C, oracle.CONP)
+    Jo = r.jacobian(T, C, oracle.CONP)
+    Sg = S.cpu().numpy().T
+    Jg = J.cpu().numpy()
+    rowmax = np.abs(Jo).max(axis=2, keepdims=True)
+    assert np.all(np.abs(Jg - Jo) <= 1e-10 * np.abs(Jo) + 1e-12 * rowmax)
+    scale = np.abs(So).max(axis=1, keepdims=True)
+    assert np.all(np.abs(Sg - So) <= 1e-10 * np.abs(So) + 1e-12 * scale)
+
+
+def test_big_mechanism_integration(big):
+    """Fixed-step backward Euler (Newton to 1e-10 of the state) on 12 cells of
+    the large-mechanism field (T in U[700, 1600] K, p in U[20, 40] atm,
+    phi in U[0.5, 1.5]) and adaptive SDIRK-4 on 6, in FP64 and with the FP32
+    Newton matrix."""
+    m, r, h = big
+    T, Y, p = inputs.field_reactor(m, 12, (700, 1600), (20, 40), (0.5, 1.5), "C7H16", seed=0)
+    o = dict(BE, dt=1e-6)
+    To, Yo, so, sto = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, stg = run(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    np.testing.assert_allclose(Tg, To, rtol=1e-10)
+    assert np.all(np.abs(Yg - Yo) <= 1e-10 * np.abs(Yo) + 1e-22)
+    Tg2, Yg2, sg2, stg2 = run(h, chemgb.make_opts(**o, precision=chemgb.CG_FP32LU), T, Y, p)
+    np.testing.assert_array_equal(sg2, so)
+    path = np.all(stg2[:, :2] == sto[:, :2], axis=1)   # same halving path as the oracle
+    assert path.mean() >= 0.75
+    np.testing.assert_allclose(Tg2[path], To[path], rtol=1e-8)
+    np.testing.assert_allclose(Tg2, To, rtol=1e-4)        # other paths: within backward Euler's error
+    a = dict(ADAPT)
+    To, Yo, so, _ = r.integrate(T[:6], Y[:6], p[:6], a, nthreads=6)
+    Tg, Yg, sg, _ = run(h, chemgb.make_opts(**a), T[:6], Y[:6], p[:6])
+    np.testing.assert_array_equal(sg, so)
+    np.testing.assert_allclose(Tg, To, rtol=1e-6)
+    assert np.max(np.abs(Yg - Yo)) < 1e-6

@@ -216,6 +216,28 @@ cg_status cg_integrate_host(const cg_mech *mech, const cg_integrate_opts *opts, 
                             double *T, double *Y, const double *p_or_rho, int32_t *cell_status,
                             int32_t *cell_stats);
 
+/* cg_integrate for callers that cannot allocate device memory while they
+ * run: a host code whose own memory manager owns the device heap, or a
+ * solver that must not enter an allocator inside its time step. The paper
+ * has no counterpart; this is a deployment variant of cg_integrate with the
+ * same arguments and results. It always uses the persistent work-stealing
+ * launch, and calls no cudaMalloc, cudaFree or other allocating routine:
+ * the per-team scratch slots and the work counter live in one fixed 32 MiB
+ * device array inside the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; each
+ *     call clears the work counter on its stream. Calls whose work overlaps
+ *     on the GPU (other streams, other threads) race on the array: serialise
+ *     them.
+ *   - Errors: as cg_integrate, and CG_ECAPACITY when one cell's arrays need
+ *     more scratch than the array holds (the message gives both sizes). */
+cg_status cg_integrate_noalloc(const cg_mech *mech, const cg_integrate_opts *opts, int64_t N, double *T,
+                               double *Y, const double *p_or_rho, int32_t *cell_status,
+                               int32_t *cell_stats, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *cg_last_error(void);
 

@@ -49,7 +49,7 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_mech_set_launch", "cg_mech_get_launch", "cg_mech_set_smem_limit",
             "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
-            "cg_last_error")
+            "cg_integrate_noalloc", "cg_last_error")
 
 
 def library_path() -> str:
@@ -77,6 +77,7 @@ def load(build_if_missing: bool = False):
     lib.cg_mech_get_launch.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.cg_mech_set_smem_limit.argtypes = [P, L]
     lib.cg_integrate_batch.argtypes = [I, P, P, P, P, P, P, P, ctypes.POINTER(cg_integrate_opts), P]
+    lib.cg_integrate_noalloc.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, P]
     lib.cg_eval_rates.argtypes = [P, I, L, P, P, P, P]
     lib.cg_eval_jacobian.argtypes = [P, I, L, P, P, P, P]
     lib.cg_temperature_from_energy.argtypes = [P, I, L, P, P, P, I, P]
@@ -177,6 +178,15 @@ def cg_integrate(h, opts, T, Y, p_or_rho, status=None, stats=None, stream=None):
     _check(load().cg_integrate(h.ptr, ctypes.byref(opts), T.shape[0], _dev(T), _dev(Y), _dev(p_or_rho),
                                None if status is None else _dev(status, "int32"),
                                None if stats is None else _dev(stats, "int32"), _stream(stream)))
+
+
+def cg_integrate_noalloc(h, opts, T, Y, p_or_rho, status=None, stats=None, stream=None):
+    """cg_integrate through the library's fixed device array instead of any
+    allocation (for callers that cannot allocate device memory while they
+    run; see include/chemgb.h for its limits)."""
+    _check(load().cg_integrate_noalloc(h.ptr, ctypes.byref(opts), T.shape[0], _dev(T), _dev(Y),
+                                       _dev(p_or_rho), None if status is None else _dev(status, "int32"),
+                                       None if stats is None else _dev(stats, "int32"), _stream(stream)))
 
 
 def cg_mech_set_smem_limit(h, nbytes: int):

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -843,3 +844,73 @@ cg_status cg_integrate_host(const cg_mech* mc, const cg_integrate_opts* o, int64
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Integration without any allocation, for callers that cannot allocate
+// device memory while they run (for example a host code whose own memory
+// manager owns the device heap, or a solver that must not enter the
+// allocator inside its time step). The per-team scratch slots and the work
+// counter live in one fixed array that every GPU loading this library holds
+// until the process exits.
+
+namespace {
+
+constexpr size_t kNoAllocBytes = 32u << 20;                      // 32 MiB
+constexpr int64_t kNoAllocDoubles = (int64_t)(kNoAllocBytes / sizeof(double));
+constexpr int64_t kNoAllocCounterDoubles = 32;                  // first 256 bytes: the work counter
+
+static __device__ __align__(256) double g_noalloc[kNoAllocDoubles];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[64] = {};   // device address of g_noalloc, per device ordinal
+
+// Device address of the array on the current device, looked up once per
+// device (a host-side reference to g_noalloc is not a device address).
+cg_status noalloc_array(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(CG_EUNSUPPORTED, "device ordinal %d above 63", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (no-alloc scratch)");
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return CG_OK;
+}
+
+}  // namespace
+
+extern "C" cg_status cg_integrate_noalloc(const cg_mech* m, const cg_integrate_opts* o, int64_t N,
+                                          double* T, double* Y, const double* p_or_rho,
+                                          int32_t* cell_status, int32_t* cell_stats, void* stream) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    IntParams P;
+    cg_status st = make_params(o, P);
+    if (st != CG_OK) return st;
+    if (N < 0) return fail(CG_EINVAL, "N < 0");
+    if (N == 0) return CG_OK;
+    if (!T || !Y || !p_or_rho) return fail(CG_EINVAL, "NULL array");
+    cg::Tasks tasks;
+    tasks.count = 1;
+    tasks.total = N;
+    tasks.t[0] = make_task(m, P, N, 0, T, Y, p_or_rho, cell_status, cell_stats);
+    const int64_t slot = cg::integrate_slot_doubles(tasks) * (m->dm.team > 32 ? 1 : m->tpb);
+    const int64_t avail = kNoAllocDoubles - kNoAllocCounterDoubles;
+    if (slot > avail)
+        return fail(CG_ECAPACITY,
+                    "one cell of this mechanism needs %lld bytes of scratch; cg_integrate_noalloc has %lld "
+                    "(raise cg_mech_set_smem_limit or use cg_integrate)",
+                    (long long)(slot * (int64_t)sizeof(double)), (long long)(avail * (int64_t)sizeof(double)));
+    double* base = nullptr;
+    if ((st = noalloc_array(&base)) != CG_OK) return st;
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(base);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (work counter)");
+    e = cg::launch_integrate_on(tasks, P, m->dm.team, m->tpb, base + kNoAllocCounterDoubles, avail, counter,
+                                (cudaStream_t)stream);
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch (no-alloc)");
+}

@@ -39,5 +39,11 @@ cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const d
 // the work counter (always used when a cell needs global scratch).
 cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, int tpb, bool persistent,
                              cudaStream_t st);
+// Persistent launch on caller-provided scratch (scratch_doubles doubles) and
+// a work counter that is zero on the stream when the kernel starts.
+// cudaErrorMemoryAllocation: not even one team's slot fits in the scratch.
+cudaError_t launch_integrate_on(const Tasks& tasks, const IntParams& P, int team, int tpb, double* scratch,
+                                int64_t scratch_doubles, unsigned long long* counter, cudaStream_t st);
+int64_t integrate_slot_doubles(const Tasks& tasks);
 
 }  // namespace cg

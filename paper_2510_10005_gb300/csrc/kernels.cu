@@ -513,6 +513,60 @@ static cudaError_t launch_integrate_t(const Tasks& tasks, const IntParams& P, in
     return e != cudaSuccess ? e : e2;
 }
 
+// Persistent launch on caller-provided memory: `scratch` holds
+// scratch_doubles doubles for the teams' slots, `counter` must be zero when
+// the kernel starts (the caller clears it on the stream). The grid is
+// limited so that every team's slot fits. Allocates nothing.
+template <int TEAM, class MT>
+static cudaError_t launch_integrate_on_t(const Tasks& tasks, const IntParams& P, int tpb, double* scratch,
+                                         int64_t scratch_doubles, unsigned long long* counter,
+                                         cudaStream_t st) {
+    if (TEAM > 32) tpb = 1;
+    int sstride = 0;
+    int64_t gstride = 0;
+    for (int k = 0; k < tasks.count; ++k) {
+        sstride = sstride > tasks.t[k].L.stotal ? sstride : tasks.t[k].L.stotal;
+        gstride = gstride > tasks.t[k].L.gtotal ? gstride : tasks.t[k].L.gtotal;
+    }
+    gstride = round_up(gstride, 32);
+    const void* fn = (const void*)integrate_kernel<TEAM, MT>;
+    const size_t smem = (size_t)tpb * sstride * sizeof(double);
+    cudaError_t e = set_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (tasks.total + tpb - 1) / tpb, res = 0;
+    if ((e = resident_blocks(fn, TEAM * tpb, smem, &res)) != cudaSuccess) return e;
+    blocks = blocks < res ? blocks : res;
+    if (gstride) {
+        const int64_t fit = scratch_doubles / (gstride * tpb);   // blocks whose slots fit
+        if (fit < 1) return cudaErrorMemoryAllocation;
+        blocks = blocks < fit ? blocks : fit;
+    }
+    integrate_kernel<TEAM, MT><<<(unsigned)blocks, TEAM * tpb, smem, st>>>(tasks, P, sstride,
+                                                                           gstride ? scratch : nullptr,
+                                                                           gstride, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_on(const Tasks& tasks, const IntParams& P, int team, int tpb, double* scratch,
+                                int64_t scratch_doubles, unsigned long long* counter, cudaStream_t st) {
+    if (P.precision == 1) {
+#define CALL(TM) launch_integrate_on_t<TM, float>(tasks, P, tpb, scratch, scratch_doubles, counter, st)
+        CG_DISPATCH_TEAM(team, CALL)
+#undef CALL
+    }
+#define CALL(TM) launch_integrate_on_t<TM, double>(tasks, P, tpb, scratch, scratch_doubles, counter, st)
+    CG_DISPATCH_TEAM(team, CALL)
+#undef CALL
+}
+
+// Shared-memory and scratch need of one slot (doubles), for callers that
+// bring their own memory.
+int64_t integrate_slot_doubles(const Tasks& tasks) {
+    int64_t g = 0;
+    for (int k = 0; k < tasks.count; ++k) g = g > tasks.t[k].L.gtotal ? g : tasks.t[k].L.gtotal;
+    return round_up(g, 32);
+}
+
 cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, int tpb, bool persistent,
                              cudaStream_t st) {
     if (P.precision == 1) {

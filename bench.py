@@ -1,20 +1,30 @@
 """Benchmark: cells integrated per second over dt on the GPU.
 
-Workload (N = 1): the 53-species / 325-reaction synthetic methane-shaped
-mechanism, 1,048,576 cells of the 1-D flame-like field (60% unburnt,
-10% front, 30% burnt; p 1-10 atm), constant pressure, SDIRK-4 with error
-control (rtol 1e-6, atol 1e-12) over dt = 1e-6 s, FP64. One step = one
-cg_integrate call over all cells (after a device-to-device restore of the
-initial state, which is part of the step). The per-cell state is
-1,048,576 x 55 doubles = 461 MB, larger than the 129 MB L2, so no L2 flush
-is needed between steps.
+Default workload (--config 2, N = 1): the 53-species / 325-reaction
+synthetic methane-shaped mechanism, 1,048,576 cells of the 1-D flame-like
+field (60% unburnt, 10% front, 30% burnt; p 1-10 atm), constant pressure,
+SDIRK-4 with error control (rtol 1e-6, atol 1e-12) over dt = 1e-6 s, FP64.
+One step = one cg_integrate call over all cells after a device-to-device
+restore of the initial state (part of the step). The per-cell state is
+1,048,576 x 55 doubles = 461 MB, larger than the 129 MB L2, so no L2 flush is
+needed between steps.
 
-Prints one JSON line (see the keys below). --impl reference times the FP64
-CPU oracle on the host cores instead.
+Other workloads (reported beside the default line):
+  --config 1  9 species, one backward-Euler step of 1e-5 s, 4096 cells
+  --config 3  53 + 9 species in ONE persistent work-stealing launch,
+              1,048,576 heavy-tailed cells each (90% frozen, 5% burnt,
+              5% reacting, randomly interleaved), FP32 Newton matrix,
+              autotuned launch shape, replayed from a captured CUDA graph;
+              error against the FP64 oracle on a sample
+  --config 5  160 species / 900 reactions, T in U[700, 1600] K,
+              p in U[20, 40] atm, adaptive SDIRK-4 (use --cells for a subset)
 
-Multi-GPU (torchrun): every rank integrates its own 1,048,576 cells (the
-cells of a field are independent; no collective on the data path);
-value = all cells / max-over-ranks time ("scaling": "weak").
+Prints one JSON line. --impl reference times the FP64 CPU oracle on the
+host cores instead (a bounded sample of the same workload).
+
+Multi-GPU (torchrun): every rank integrates its own cells (cells are
+independent; no collective on the data path); value = all cells /
+max-over-ranks time ("scaling": "weak").
 """
 from __future__ import annotations
 
@@ -32,27 +42,43 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CELLS = 1 << 20
-OPTS = dict(method=2, reactor=1, adaptive=1, dt=1e-6, rtol=1e-6, atol=1e-12, newton_tol=0.03,
-            max_newton=7, max_steps=100000, max_halvings=10, err_filter=1, neg_tol=1e-6)
 METRIC = "cells integrated/s over dt"
-WORKLOAD = ("53-species/325-reaction synthetic methane-shaped mechanism, 1,048,576-cell 1-D "
-            "flame-like field, constant pressure, adaptive SDIRK-4 rtol 1e-6 atol 1e-12, dt 1e-6 s")
+SDIRK4 = dict(method=2, reactor=1, adaptive=1, dt=1e-6, rtol=1e-6, atol=1e-12, newton_tol=0.03,
+              max_newton=7, max_steps=100000, max_halvings=10, err_filter=1, neg_tol=1e-6)
+BE = dict(method=0, reactor=1, adaptive=0, dt=1e-5, rtol=1e-10, atol=1e-16, newton_tol=1.0,
+          max_newton=20, max_halvings=10, neg_tol=1e-6)
+
+CONFIGS = {
+    1: dict(cells=4096, opts=BE, precision=0,
+            workload="9-species/21-reaction synthetic H2/O2 mechanism, 4096 cells, T0 U[1000,1500] K, "
+                     "1 atm, phi U[0.5,2], constant pressure, one backward-Euler step of 1e-5 s (+halvings)"),
+    2: dict(cells=1 << 20, opts=SDIRK4, precision=0,
+            workload="53-species/325-reaction synthetic methane-shaped mechanism, 1,048,576-cell 1-D "
+                     "flame-like field, constant pressure, adaptive SDIRK-4 rtol 1e-6 atol 1e-12, dt 1e-6 s"),
+    3: dict(cells=1 << 20, opts=SDIRK4, precision=1,
+            workload="53-species + 9-species mechanisms in one persistent work-stealing launch, "
+                     "2 x 1,048,576 heavy-tailed cells (90% frozen, 5% burnt, 5% reacting, interleaved), "
+                     "FP32 Newton matrix, autotuned, CUDA graph, adaptive SDIRK-4 rtol 1e-6, dt 1e-6 s"),
+    5: dict(cells=1 << 18, opts=SDIRK4, precision=0,
+            workload="160-species/900-reaction synthetic n-heptane-shaped mechanism, T U[700,1600] K, "
+                     "p U[20,40] atm, phi U[0.5,1.5], constant pressure, adaptive SDIRK-4 rtol 1e-6, dt 1e-6 s"),
+}
 
 
-def algorithmic_flops_per_newton(n_species: int, n_reactions: int, j_terms: int) -> float:
-    """FP64 flops of one Newton iteration of one cell:
-    LU 2n^3/3, two triangular solves 2n^2, Newton matrix 2n^2, temperature
-    row and constant-pressure correction 4n^2, Jacobian terms 2 per term,
-    rates 30 per reaction, thermo 40 per species. Transcendentals excluded."""
+def algorithmic_flops_per_newton(n_species: int, n_reactions: int, j_terms: int, fp32_lu: bool) -> float:
+    """FP64 flops of one Newton iteration of one cell: LU 2n^3/3 (FP64 mode
+    only), two triangular solves 2n^2, Newton matrix 2n^2, temperature row
+    and constant-pressure correction 4n^2, Jacobian terms 2 per term, rates
+    30 per reaction, thermo 40 per species. Transcendentals excluded."""
     n = n_species + 1
-    return 2.0 * n**3 / 3 + 8.0 * n * n + 2.0 * j_terms + 30.0 * n_reactions + 40.0 * n_species
+    lu = 0.0 if fp32_lu else 2.0 * n**3 / 3
+    return lu + 8.0 * n * n + 2.0 * j_terms + 30.0 * n_reactions + 40.0 * n_species
 
 
 def j_term_count(mech) -> int:
-    """Number of sparse Jacobian terms the assembly schedule adds (same rule
-    as the library: for every species with nonzero net coefficient in a
-    reaction, one temperature term, one per used slot, one per efficiency)."""
+    """Sparse Jacobian terms of the assembly schedule: for every species with
+    a nonzero net coefficient in a reaction, one temperature term, one per
+    used slot and one per efficiency."""
     total = 0
     for j in range(mech.nr):
         nu = {}
@@ -68,9 +94,9 @@ def j_term_count(mech) -> int:
 
 
 def fp64_peak(sm_count: int, sm_max_mhz: float) -> float:
-    """FP64 FMA pipe: 2 lanes per clock per SM on GB300 (measured: a
-    register-resident DFMA loop reaches 1.195e12 FLOP/s at 1987 MHz on 152
-    SMs = 3.96 FLOP/clk/SM), taken at the maximum SM clock."""
+    """FP64 FMA pipe: one unit per SM sub-partition retiring half a lane per
+    clock, 2 lanes (4 FLOP) per clock per SM (measured: 1.195e12 FLOP/s at
+    1987 MHz on 152 SMs), at the maximum SM clock."""
     return 4.0 * sm_count * sm_max_mhz * 1e6
 
 
@@ -80,7 +106,8 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
         self.idx = gpu_index
         self.proc = None
 
@@ -103,68 +130,103 @@ class ClockSampler:
     def summary(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = [[p.strip() for p in line.split(",")] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 9]
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        num = lambda v: v.replace(".", "").isdigit()
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for r in rows if num(r[2])]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_workload(seed: int = 0, cells: int = CELLS):
+# ---------------------------------------------------------------------------
+# workloads: list of (mechanism, T, Y, p)
+
+
+def make_workload(config: int, cells: int, seed: int = 0):
     from paper_2510_10005_gb300 import inputs
-    mech = inputs.gen_mechanism("ch4")
-    T, Y, p = inputs.field_flames(mech, cells, seed=seed)
-    return mech, T, Y, p
+    if config == 1:
+        m = inputs.gen_mechanism("h2")
+        T, Y, p = inputs.field_reactor(m, cells, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=seed)
+        return [(m, T, Y, p)]
+    if config == 2:
+        m = inputs.gen_mechanism("ch4")
+        T, Y, p = inputs.field_flames(m, cells, seed=seed)
+        return [(m, T, Y, p)]
+    if config == 3:
+        m53, m9 = inputs.gen_mechanism("ch4"), inputs.gen_mechanism("h2")
+        T, Y, p, _ = inputs.field_mixed(m53, cells, "CH4", seed=seed, argon=0.0093)
+        T9, Y9, p9, _ = inputs.field_mixed(m9, cells, "H2", seed=seed + 1000)
+        return [(m53, T, Y, p), (m9, T9, Y9, p9)]
+    if config == 5:
+        m = inputs.gen_mechanism("c7")
+        T, Y, p = inputs.field_reactor(m, cells, (700, 1600), (20, 40), (0.5, 1.5), "C7H16", seed=seed)
+        return [(m, T, Y, p)]
+    raise ValueError(config)
 
 
-def cpu_oracle_sample(mech, T, Y, p, n_sample: int, threads: int):
-    """Time the oracle on a stratified sample; returns (cells/s, seconds)."""
+def opts_dict(config: int, precision: int):
+    o = dict(CONFIGS[config]["opts"])
+    o["precision"] = precision
+    if config == 3:
+        o["persistent"] = 1
+    return o
+
+
+def oracle_opts(o: dict) -> dict:
+    return {k: v for k, v in o.items() if k not in ("precision", "persistent")}
+
+
+def cpu_oracle_sample(parts, opts, n_sample: int, threads: int):
+    """Time the oracle on an evenly spaced sample of every mechanism's cells
+    (shares in proportion to the cells); returns (cells/s, seconds, cells)."""
     import oracle
-    r = oracle.RefMech(mech)
-    idx = np.linspace(0, len(T) - 1, n_sample).astype(np.int64)
-    t0 = time.perf_counter()
-    r.integrate(T[idx], Y[idx], p[idx], OPTS, nthreads=threads)
-    el = time.perf_counter() - t0
-    return n_sample / el, el
+    total = sum(len(T) for _, T, _, _ in parts)
+    t, done = 0.0, 0
+    for m, T, Y, p in parts:
+        k = max(1, int(round(n_sample * len(T) / total)))
+        idx = np.linspace(0, len(T) - 1, k).astype(np.int64)
+        r = oracle.RefMech(m)
+        t0 = time.perf_counter()
+        r.integrate(T[idx], Y[idx], p[idx], oracle_opts(opts), nthreads=threads)
+        t += time.perf_counter() - t0
+        done += k
+    return done / t, t, done
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    mech, T, Y, p = make_workload()
+    cfg = CONFIGS[args.config]
+    parts = make_workload(args.config, args.cells or cfg["cells"])
+    opts = opts_dict(args.config, 0)
     threads = os.cpu_count() or 1
-    n_sample = args.ref_sample
     for _ in range(args.warmup):
-        cpu_oracle_sample(mech, T, Y, p, max(16, n_sample // 8), threads)
-    times = []
+        cpu_oracle_sample(parts, opts, max(16, args.ref_sample // 8), threads)
+    times, cells = [], 0
     for _ in range(args.steps):
-        v, el = cpu_oracle_sample(mech, T, Y, p, n_sample, threads)
+        v, el, k = cpu_oracle_sample(parts, opts, args.ref_sample, threads)
         times.append(el)
-    value = n_sample * args.steps / sum(times)
+        cells += k
+    value = cells / sum(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic", "config": {"workload": cfg["workload"], "config": args.config},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{n_sample} cells evenly spaced through the field, per step"},
+                         "sample": f"{args.ref_sample} cells evenly spaced through the field, per step"},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -178,28 +240,69 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group("nccl")
     dev = torch.device(f"cuda:{local}")
-    chemgb.load(build_if_missing=(rank == 0 and ws == 1))
+    torch.cuda.set_device(dev)
+    chemgb.load(build_if_missing=(ws == 1))
+    cfg = CONFIGS[args.config]
+    precision = cfg["precision"] if args.precision is None else args.precision
+    parts = make_workload(args.config, args.cells or cfg["cells"], seed=rank)
+    opts_d = opts_dict(args.config, precision)
+    opts = chemgb.make_opts(**opts_d)
+    stream = torch.cuda.Stream(dev)   # a side stream (graph capture needs one); all work goes there
+    torch.cuda.set_stream(stream)
 
-    mech, T, Y, p = make_workload(seed=rank, cells=args.cells)
-    h = chemgb.cg_mech_create(mech)
-    if args.team:
-        chemgb.cg_mech_set_launch(h, args.team, args.tpb)
-    opts = chemgb.make_opts(**OPTS, precision=args.precision)
-    N = len(T)
-    T0 = torch.tensor(T, dtype=torch.float64, device=dev)
-    Y0 = torch.tensor(np.ascontiguousarray(Y.T), dtype=torch.float64, device=dev)
-    P0 = torch.tensor(p, dtype=torch.float64, device=dev)
-    Tw, Yw = torch.empty_like(T0), torch.empty_like(Y0)
-    st = torch.empty(N, dtype=torch.int32, device=dev)
-    stats = torch.empty((4, N), dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    handles, bufs = [], []
+    for m, T, Y, p in parts:
+        h = chemgb.cg_mech_create(m)
+        if args.team:
+            chemgb.cg_mech_set_launch(h, args.team, args.tpb)
+        N = len(T)
+        b = dict(T0=torch.tensor(T, dtype=torch.float64, device=dev),
+                 Y0=torch.tensor(np.ascontiguousarray(Y.T), dtype=torch.float64, device=dev),
+                 P=torch.tensor(p, dtype=torch.float64, device=dev),
+                 st=torch.empty(N, dtype=torch.int32, device=dev),
+                 stats=torch.empty((4, N), dtype=torch.int32, device=dev))
+        b["T"], b["Y"] = torch.empty_like(b["T0"]), torch.empty_like(b["Y0"])
+        handles.append(h)
+        bufs.append(b)
+    N_total = sum(len(b["T0"]) for b in bufs)
 
-    def step():
-        Tw.copy_(T0)
-        Yw.copy_(Y0)
-        chemgb.cg_integrate(h, opts, Tw, Yw, P0, st, stats, stream=stream.cuda_stream)
+    tuned = None
+    if args.config == 3 and not args.team:
+        # autotune the launch shape on the dominant mechanism, then give the
+        # other one the same team size (one launch needs one team size)
+        k = min(16384, len(bufs[0]["T0"]))
+        sel = torch.linspace(0, len(bufs[0]["T0"]) - 1, k, device=dev).long()
+        ms = chemgb.cg_autotune(handles[0], opts, bufs[0]["T0"][sel].contiguous(),
+                                bufs[0]["Y0"][:, sel].contiguous(), bufs[0]["P"][sel].contiguous())
+        team, tpb = chemgb.cg_mech_get_launch(handles[0])
+        for h in handles[1:]:
+            chemgb.cg_mech_set_launch(h, team, tpb if team == 32 else 1)
+        tuned = {"team": team, "teams_per_block": tpb, "sample_ms": ms}
+
+    def integrate():
+        for b in bufs:
+            b["T"].copy_(b["T0"])
+            b["Y"].copy_(b["Y0"])
+        if len(handles) == 1:
+            b = bufs[0]
+            chemgb.cg_integrate(handles[0], opts, b["T"], b["Y"], b["P"], b["st"], b["stats"],
+                                stream=stream.cuda_stream)
+        else:
+            chemgb.cg_integrate_batch(handles, opts, [b["T"] for b in bufs], [b["Y"] for b in bufs],
+                                      [b["P"] for b in bufs], [b["st"] for b in bufs],
+                                      [b["stats"] for b in bufs], stream=stream.cuda_stream)
+
+    step = integrate
+    graph = None
+    if args.config == 3 and not args.no_graph:
+        integrate()                      # first call outside capture (kernel attributes, pools)
+        torch.cuda.synchronize(dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            integrate()
+        step = graph.replay
 
     def barrier():
         if ws > 1:
@@ -225,90 +328,116 @@ def run_gpu(args):
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = ws * N * args.steps / (ms * 1e-3)
-
-    st_h = st.cpu().numpy()
-    stats_h = stats.cpu().numpy()
-    newton = int(stats_h[2].astype(np.int64).sum())
-    jt = j_term_count(mech)
-    fpu = algorithmic_flops_per_newton(mech.ns, mech.nr, jt)
+    value = ws * N_total * args.steps / (ms * 1e-3)
     launch_ms = ms / args.steps
-    achieved = fpu * newton / (launch_ms * 1e-3)
+
+    newton, flops, failed, stat_means = 0, 0.0, 0, []
+    for (m, *_), b in zip(parts, bufs):
+        sh = b["stats"].cpu().numpy()
+        nwt = int(sh[2].astype(np.int64).sum())
+        newton += nwt
+        flops += nwt * algorithmic_flops_per_newton(m.ns, m.nr, j_term_count(m), precision == 1)
+        failed += int((b["st"].cpu().numpy() != 0).sum())
+        stat_means.append({"species": m.ns, "steps": float(sh[0].mean()), "rejects": float(sh[1].mean()),
+                           "newton": float(sh[2].mean())})
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = fp64_peak(props.multi_processor_count, sm_max)
+    peak = fp64_peak(props.multi_processor_count, clocks.get("sm_max_mhz") or 2070.0)
+    achieved = flops / (launch_ms * 1e-3)
 
-    # end to end: host arrays through cg_integrate_host (copies inside the timed region)
-    e2e_steps = min(args.steps, args.e2e_steps)
-    Th0 = np.ascontiguousarray(T)
-    Yh0 = np.ascontiguousarray(Y.T)
-    ph = np.ascontiguousarray(p)
-    sh = np.zeros(N, np.int32)
-    sth = np.zeros((4, N), np.int32)
-    e2e_t = 0.0
-    for k in range(e2e_steps + 1):
-        Th, Yh = Th0.copy(), Yh0.copy()
-        barrier()
-        t0 = time.perf_counter()
-        chemgb.cg_integrate_host(h, opts, Th, Yh, ph, sh, sth)
-        el = time.perf_counter() - t0
-        if k > 0:   # first call allocates the library's workspace: untimed
-            e2e_t += el
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = ws * N * e2e_steps / e2e_t
-    h2d = N * (1 + mech.ns + 1) * 8
-    d2h = N * (1 + mech.ns) * 8 + N * 4 + 4 * N * 4
+    # end to end through the host entry point (copies inside the timed region)
+    e2e = None
+    if len(handles) == 1 and args.e2e_steps > 0:
+        m, T, Y, p = parts[0]
+        N = len(T)
+        Th0, Yh0, ph = np.ascontiguousarray(T), np.ascontiguousarray(Y.T), np.ascontiguousarray(p)
+        sh_, sth = np.zeros(N, np.int32), np.zeros((4, N), np.int32)
+        e2e_t = 0.0
+        for k in range(args.e2e_steps + 1):
+            Th, Yh = Th0.copy(), Yh0.copy()
+            barrier()
+            t0 = time.perf_counter()
+            chemgb.cg_integrate_host(handles[0], opts, Th, Yh, ph, sh_, sth)
+            if k > 0:   # the first call allocates the library's host-call workspace: untimed
+                e2e_t += time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_t = float(t.item())
+        e2e = {"value": ws * N * args.e2e_steps / e2e_t, "unit": "cells/s",
+               "h2d_bytes_per_step": N * (m.ns + 2) * 8, "d2h_bytes_per_step": N * (m.ns + 1) * 8 + 20 * N,
+               "steps": args.e2e_steps}
+
+    # error against the FP64 oracle on a sample (mixed precision and batches)
+    err = None
+    if (precision == 1 or args.config == 3) and args.err_sample > 0 and rank == 0:
+        import oracle
+        err = {}
+        for (m, T, Y, p), b in zip(parts, bufs):
+            idx = np.linspace(0, len(T) - 1, min(args.err_sample, len(T))).astype(np.int64)
+            To, Yo, so, _ = oracle.RefMech(m).integrate(T[idx], Y[idx], p[idx], oracle_opts(opts_d),
+                                                        nthreads=os.cpu_count() or 1)
+            Tg = b["T"].cpu().numpy()[idx]
+            Yg = b["Y"].cpu().numpy()[:, idx].T
+            err[f"{m.ns}sp"] = {"cells": int(len(idx)), "max_rel_T": float(np.max(np.abs(Tg - To) / To)),
+                                "max_abs_Y": float(np.max(np.abs(Yg - Yo))),
+                                "status_match": float(np.mean(b["st"].cpu().numpy()[idx] == so))}
 
     if rank != 0:
         return
     cpu = None
     if ws == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
-        v, el = cpu_oracle_sample(mech, T, Y, p, args.cpu_sample, threads)
+        v, el, k = cpu_oracle_sample(parts, opts_d, args.cpu_sample, threads)
         cpu = {"value": v, "unit": "cells/s", "cores": threads, "kind": "oracle",
-               "sample": f"{args.cpu_sample} cells evenly spaced through the field ({el:.1f} s)"}
+               "sample": f"{k} cells evenly spaced through the field ({el:.1f} s)"}
+    state_bytes = sum(len(T) * (m.ns + 2) * 8 for m, T, _, _ in parts)
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells_per_gpu": N, "state_bytes": int(N * 55 * 8),
-                   "l2": "state (461 MB) larger than L2; no flush"},
-        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "config": {"workload": cfg["workload"], "config": args.config, "cells_per_gpu": N_total,
+                   "newton_matrix": "fp32" if precision == 1 else "fp64", "state_bytes": state_bytes,
+                   "l2": "state larger than L2 (129 MB); no flush" if state_bytes > 129e6
+                   else "state smaller than L2; each step restores it from a second copy"},
+        "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": "derived: 4 FP64 FLOP/clk/SM (measured DFMA rate) x SMs x max SM clock",
-                     "kernel": "integrate_kernel", "newton_per_launch": newton,
-                     "flops_per_newton": fpu},
+                     "kernel": "integrate_kernel", "newton_per_launch": newton},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": args.steps,
-        "cells_failed": int((st_h != 0).sum()),
-        "stats_mean": {"steps": float(stats_h[0].mean()), "rejects": float(stats_h[1].mean()),
-                       "newton": float(stats_h[2].mean())},
+        "cells_failed": failed,
+        "stats_mean": stat_means,
     }
+    if tuned:
+        line["autotune"] = tuned
+    if graph is not None:
+        line["cuda_graph"] = True
+    if err is not None:
+        line["error_vs_fp64_oracle"] = err
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
+    ap.add_argument("--cells", type=int, default=0, help="cells per mechanism (default: the workload's)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=2048)
     ap.add_argument("--ref-sample", type=int, default=1024)
+    ap.add_argument("--err-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cells", type=int, default=CELLS, help="cells per GPU (default: the workload's)")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--team", type=int, default=0, help="threads per cell (default: the library's choice)")
     ap.add_argument("--tpb", type=int, default=1, help="cells per block with --team 32")
-    ap.add_argument("--precision", type=int, default=0, help="0: FP64 Newton matrix, 1: FP32 LU")
+    ap.add_argument("--precision", type=int, default=None, help="0: FP64 Newton matrix, 1: FP32 LU")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -181,6 +181,21 @@ typedef struct {
 
 void cg_integrate_opts_default(cg_integrate_opts *opts);
 
+/* Autotuner: integrates a caller-given sample of cells (device arrays as in
+ * cg_integrate; not modified: each timing runs on a copy) once per launch
+ * shape -- threads per cell {32, 64, 128, 256}, cells per block {1, 2, 4}
+ * for one-warp teams, shared-memory limit {227, 113, 48} KiB -- and applies
+ * the fastest to the mechanism (cg_mech_set_launch, cg_mech_set_smem_limit).
+ * Synchronises `stream`; allocates two sample-sized work arrays for its
+ * duration. With cache_json != NULL, a file written by an earlier call for
+ * a mechanism of the same size and the same method and precision is applied
+ * without timing, otherwise the result is written there. *best_ms (may be
+ * NULL) receives the sample's time with the chosen shape. Launch tuning, not
+ * part of the paper's method. */
+cg_status cg_autotune(cg_mech *mech, const cg_integrate_opts *opts, int64_t N, const double *T,
+                      const double *Y, const double *p_or_rho, const char *cache_json, void *stream,
+                      double *best_ms);
+
 /* Integrate N cells over opts->dt.
  *   T[N], Y[ns*N]   in: initial temperature and mass fractions;
  *                   out: final ones (overwritten in place)

@@ -61,6 +61,11 @@ def _load():
         lib.cgref_lu_solve.argtypes = [ctypes.c_int, P, P]
         lib.cgref_temperature.argtypes = [P, ctypes.c_int, ctypes.c_long, P, P, P, ctypes.c_int, P]
         lib.cgref_integrate.argtypes = [P, P, P, P, ctypes.c_long, P, P, P, ctypes.c_int]
+        I = ctypes.c_int
+        lib.cgref_integrate_hist.argtypes = [P, P, P, P, ctypes.c_long, P, P, P, P, I, I]
+        lib.cgref_replay.argtypes = [P, P, P, P, ctypes.c_long, P, P, P, I, P, I]
+        lib.cgref_adjoint.argtypes = [P, P, P, P, ctypes.c_long, P, P, P, P, P, I]
+        lib.cgref_tangent.argtypes = [P, P, P, P, ctypes.c_long, P, P, I, I, P, P, I]
         _lib = lib
     return _lib
 
@@ -175,14 +180,72 @@ class RefMech:
         rho_i = np.asarray(C) * self.mech.W
         return rho_i / rho_i.sum(axis=1, keepdims=True)
 
-    def integrate_y(self, y: np.ndarray, opts: dict, nthreads: int = 1):
-        """Integrate states y[N, ns+1] over opts['dt']; returns (y, status, stats)."""
+    @staticmethod
+    def _packed(opts: dict):
         o = default_opts(**opts)
         iopt = _i32([o["method"], o["reactor"], o["adaptive"], o["nsub"], o["max_newton"],
                      o["max_steps"], o["max_halvings"], o["err_filter"]])
         dopt = _f64([o["dt"], o["rtol"], o["atol"], o["newton_tol"], o["h0"], o["hmin"],
                      o["neg_tol"]])
         tab = _tableau.pack(_tableau.tableau(o["method"]))
+        return iopt, dopt, tab
+
+    def integrate_hist(self, y, opts: dict, cap: int = 4096, nthreads: int = 1):
+        """Integrate y[N, n] and return (y_end, status, step sizes hs[N, cap],
+        accepted-step counts hn[N])."""
+        iopt, dopt, tab = self._packed(opts)
+        y = _f64(y).copy()
+        N = y.shape[0]
+        st = np.zeros(N, np.int32)
+        hs = np.zeros((N, cap))
+        hn = np.zeros(N, np.int32)
+        _load().cgref_integrate_hist(self.h, _p(iopt), _p(dopt), _p(tab), N, _p(y), _p(st), _p(hs), _p(hn),
+                                     cap, int(nthreads))
+        return y, st, hs, hn
+
+    def replay(self, y, opts: dict, hs, hn, nthreads: int = 1):
+        """Steps of the given sizes (no step-size control) from y[N, n]."""
+        iopt, dopt, tab = self._packed(opts)
+        y = _f64(y).copy()
+        hs = _f64(hs)
+        hn = _i32(hn)
+        N = y.shape[0]
+        st = np.zeros(N, np.int32)
+        _load().cgref_replay(self.h, _p(iopt), _p(dopt), _p(tab), N, _p(y), _p(hs), _p(hn), hs.shape[1],
+                             _p(st), int(nthreads))
+        return y, st
+
+    def adjoint(self, y0, lam_end, opts: dict, nthreads: int = 1):
+        """Discrete adjoint of the integration from y0[N, n] with
+        lam_end = dL/dy_end[N, n]; returns (dL/dy0 [N, n],
+        dL/dtheta [N, nr, 3] for (ln A, b, Ea), status)."""
+        iopt, dopt, tab = self._packed(opts)
+        y0 = _f64(y0)
+        lam = _f64(lam_end)
+        N = y0.shape[0]
+        dy0 = np.zeros_like(y0)
+        grad = np.zeros((N, self.nr, 3))
+        st = np.zeros(N, np.int32)
+        _load().cgref_adjoint(self.h, _p(iopt), _p(dopt), _p(tab), N, _p(y0), _p(lam), _p(dy0), _p(grad),
+                              _p(st), int(nthreads))
+        return dy0, grad, st
+
+    def tangent(self, y0, dy0, opts: dict, pj: int = -1, pk: int = 0, nthreads: int = 1):
+        """Forward sensitivity dy_end for the initial perturbation dy0 and
+        the parameter (reaction pj, kind pk: 0 ln A, 1 b, 2 Ea)."""
+        iopt, dopt, tab = self._packed(opts)
+        y0 = _f64(y0)
+        dy0 = _f64(dy0)
+        N = y0.shape[0]
+        dyend = np.zeros_like(y0)
+        st = np.zeros(N, np.int32)
+        _load().cgref_tangent(self.h, _p(iopt), _p(dopt), _p(tab), N, _p(y0), _p(dy0), int(pj), int(pk),
+                              _p(dyend), _p(st), int(nthreads))
+        return dyend, st
+
+    def integrate_y(self, y: np.ndarray, opts: dict, nthreads: int = 1):
+        """Integrate states y[N, ns+1] over opts['dt']; returns (y, status, stats)."""
+        iopt, dopt, tab = self._packed(opts)
         y = _f64(y).copy()
         N = y.shape[0]
         status = np.zeros(N, dtype=np.int32)

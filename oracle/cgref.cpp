@@ -451,6 +451,87 @@ double wrms(int n, const double* v, const double* ya, const double* yb, double r
     return std::sqrt(s / n);
 }
 
+// ---------------------------------------------------------------------------
+// Parameter derivatives for the adjoint and the forward sensitivity. The
+// differentiated parameters of reaction j are theta_j = (ln A, b, Ea) of its
+// Arrhenius triple (k_inf for falloff reactions, k_0 held fixed).
+
+// dq_j / d ln k_j (with k_j the Arrhenius triple's rate): q_j itself for
+// elementary and third-body reactions; for falloff, ln k_f = ln k_inf +
+// ln(Pr/(1+Pr)) + ln F with Pr = k_0 [M] / k_inf, so the factor is
+// Pr/(1+Pr) - dlog10F/dlog10Pr.
+double dq_dlnk(const Mech& m, int j, double T, const double* C) {
+    std::vector<double> q(m.nr);
+    progress_rates(m, T, C, (double*)nullptr, (double*)nullptr, q.data());
+    const Reaction& r = m.rx[j];
+    if (r.type == ELEMENTARY || r.type == THREE_BODY) return q[j];
+    double M = 0.0;
+    for (int i = 0; i < m.ns; ++i) M += C[i];
+    for (size_t e = 0; e < r.eff_sp.size(); ++e) M += (r.eff_val[e] - 1.0) * C[r.eff_sp[e]];
+    const double lnT = std::log(T);
+    const double kinf = std::exp(r.lnA + r.b * lnT - r.Ea / (R_U * T));
+    const double k0 = std::exp(r.lnA0 + r.b0 * lnT - r.Ea0 / (R_U * T));
+    const double Pr = k0 * M / kinf;
+    double dlogF_dP = 0.0;
+    if (r.type == TROE && Pr >= 1e-300) {
+        double Fc = (1.0 - r.alpha) * std::exp(-T / r.T3) + r.alpha * std::exp(-T / r.T1);
+        if (r.has_T2) Fc += std::exp(-r.T2 / T);
+        const double L = std::log10(Fc);
+        const double c = -0.4 - 0.67 * L, nn = 0.75 - 1.27 * L;
+        const double x = std::log10(Pr) + c, den = nn - 0.14 * x;
+        const double f1 = x / den;
+        dlogF_dP = -L * 2.0 * f1 / ((1.0 + f1 * f1) * (1.0 + f1 * f1)) * nn / (den * den);
+    }
+    return q[j] * (Pr / (1.0 + Pr) - dlogF_dP);
+}
+
+// dS/dq_j for every reaction: column j of an n x nr matrix (row-major).
+// Species rows: net coefficients nu_kj (CONP adds the dilution terms);
+// temperature row: -sum_k W_k e_k nu_kj / (rho c).
+void dS_dq(const Mech& m, int reactor, const double* y, std::vector<double>& out) {
+    const int ns = m.ns, n = ns + 1, nr = m.nr;
+    const double T = y[0];
+    const double* C = y + 1;
+    out.assign((size_t)n * nr, 0.0);
+    std::vector<double> e(ns);
+    double D = 0.0, sc = 0.0;
+    for (int i = 0; i < ns; ++i) {
+        e[i] = reactor == CONV ? u_i(m, i, T) : h_i(m, i, T);
+        D += m.W[i] * C[i] * (reactor == CONV ? cv_i(m, i, T) : cp_i(m, i, T));
+        sc += C[i];
+    }
+    for (int j = 0; j < nr; ++j) {
+        const Reaction& r = m.rx[j];
+        std::vector<double> nu(ns, 0.0);
+        for (int s = 0; s < 3; ++s) {
+            if (r.r_idx[s] >= 0) nu[r.r_idx[s]] += r.r_nu[s];
+            if (r.f_idx[s] >= 0) nu[r.f_idx[s]] -= r.f_nu[s];
+        }
+        double dwT = 0.0, snu = 0.0;
+        for (int k = 0; k < ns; ++k) { dwT -= m.W[k] * e[k] * nu[k] / D; snu += nu[k]; }
+        out[(size_t)0 * nr + j] = dwT;
+        for (int k = 0; k < ns; ++k) {
+            double v = nu[k];
+            if (reactor == CONP) v -= C[k] * (dwT / T + snu / sc);
+            out[(size_t)(1 + k) * nr + j] = v;
+        }
+    }
+}
+
+void transpose_solve(int n, const double* G, std::vector<double>& x) {
+    std::vector<double> Gt((size_t)n * n);
+    std::vector<int> piv(n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Gt[(size_t)i * n + j] = G[(size_t)j * n + i];
+    lu_factor(n, Gt.data(), piv.data());
+    lu_solve(n, Gt.data(), piv.data(), x.data());
+}
+
+struct Step {
+    std::vector<double> y;   // state at the start of an accepted step
+    double h;
+};
+
 struct Cell {
     const Mech& m;
     const Opts& o;
@@ -458,6 +539,9 @@ struct Cell {
     int n;
     std::vector<double> S, J, G, f, d;
     std::vector<int> piv;
+    bool record = false;                     // keep the accepted steps in hist
+    std::vector<Step> hist;
+    std::vector<std::vector<double>> lastY;  // converged stage states of the last step
     Cell(const Mech& mm, const Opts& oo) : m(mm), o(oo), n(mm.ns + 1),
         S(n), J(n * n), G(n * n), f(n), d(n), piv(n) {}
 
@@ -481,8 +565,10 @@ struct Cell {
             lu_solve(n, G.data(), piv.data(), d.data());
             for (int i = 0; i < n; ++i) y[i] += d[i];
             if (!finite_vec(y)) return false;
-            if (wrms(n, d.data(), yn.data(), y.data(), o.rtol, o.atol) <= o.newton_tol)
+            if (wrms(n, d.data(), yn.data(), y.data(), o.rtol, o.atol) <= o.newton_tol) {
+                lastY.assign(1, y);   // the one stage state of backward Euler is y^{n+1}
                 return admissible(y, o.neg_tol);
+            }
         }
         return false;
     }
@@ -500,6 +586,7 @@ struct Cell {
                     std::vector<double>& y1, std::vector<double>& err) {
         std::vector<std::vector<double>> Gam(tb.s, std::vector<double>(n));
         std::vector<double> S0(n), Y(n), base(n);
+        lastY.assign(tb.s, std::vector<double>(n));
         source(m, o.reactor, yn.data(), S0.data());
         for (int p = 0; p < tb.s; ++p) {
             double gh = tb.A[p][p] * h;
@@ -531,6 +618,7 @@ struct Cell {
                 }
             }
             if (!conv) return false;
+            lastY[p] = Y;
         }
         y1 = yn;
         err.assign(n, 0.0);
@@ -554,7 +642,12 @@ struct Cell {
     // recursively, at most max_halvings levels deep.
     int fixed_recursive(const Tableau& tb, std::vector<double>& y, double h, int depth) {
         std::vector<double> y1;
-        if (fixed_step(tb, y, h, y1)) { y = y1; st.steps++; return ST_OK; }
+        if (fixed_step(tb, y, h, y1)) {
+            if (record) hist.push_back({y, h});
+            y = y1;
+            st.steps++;
+            return ST_OK;
+        }
         st.rejects++;
         if (depth >= o.max_halvings) return ST_NEWTON_FAIL;
         int s = fixed_recursive(tb, y, 0.5 * h, depth + 1);
@@ -584,6 +677,7 @@ struct Cell {
             double fac = e > 0.0 ? 0.9 * std::pow(e, expo) : 5.0;
             fac = std::min(5.0, std::max(0.2, fac));
             if (e <= 1.0) {
+                if (record) hist.push_back({y, hh});
                 y = y1;
                 t = last ? o.dt : t + hh;
                 st.steps++;
@@ -605,6 +699,113 @@ struct Cell {
             if (s != ST_OK) return s;
         }
         return ST_OK;
+    }
+
+    // Converged stage states of the step (y_n, h) into lastY.
+    bool stages(const Tableau& tb, const std::vector<double>& yn, double h) {
+        std::vector<double> y1, err;
+        if (o.method == 0) return be_step(yn, h, y1);
+        return sdirk_step(tb, yn, h, y1, err);
+    }
+
+    // Steps of prescribed sizes (no step-size decisions).
+    int replay(const Tableau& tb, std::vector<double>& y, const double* hs, int count) {
+        std::vector<double> y1, err;
+        for (int k = 0; k < count; ++k) {
+            bool ok = o.method == 0 ? be_step(y, hs[k], y1) : sdirk_step(tb, y, hs[k], y1, err);
+            if (!ok) return ST_NEWTON_FAIL;
+            y = y1;
+        }
+        return ST_OK;
+    }
+
+    // Discrete adjoint of the converged stage equations with the accepted
+    // steps frozen: for a step (y_n, h) with stages Y_p, Gamma_p = S(Y_p),
+    //   (I - h a_pp J_p)^T nu_p = h b_p lam + sum_{q>p} h a_qp J_q^T nu_q,
+    //   lam_n = lam + sum_p J_p^T nu_p,  dL/dtheta += sum_p nu_p^T dS/dtheta(Y_p).
+    // Backward Euler is the one-stage case a = b = 1. lam: dL/dy_end in,
+    // dL/dy_0 out; grad[3 nr] accumulates (ln A, b, Ea) of every reaction.
+    bool adjoint(const Tableau& tb, std::vector<double>& lam, std::vector<double>& grad) {
+        const int s = o.method == 0 ? 1 : tb.s;
+        const double A00 = 1.0;
+        std::vector<double> dSq;
+        for (int stp = (int)hist.size() - 1; stp >= 0; --stp) {
+            const double h = hist[stp].h;
+            if (!stages(tb, hist[stp].y, h)) return false;
+            std::vector<std::vector<double>> acc(s, std::vector<double>(n, 0.0));
+            std::vector<double> lam_n = lam;
+            for (int p = s - 1; p >= 0; --p) {
+                const double app = o.method == 0 ? A00 : tb.A[p][p];
+                const double bp = o.method == 0 ? 1.0 : tb.b[p];
+                std::vector<double> nu(n);
+                for (int i = 0; i < n; ++i) nu[i] = h * bp * lam[i] + acc[p][i];
+                jacobian(m, o.reactor, lastY[p].data(), J.data());
+                for (int i = 0; i < n; ++i)
+                    for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 : 0.0) - h * app * J[i * n + j];
+                transpose_solve(n, G.data(), nu);
+                std::vector<double> w(n, 0.0);   // J_p^T nu_p
+                for (int i = 0; i < n; ++i)
+                    for (int j = 0; j < n; ++j) w[j] += J[i * n + j] * nu[i];
+                for (int q = 0; q < p; ++q)
+                    for (int i = 0; i < n; ++i) acc[q][i] += h * tb.A[p][q] * w[i];
+                for (int i = 0; i < n; ++i) lam_n[i] += w[i];
+                dS_dq(m, o.reactor, lastY[p].data(), dSq);
+                const double T = lastY[p][0];
+                for (int j = 0; j < m.nr; ++j) {
+                    double g = 0.0;
+                    for (int i = 0; i < n; ++i) g += nu[i] * dSq[(size_t)i * m.nr + j];
+                    const double dq = g * dq_dlnk(m, j, T, lastY[p].data() + 1);
+                    grad[3 * j + 0] += dq;
+                    grad[3 * j + 1] += dq * std::log(T);
+                    grad[3 * j + 2] -= dq / (R_U * T);
+                }
+            }
+            lam = lam_n;
+        }
+        return true;
+    }
+
+    // Forward sensitivity (tangent linear) of the same frozen steps:
+    //   (I - h a_pp J_p) dGamma_p = J_p (dy_n + h sum_{q<p} a_pq dGamma_q)
+    //                               + dS/dtheta(Y_p),
+    //   dy_{n+1} = dy_n + h sum_p b_p dGamma_p;
+    // for the parameter (reaction pj, kind pk: 0 ln A, 1 b, 2 Ea; pj < 0: none).
+    bool tangent(const Tableau& tb, std::vector<double>& dy, int pj, int pk) {
+        const int s = o.method == 0 ? 1 : tb.s;
+        std::vector<double> dSq;
+        for (size_t stp = 0; stp < hist.size(); ++stp) {
+            const double h = hist[stp].h;
+            if (!stages(tb, hist[stp].y, h)) return false;
+            std::vector<std::vector<double>> dG(s, std::vector<double>(n, 0.0));
+            for (int p = 0; p < s; ++p) {
+                const double app = o.method == 0 ? 1.0 : tb.A[p][p];
+                std::vector<double> z = dy;
+                for (int q = 0; q < p; ++q)
+                    for (int i = 0; i < n; ++i) z[i] += h * tb.A[p][q] * dG[q][i];
+                jacobian(m, o.reactor, lastY[p].data(), J.data());
+                std::vector<double> rhs(n, 0.0);
+                for (int i = 0; i < n; ++i)
+                    for (int j = 0; j < n; ++j) rhs[i] += J[i * n + j] * z[j];
+                if (pj >= 0) {
+                    dS_dq(m, o.reactor, lastY[p].data(), dSq);
+                    const double T = lastY[p][0];
+                    double dq = dq_dlnk(m, pj, T, lastY[p].data() + 1);
+                    if (pk == 1) dq *= std::log(T);
+                    if (pk == 2) dq *= -1.0 / (R_U * T);
+                    for (int i = 0; i < n; ++i) rhs[i] += dSq[(size_t)i * m.nr + pj] * dq;
+                }
+                for (int i = 0; i < n; ++i)
+                    for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 : 0.0) - h * app * J[i * n + j];
+                lu_factor(n, G.data(), piv.data());
+                lu_solve(n, G.data(), piv.data(), rhs.data());
+                dG[p] = rhs;
+            }
+            for (int p = 0; p < s; ++p) {
+                const double bp = o.method == 0 ? 1.0 : tb.b[p];
+                for (int i = 0; i < n; ++i) dy[i] += h * bp * dG[p][i];
+            }
+        }
+        return true;
     }
 };
 
@@ -793,6 +994,105 @@ void cgref_integrate(const void* h, const int* iopt, const double* dopt, const d
         stats[4 * c + 1] = cell.st.rejects;
         stats[4 * c + 2] = cell.st.newton;
         stats[4 * c + 3] = cell.st.lu;
+    });
+}
+
+namespace {
+
+void unpack(const int* iopt, const double* dopt, const double* tab, Opts& o, Tableau& tb) {
+    o.method = iopt[0]; o.reactor = iopt[1]; o.adaptive = iopt[2]; o.nsub = iopt[3];
+    o.max_newton = iopt[4]; o.max_steps = iopt[5]; o.max_halvings = iopt[6]; o.err_filter = iopt[7];
+    o.dt = dopt[0]; o.rtol = dopt[1]; o.atol = dopt[2]; o.newton_tol = dopt[3];
+    o.h0 = dopt[4]; o.hmin = dopt[5]; o.neg_tol = dopt[6];
+    tb.s = (int)tab[0];
+    tb.err_order = (int)tab[1];
+    for (int i = 0; i < 5; ++i) {
+        for (int j = 0; j < 5; ++j) tb.A[i][j] = tab[2 + 5 * i + j];
+        tb.b[i] = tab[27 + i];
+        tb.bhat[i] = tab[32 + i];
+    }
+}
+
+}  // namespace
+
+// Integrate and return the accepted step sizes (hs[N][cap], hn[N]); a cell
+// with more than cap accepted steps gets hn = -1.
+void cgref_integrate_hist(const void* h, const int* iopt, const double* dopt, const double* tab, long N,
+                          double* y, int* status, double* hs, int* hn, int cap, int nthreads) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    Opts o;
+    Tableau tb;
+    unpack(iopt, dopt, tab, o, tb);
+    const int n = m.ns + 1;
+    parallel_for(N, nthreads, [&](long c) {
+        Cell cell(m, o);
+        cell.record = true;
+        std::vector<double> yc(y + c * n, y + (c + 1) * n);
+        status[c] = cell.integrate(tb, yc);
+        std::copy(yc.begin(), yc.end(), y + c * n);
+        hn[c] = (int)cell.hist.size() <= cap ? (int)cell.hist.size() : -1;
+        for (size_t k = 0; k < cell.hist.size() && (int)k < cap; ++k) hs[c * cap + k] = cell.hist[k].h;
+    });
+}
+
+// Steps of the given sizes from y (in/out).
+void cgref_replay(const void* h, const int* iopt, const double* dopt, const double* tab, long N, double* y,
+                  const double* hs, const int* hn, int cap, int* status, int nthreads) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    Opts o;
+    Tableau tb;
+    unpack(iopt, dopt, tab, o, tb);
+    const int n = m.ns + 1;
+    parallel_for(N, nthreads, [&](long c) {
+        Cell cell(m, o);
+        std::vector<double> yc(y + c * n, y + (c + 1) * n);
+        status[c] = cell.replay(tb, yc, hs + c * cap, hn[c]);
+        std::copy(yc.begin(), yc.end(), y + c * n);
+    });
+}
+
+// Discrete adjoint: integrates y0 (recording the accepted steps), then
+// sweeps back with lam = dL/dy_end. Out: dL/dy_0 (dy0[N][n]) and
+// dL/dtheta per cell (grad[N][3 nr], (ln A, b, Ea) of each reaction).
+void cgref_adjoint(const void* h, const int* iopt, const double* dopt, const double* tab, long N,
+                   const double* y0, const double* lam_end, double* dy0, double* grad, int* status,
+                   int nthreads) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    Opts o;
+    Tableau tb;
+    unpack(iopt, dopt, tab, o, tb);
+    const int n = m.ns + 1;
+    parallel_for(N, nthreads, [&](long c) {
+        Cell cell(m, o);
+        cell.record = true;
+        std::vector<double> yc(y0 + c * n, y0 + (c + 1) * n);
+        int s = cell.integrate(tb, yc);
+        std::vector<double> lam(lam_end + c * n, lam_end + (c + 1) * n), g(3 * m.nr, 0.0);
+        if (s == ST_OK && !cell.adjoint(tb, lam, g)) s = ST_NEWTON_FAIL;
+        status[c] = s;
+        std::copy(lam.begin(), lam.end(), dy0 + c * n);
+        std::copy(g.begin(), g.end(), grad + c * 3 * m.nr);
+    });
+}
+
+// Forward sensitivity of y_end to dy0 and to one parameter (pj, pk).
+void cgref_tangent(const void* h, const int* iopt, const double* dopt, const double* tab, long N,
+                   const double* y0, const double* dy0, int pj, int pk, double* dyend, int* status,
+                   int nthreads) {
+    const Mech& m = *static_cast<const Mech*>(h);
+    Opts o;
+    Tableau tb;
+    unpack(iopt, dopt, tab, o, tb);
+    const int n = m.ns + 1;
+    parallel_for(N, nthreads, [&](long c) {
+        Cell cell(m, o);
+        cell.record = true;
+        std::vector<double> yc(y0 + c * n, y0 + (c + 1) * n);
+        int s = cell.integrate(tb, yc);
+        std::vector<double> dy(dy0 + c * n, dy0 + (c + 1) * n);
+        if (s == ST_OK && !cell.tangent(tb, dy, pj, pk)) s = ST_NEWTON_FAIL;
+        status[c] = s;
+        std::copy(dy.begin(), dy.end(), dyend + c * n);
     });
 }
 

@@ -49,7 +49,7 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_mech_set_launch", "cg_mech_get_launch", "cg_mech_set_smem_limit",
             "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
-            "cg_integrate_noalloc", "cg_last_error")
+            "cg_integrate_noalloc", "cg_autotune", "cg_last_error")
 
 
 def library_path() -> str:
@@ -78,6 +78,8 @@ def load(build_if_missing: bool = False):
     lib.cg_mech_set_smem_limit.argtypes = [P, L]
     lib.cg_integrate_batch.argtypes = [I, P, P, P, P, P, P, P, ctypes.POINTER(cg_integrate_opts), P]
     lib.cg_integrate_noalloc.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, P]
+    lib.cg_autotune.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, ctypes.c_char_p, P,
+                                ctypes.POINTER(ctypes.c_double)]
     lib.cg_eval_rates.argtypes = [P, I, L, P, P, P, P]
     lib.cg_eval_jacobian.argtypes = [P, I, L, P, P, P, P]
     lib.cg_temperature_from_energy.argtypes = [P, I, L, P, P, P, I, P]
@@ -187,6 +189,15 @@ def cg_integrate_noalloc(h, opts, T, Y, p_or_rho, status=None, stats=None, strea
     _check(load().cg_integrate_noalloc(h.ptr, ctypes.byref(opts), T.shape[0], _dev(T), _dev(Y),
                                        _dev(p_or_rho), None if status is None else _dev(status, "int32"),
                                        None if stats is None else _dev(stats, "int32"), _stream(stream)))
+
+
+def cg_autotune(h, opts, T, Y, p_or_rho, cache_json=None, stream=None) -> float:
+    """Pick the fastest launch shape on a sample (device tensors); returns its
+    time in ms."""
+    ms = ctypes.c_double(0.0)
+    _check(load().cg_autotune(h.ptr, ctypes.byref(opts), T.shape[0], _dev(T), _dev(Y), _dev(p_or_rho),
+                              cache_json.encode() if cache_json else None, _stream(stream), ctypes.byref(ms)))
+    return ms.value
 
 
 def cg_mech_set_smem_limit(h, nbytes: int):

@@ -843,6 +843,93 @@ cg_status cg_integrate_host(const cg_mech* mc, const cg_integrate_opts* o, int64
     return CG_OK;
 }
 
+// Autotuner: time cg_integrate on a sample of cells for every launch shape
+// (threads per cell, cells per block, shared-memory limit) that fits, keep
+// the fastest. The sample is integrated from a fresh copy of its inputs for
+// each timing; the caller's arrays are not modified.
+cg_status cg_autotune(cg_mech* m, const cg_integrate_opts* o, int64_t N, const double* T, const double* Y,
+                      const double* p_or_rho, const char* cache_json, void* stream, double* best_ms) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    IntParams P;
+    cg_status st = make_params(o, P);
+    if (st != CG_OK) return st;
+    if (N <= 0 || !T || !Y || !p_or_rho) return fail(CG_EINVAL, "a non-empty sample is required");
+    if (cache_json) {   // reuse a previous result for the same mechanism size and options
+        FILE* f = fopen(cache_json, "r");
+        if (f) {
+            int ns = -1, nr = -1, prec = -1, method = -1, team = 0, tpb = 0;
+            long long lim = 0;
+            double ms = 0;
+            const int got = fscanf(f, "{\"ns\": %d, \"nr\": %d, \"precision\": %d, \"method\": %d, \"team\": %d, "
+                                      "\"teams_per_block\": %d, \"smem_limit\": %lld, \"ms\": %lf}",
+                                   &ns, &nr, &prec, &method, &team, &tpb, &lim, &ms);
+            fclose(f);
+            if (got == 8 && ns == m->ns && nr == m->nr && prec == o->precision && method == o->method) {
+                if ((st = cg_mech_set_smem_limit(m, lim)) != CG_OK) return st;
+                if ((st = cg_mech_set_launch(m, team, tpb)) != CG_OK) return st;
+                if (best_ms) *best_ms = ms;
+                return CG_OK;
+            }
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double *wT = nullptr, *wY = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    const size_t yb = (size_t)N * m->ns * sizeof(double);
+    if ((e = cudaMalloc(&wT, N * sizeof(double))) != cudaSuccess || (e = cudaMalloc(&wY, yb)) != cudaSuccess ||
+        (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaFree(wT);
+        cudaFree(wY);
+        return cuda_fail(e, "autotune workspace");
+    }
+    const int old_team = m->dm.team, old_tpb = m->tpb;
+    const int64_t old_lim = (int64_t)m->smem_limit;
+    struct Shape { int team, tpb; int64_t lim; };
+    std::vector<Shape> shapes;
+    for (int64_t lim : {(int64_t)kMaxSmemPerBlock, (int64_t)kMaxSmemPerBlock / 2, (int64_t)48 * 1024})
+        for (int team : {32, 64, 128, 256})
+            for (int tpb : {1, 2, 4})
+                if (team == 32 || tpb == 1) shapes.push_back({team, tpb, lim});
+    Shape best = {old_team, old_tpb, old_lim};
+    float best_t = -1.0f;
+    for (const Shape& sh : shapes) {
+        if (cg_mech_set_smem_limit(m, sh.lim) != CG_OK || cg_mech_set_launch(m, sh.team, sh.tpb) != CG_OK) continue;
+        float t_ms = 0.0f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {   // first run warms up, second is timed
+            ok = cudaMemcpyAsync(wT, T, N * sizeof(double), cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+                 cudaMemcpyAsync(wY, Y, yb, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+                 cudaEventRecord(e0, s) == cudaSuccess &&
+                 cg_integrate(m, o, N, wT, wY, p_or_rho, nullptr, nullptr, stream) == CG_OK &&
+                 cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                 cudaEventElapsedTime(&t_ms, e0, e1) == cudaSuccess;
+        }
+        if (ok && (best_t < 0.0f || t_ms < best_t)) {
+            best_t = t_ms;
+            best = sh;
+        }
+    }
+    cudaFree(wT);
+    cudaFree(wY);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((st = cg_mech_set_smem_limit(m, best.lim)) != CG_OK) return st;
+    if ((st = cg_mech_set_launch(m, best.team, best.tpb)) != CG_OK) return st;
+    if (best_t < 0.0f) return fail(CG_ECUDA, "no launch shape ran: %s", g_err.c_str());
+    if (best_ms) *best_ms = best_t;
+    if (cache_json) {
+        FILE* f = fopen(cache_json, "w");
+        if (f) {
+            fprintf(f, "{\"ns\": %d, \"nr\": %d, \"precision\": %d, \"method\": %d, \"team\": %d, "
+                       "\"teams_per_block\": %d, \"smem_limit\": %lld, \"ms\": %.6f}\n",
+                    m->ns, m->nr, o->precision, o->method, best.team, best.tpb, (long long)best.lim, best_t);
+            fclose(f);
+        }
+    }
+    return CG_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -507,6 +507,27 @@ def field_reactor(mech: Mechanism, n: int, T_range, p_range_atm, phi_range, fuel
     return T, X_to_Y(mech, _fuel_air_X(mech, fuel, phi, argon)), p
 
 
+def field_mixed(mech: Mechanism, n: int, fuel: str, seed: int = 0, argon: float = 0.0,
+                frozen=(300.0, 600.0), burnt=(1800.0, 2400.0), active=(1000.0, 1700.0),
+                shares=(0.90, 0.05, 0.05)):
+    """Cells of very uneven cost, randomly interleaved: `shares` of frozen
+    fuel/air (T in `frozen`), burnt gas (complete-combustion products plus
+    radicals, T in `burnt`) and reacting cells (T in `active` with the
+    composition blended linearly in T between unburnt and burnt, as in a
+    flame front). p in U[1, 10] atm, phi in U[0.5, 1.5] per cell."""
+    rng = np.random.default_rng(seed)
+    kind = rng.choice(3, size=n, p=np.asarray(shares) / np.sum(shares))
+    phi = rng.uniform(0.5, 1.5, n)
+    p = rng.uniform(1.0, 10.0, n) * P_ATM
+    Xu = _fuel_air_X(mech, fuel, phi, argon)
+    Xb = _burnt_X(mech, Xu)
+    T = np.where(kind == 0, rng.uniform(*frozen, n),
+                 np.where(kind == 1, rng.uniform(*burnt, n), rng.uniform(*active, n)))
+    w = np.where(kind == 0, 0.0, np.where(kind == 1, 1.0, (T - active[0]) / (active[1] - active[0])))
+    X = (1.0 - w[:, None]) * Xu + w[:, None] * Xb
+    return T, X_to_Y(mech, X), p, kind
+
+
 def field_flames(mech: Mechanism, n: int, seed: int = 0, cells_per_flame: int = 4096,
                  fuel: str = "CH4", argon: float = 0.0093):
     """Contiguous 1-D flame-like field, one flame per block of cells: 60% unburnt

@@ -96,6 +96,54 @@ def test_batch_of_two_mechanisms_matches_separate_launches(mechs, flame_cells):
         chemgb.cg_integrate_batch([h9, h53], o, Ts, Ys, ps)
 
 
+def test_autotune_picks_a_shape_and_keeps_results(mechs, tmp_path):
+    m = mechs["ch4"]
+    h = chemgb.cg_mech_create(m)
+    T, Y, p, _ = inputs.field_mixed(m, 2048, "CH4", seed=3, argon=0.0093)
+    o = chemgb.make_opts(**ADAPT, precision=chemgb.CG_FP32LU)
+    before = run(h, o, T, Y, p)
+    cache = str(tmp_path / "tune.json")
+    Tt, Yt, pt = d(T), d(Y.T), d(p)
+    ms = chemgb.cg_autotune(h, o, Tt, Yt, pt, cache)
+    assert ms > 0
+    np.testing.assert_array_equal(Tt.cpu().numpy(), T)       # the sample is not modified
+    team, tpb = chemgb.cg_mech_get_launch(h)
+    assert team in (32, 64, 128, 256) and tpb in (1, 2, 4)
+    after = run(h, o, T, Y, p)
+    np.testing.assert_array_equal(after[2], before[2])
+    np.testing.assert_allclose(after[0], before[0], rtol=1e-9)
+    h2 = chemgb.cg_mech_create(m)                              # the cache file is applied
+    assert chemgb.cg_autotune(h2, o, Tt, Yt, pt, cache) == pytest.approx(ms)
+    assert chemgb.cg_mech_get_launch(h2) == (team, tpb)
+
+
+def test_batch_replays_from_a_cuda_graph(mechs, flame_cells):
+    """The batched launch (stream-ordered scratch, counter reset, kernel)
+    captured in a CUDA graph and replayed gives the direct call's results."""
+    h53 = chemgb.cg_mech_create(mechs["ch4"])
+    T, Y, p = flame_cells
+    o = chemgb.make_opts(**ADAPT, persistent=1)
+    ref = run(h53, o, T, Y, p)
+    T0, Y0, P0 = d(T), d(Y.T), d(p)
+    Tw, Yw = torch.empty_like(T0), torch.empty_like(Y0)
+    st = torch.empty(len(T), dtype=torch.int32, device=DEV)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        Tw.copy_(T0); Yw.copy_(Y0)
+        chemgb.cg_integrate_batch([h53], o, [Tw], [Yw], [P0], [st], stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        Tw.copy_(T0); Yw.copy_(Y0)
+        chemgb.cg_integrate_batch([h53], o, [Tw], [Yw], [P0], [st], stream=stream.cuda_stream)
+    for _ in range(2):
+        Tw.fill_(0.0)
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(Tw.cpu().numpy(), ref[0])
+        np.testing.assert_array_equal(Yw.cpu().numpy().T, ref[1])
+
+
 # ---------------------------------------------------------------------------
 # 160 species, 900 reactions
 

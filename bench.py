@@ -16,6 +16,12 @@ Other workloads (reported beside the default line):
               5% reacting, randomly interleaved), FP32 Newton matrix,
               autotuned launch shape, replayed from a captured CUDA graph;
               error against the FP64 oracle on a sample
+  --config 4  discrete adjoint: 53 species, 65,536 cells, T0 in U[1100, 1400] K,
+              1 atm, phi in U[0.5, 2], adaptive SDIRK-4 over dt = 1e-4 s with
+              checkpoints, then the backward sweep for
+              L = sum (T_end - T_target)^2 (target from ln A + N(0, 0.1^2));
+              gradients w.r.t. (ln A, b, Ea) of all reactions and (T0, Y0);
+              sampled cells checked against the oracle's adjoint
   --config 5  160 species / 900 reactions, T in U[700, 1600] K,
               p in U[20, 40] atm, adaptive SDIRK-4 (use --cells for a subset)
 
@@ -43,6 +49,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cells integrated/s over dt"
+METRIC_ADJ = "cells differentiated/s over dt (forward with checkpoints + adjoint)"
 SDIRK4 = dict(method=2, reactor=1, adaptive=1, dt=1e-6, rtol=1e-6, atol=1e-12, newton_tol=0.03,
               max_newton=7, max_steps=100000, max_halvings=10, err_filter=1, neg_tol=1e-6)
 BE = dict(method=0, reactor=1, adaptive=0, dt=1e-5, rtol=1e-10, atol=1e-16, newton_tol=1.0,
@@ -59,6 +66,11 @@ CONFIGS = {
             workload="53-species + 9-species mechanisms in one persistent work-stealing launch, "
                      "2 x 1,048,576 heavy-tailed cells (90% frozen, 5% burnt, 5% reacting, interleaved), "
                      "FP32 Newton matrix, autotuned, CUDA graph, adaptive SDIRK-4 rtol 1e-6, dt 1e-6 s"),
+    4: dict(cells=1 << 16, opts=dict(SDIRK4, dt=1e-4), precision=0,
+            workload="53-species/325-reaction synthetic methane-shaped mechanism, 65,536 cells, T0 U[1100,1400] K, "
+                     "1 atm, phi U[0.5,2], constant pressure, adaptive SDIRK-4 rtol 1e-6 over dt 1e-4 s with "
+                     "checkpoints + discrete adjoint of L = sum (T_end - T_target)^2, T_target from "
+                     "ln A + N(0, 0.1^2); gradients w.r.t. 975 Arrhenius parameters and (T0, Y0)"),
     5: dict(cells=1 << 18, opts=SDIRK4, precision=0,
             workload="160-species/900-reaction synthetic n-heptane-shaped mechanism, T U[700,1600] K, "
                      "p U[20,40] atm, phi U[0.5,1.5], constant pressure, adaptive SDIRK-4 rtol 1e-6, dt 1e-6 s"),
@@ -163,6 +175,10 @@ def make_workload(config: int, cells: int, seed: int = 0):
         T, Y, p, _ = inputs.field_mixed(m53, cells, "CH4", seed=seed, argon=0.0093)
         T9, Y9, p9, _ = inputs.field_mixed(m9, cells, "H2", seed=seed + 1000)
         return [(m53, T, Y, p), (m9, T9, Y9, p9)]
+    if config == 4:
+        m = inputs.gen_mechanism("ch4")
+        T, Y, p = inputs.field_reactor(m, cells, (1100, 1400), (1, 1), (0.5, 2), "CH4", seed=seed)
+        return [(m, T, Y, p)]
     if config == 5:
         m = inputs.gen_mechanism("c7")
         T, Y, p = inputs.field_reactor(m, cells, (700, 1600), (20, 40), (0.5, 1.5), "C7H16", seed=seed)
@@ -421,6 +437,250 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_flops(m, stats, s_stages: int) -> float:
+    """Algorithmic FP64 flops of the backward sweep of cells with the given
+    forward counters: the recomputed stages (every forward Newton iteration
+    of the accepted steps, taken as the forward's iterations), and per stage
+    one Jacobian and LU of G_p (one Newton iteration's work), the transposed
+    solve 2 n^2, the stage coupling 2 s n, and the parameter gradient
+    (2 per slot of every reaction, 6 per reaction)."""
+    fpn = algorithmic_flops_per_newton(m.ns, m.nr, j_term_count(m), False)
+    n = m.ns + 1
+    per_stage = fpn + 2.0 * n * n + 2.0 * s_stages * n + 18.0 * m.nr
+    steps = float(stats[0].astype(np.int64).sum())
+    return float(stats[2].astype(np.int64).sum()) * fpn + steps * s_stages * per_stage
+
+
+def run_adjoint(args):
+    """--config 4: forward with checkpoints plus the discrete adjoint."""
+    import torch
+    from paper_2510_10005_gb300 import autograd, chemgb
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    chemgb.load(build_if_missing=(ws == 1))
+    cfg = CONFIGS[4]
+    (m, T, Y, p), = make_workload(4, args.cells or cfg["cells"], seed=rank)
+    N = len(T)
+    opts_d = opts_dict(4, 0)
+    opts = chemgb.make_opts(**opts_d)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    h = chemgb.cg_mech_create(m)
+    f64 = dict(dtype=torch.float64, device=dev)
+    T0 = torch.tensor(T, **f64)
+    Y0 = torch.tensor(np.ascontiguousarray(Y.T), **f64)
+    P = torch.tensor(p, **f64)
+    Tb, Yb = torch.empty_like(T0), torch.empty_like(Y0)
+    st = torch.empty(N, dtype=torch.int32, device=dev)
+    stats = torch.empty((4, N), dtype=torch.int32, device=dev)
+
+    # the target: the same cells integrated with ln A + N(0, 0.1^2) (seed 1)
+    arr_t = m.arr.copy()
+    arr_t[:, 0] += np.random.default_rng(1).normal(0.0, 0.1, m.nr)
+    chemgb.cg_mech_set_arrhenius(h, arr_t)
+    Tb.copy_(T0); Yb.copy_(Y0)
+    chemgb.cg_integrate(h, opts, Tb, Yb, P, st, stats)
+    T_target = Tb.clone()
+    chemgb.cg_mech_set_arrhenius(h, m.arr)
+    # checkpoint slots: the largest accepted-step count of the forward pass, with margin
+    Tb.copy_(T0); Yb.copy_(Y0)
+    chemgb.cg_integrate(h, opts, Tb, Yb, P, st, stats)
+    torch.cuda.synchronize(dev)
+    cap = int(stats[0].max().item()) * 2 + 8
+    ckpt = torch.empty((N, cap, m.ns + 2), **f64)
+    ckpt_n = torch.empty(N, dtype=torch.int32, device=dev)
+    gY = torch.zeros((m.ns, N), **f64)
+    dT0, dY0 = torch.empty(N, **f64), torch.empty((m.ns, N), **f64)
+    dth = torch.empty((m.nr, 3), **f64)
+    dcells = torch.empty((m.nr, 3, N), **f64)
+    ast = torch.empty(N, dtype=torch.int32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step(split=False):
+        Tb.copy_(T0)
+        Yb.copy_(Y0)
+        if split:
+            ev[0].record(stream)
+        chemgb.cg_integrate_ckpt(h, opts, Tb, Yb, P, ckpt, ckpt_n, st, stats, stream=stream.cuda_stream)
+        if split:
+            ev[1].record(stream)
+        gT = 2.0 * (Tb - T_target)
+        chemgb.cg_integrate_adjoint(h, opts, ckpt, ckpt_n, gT, gY, dT0, dY0, dth, dcells, ast,
+                                    stream=stream.cuda_stream)
+        if split:
+            ev[2].record(stream)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    step(split=True)                      # per-kernel durations (forward, adjoint)
+    torch.cuda.synchronize(dev)
+    fwd_ms, adj_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        # the parameter gradient of the whole job: one sum over ranks
+        dist.all_reduce(dth)
+    value = ws * N * args.steps / (ms * 1e-3)
+    sh = stats.cpu().numpy()
+    s_stages = 5
+    a_flops = adjoint_flops(m, sh, s_stages)
+    f_flops = float(sh[2].astype(np.int64).sum()) * algorithmic_flops_per_newton(m.ns, m.nr, j_term_count(m),
+                                                                                  False)
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    peak = fp64_peak(props.multi_processor_count, clocks.get("sm_max_mhz") or 2070.0)
+    adj_status = ast.cpu().numpy()
+    loss = float(((Tb - T_target) ** 2).sum().item())
+
+    # end to end through the torch.autograd entry point: pinned host inputs
+    # in, gradients out, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        Th = torch.tensor(T, dtype=torch.float64).pin_memory()
+        Yh = torch.tensor(np.ascontiguousarray(Y.T), dtype=torch.float64).pin_memory()
+        ph = torch.tensor(p, dtype=torch.float64).pin_memory()
+        theta = torch.tensor(m.arr, dtype=torch.float64, requires_grad=True)
+        out = [torch.empty(N, dtype=torch.float64).pin_memory(),
+               torch.empty((m.ns, N), dtype=torch.float64).pin_memory()]
+        e2e_t = 0.0
+        for k in range(args.e2e_steps + 1):
+            barrier()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            Td = Th.to(dev, non_blocking=True).requires_grad_()
+            Yd = Yh.to(dev, non_blocking=True).requires_grad_()
+            Te, _, _ = autograd.integrate(h, opts, Td, Yd, ph.to(dev, non_blocking=True), theta, cap=cap)
+            L = ((Te - T_target) ** 2).sum()
+            theta.grad = None
+            L.backward()
+            out[0].copy_(Td.grad, non_blocking=True)
+            out[1].copy_(Yd.grad, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            if k > 0:
+                e2e_t += time.perf_counter() - t0
+        e2e = {"value": ws * N * args.e2e_steps / e2e_t, "unit": "cells/s",
+               "h2d_bytes_per_step": N * (m.ns + 2) * 8,
+               "d2h_bytes_per_step": N * (m.ns + 1) * 8 + m.nr * 3 * 8, "steps": args.e2e_steps,
+               "api": "paper_2510_10005_gb300.autograd.integrate + loss.backward()"}
+
+    # parity at full size: sampled cells against the oracle's adjoint
+    parity = None
+    if args.adj_sample > 0 and rank == 0:
+        import oracle
+        idx = np.linspace(0, N - 1, args.adj_sample).astype(np.int64)
+        gT = 2.0 * (Tb - T_target).cpu().numpy()
+        r = oracle.RefMech(m)
+        t0 = time.perf_counter()
+        oT, oY, og, ost = r.adjoint_TY(T[idx], Y[idx], p[idx], gT[idx], np.zeros((len(idx), m.ns)),
+                                       oracle_opts(opts_d), nthreads=os.cpu_count() or 1)
+        el = time.perf_counter() - t0
+        gT0 = dT0.cpu().numpy()[idx]
+        gY0 = dY0.cpu().numpy()[:, idx].T
+        gc = np.moveaxis(dcells.cpu().numpy()[:, :, idx], 2, 0)
+        rel = lambda a, b: float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+        parity = {"cells": int(len(idx)), "oracle_s": el, "status_ok": bool(np.all(ost == 0)),
+                  "max_rel_dT0": rel(gT0, oT), "max_rel_dY0": rel(gY0, oY),
+                  "max_rel_dtheta_cells": max(rel(gc[:, :, k], og[:, :, k]) for k in range(3))}
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        import oracle
+        threads = os.cpu_count() or 1
+        k = max(1, min(args.cpu_sample // 16, N))
+        idx = np.linspace(0, N - 1, k).astype(np.int64)
+        r = oracle.RefMech(m)
+        t0 = time.perf_counter()
+        r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(k), np.zeros((k, m.ns)), oracle_opts(opts_d),
+                     nthreads=threads)
+        el = time.perf_counter() - t0
+        cpu = {"value": k / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
+               "sample": f"{k} cells evenly spaced, forward + adjoint ({el:.1f} s)"}
+    line = {
+        "metric": METRIC_ADJ, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "config": 4, "cells_per_gpu": N, "ckpt_cap": cap,
+                   "ckpt_bytes": int(ckpt.numel() * 8),
+                   "l2": "checkpoints larger than L2 (129 MB); no flush" if ckpt.numel() * 8 > 129e6
+                   else "state smaller than L2"},
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "achieved": a_flops / (adj_ms * 1e-3) / 1e12, "peak": peak / 1e12,
+                     "unit": "TFLOP/s", "frac": a_flops / (adj_ms * 1e-3) / peak, "traffic": None,
+                     "peak_source": "derived: 4 FP64 FLOP/clk/SM (measured DFMA rate) x SMs x max SM clock",
+                     "kernel": "adjoint_kernel (+ sum_rows_kernel)", "kernel_ms": adj_ms,
+                     "forward_kernel_ms": fwd_ms,
+                     "forward_frac": f_flops / (fwd_ms * 1e-3) / peak},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": 3 * args.steps,
+        "cells_failed": int((adj_status != 0).sum()),
+        "stats_mean": {"steps": float(sh[0].mean()), "max_steps": int(sh[0].max()), "newton": float(sh[2].mean())},
+        "loss": loss,
+        "adjoint_vs_oracle": parity,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_adjoint(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    cfg = CONFIGS[4]
+    (m, T, Y, p), = make_workload(4, args.cells or cfg["cells"])
+    o = oracle_opts(opts_dict(4, 0))
+    r = oracle.RefMech(m)
+    threads = os.cpu_count() or 1
+    k = max(1, args.ref_sample // 16)
+
+    def sample(kk, off):
+        idx = (np.linspace(0, len(T) - 1, kk).astype(np.int64) + off) % len(T)
+        t0 = time.perf_counter()
+        r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(kk), np.zeros((kk, m.ns)), o, nthreads=threads)
+        return time.perf_counter() - t0
+
+    for w in range(args.warmup):
+        sample(max(1, k // 8), w)
+    el = sum(sample(k, s) for s in range(args.steps))
+    value = k * args.steps / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC_ADJ, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "config": 4},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{k} cells evenly spaced, forward + adjoint, per step"},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,8 +698,11 @@ def main():
     ap.add_argument("--team", type=int, default=0, help="threads per cell (default: the library's choice)")
     ap.add_argument("--tpb", type=int, default=1, help="cells per block with --team 32")
     ap.add_argument("--precision", type=int, default=None, help="0: FP64 Newton matrix, 1: FP32 LU")
+    ap.add_argument("--adj-sample", type=int, default=8, help="--config 4: cells checked against the oracle")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.config == 4:
+        (run_reference_adjoint if args.impl == "reference" else run_adjoint)(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -26,8 +26,8 @@
  *     or CUDA failures; cg_last_error() then describes the failure (per
  *     calling thread). Numerical failures of individual cells are reported in
  *     the per-cell status array, never as a process abort.
- *   - A cg_mech is immutable after creation; concurrent calls with the same
- *     mechanism on different streams are allowed.
+ *   - A cg_mech changes only through the cg_mech_set_* calls; other calls
+ *     with the same mechanism may run concurrently on different streams.
  */
 #ifndef CHEMGB_H
 #define CHEMGB_H
@@ -55,7 +55,9 @@ enum {
     CG_CELL_NEWTON_FAIL = 1,      /* Newton failed at the deepest halving   */
     CG_CELL_STEP_TOO_SMALL = 2,   /* adaptive step fell below hmin          */
     CG_CELL_MAX_STEPS = 3,        /* more than max_steps step attempts      */
-    CG_CELL_NONFINITE = 4         /* input state not finite                 */
+    CG_CELL_NONFINITE = 4,        /* input state not finite                 */
+    CG_CELL_NO_RECORD = 5         /* adjoint: the forward pass left no usable
+                                     checkpoints (failed cell or too few slots) */
 };
 
 /* reaction types (Section 2.2) */
@@ -162,7 +164,9 @@ typedef struct {
     int method;        /* CG_BE, CG_SDIRK2, CG_SDIRK4                                 */
     int reactor;       /* CG_CONV, CG_CONP, CG_CONP_LITERAL                           */
     int adaptive;      /* 1: error-controlled steps (SDIRK only); 0: nsub fixed steps */
-    int precision;     /* CG_FP64 (CG_FP32LU reserved)                                */
+    int precision;     /* CG_FP64, or CG_FP32LU: Newton matrix assembled and factored
+                          in FP32, residual, solves and updates in FP64 (an inexact
+                          Newton whose converged result meets the same tolerances)  */
     int nsub;          /* fixed mode: number of equal steps over dt                   */
     int max_newton;    /* Newton iterations per stage                                 */
     int max_steps;     /* adaptive: step attempts before CG_CELL_MAX_STEPS            */
@@ -222,6 +226,55 @@ cg_status cg_integrate_batch(int n_mech, const cg_mech *const *mechs, const int6
                              double *const *T, double *const *Y, const double *const *p_or_rho,
                              int32_t *const *cell_status, int32_t *const *cell_stats,
                              const cg_integrate_opts *opts, void *stream);
+
+/*
+ * Discrete adjoint (reverse-mode gradients of a loss of the final states).
+ * The paper builds ChemGen for use in differentiable solvers (Section 1); the
+ * derivative here is that of the integrators of Section 3.2 and Appendix A on
+ * their converged stage equations, with the accepted steps (y_n, h_n) frozen
+ * to those of the forward pass (Newton iterations and step-size decisions
+ * are not differentiated). Parameters theta are (ln A, b, Ea) of every
+ * reaction (k_inf for falloff reactions; k_0 held fixed).
+ *
+ * cg_integrate_ckpt: cg_integrate that also records, per cell c, the state
+ * y = (T, C) at the start of every accepted step and the step size:
+ *   ckpt[(c * ckpt_cap + k) * (ns + 2) + i], i <= ns: y_k,  i = ns + 1: h_k;
+ *   record ckpt_n[c] holds the final state and the initial density.
+ *   ckpt[N * ckpt_cap * (ns + 2)] and ckpt_n[N] are caller-owned device
+ *   arrays; ckpt_n[c] = -1 when the cell failed or took more than
+ *   ckpt_cap - 1 steps (its adjoint then reports CG_CELL_NO_RECORD).
+ *   ckpt_cap >= 2. Other arguments and results as cg_integrate.
+ *
+ * cg_integrate_adjoint: from dL/dT_end[N] and dL/dY_end[ns*N] (SoA, device),
+ * computes dL/dT0[N], dL/dY0[ns*N] (through C = rho Y / W, with rho fixed at
+ * constant volume or rho = p / (R T0 sum Y/W) otherwise) and
+ *   dtheta[nr*3]              sum over cells of dL/d(ln A, b, Ea), in the
+ *                             caller's reaction order (may be NULL)
+ *   dtheta_cells[nr*3*N]      per-cell gradients, entry (3 j + k) * N + c
+ *                             (may be NULL: then a stream-ordered temporary)
+ *   cell_status[N]            CG_CELL_OK, CG_CELL_NO_RECORD, or
+ *                             CG_CELL_NEWTON_FAIL (may be NULL)
+ * Cells that do not end CG_CELL_OK contribute zeros. `opts` must be those of
+ * the forward call (the stages are recomputed with them, bit for bit). The
+ * sum over cells is in a fixed order: results do not depend on the launch
+ * shape or on timing. FP64 transposed solves whatever opts->precision.
+ * Errors: as cg_integrate; CG_ECAPACITY when one cell's adjoint arrays do not
+ * fit in shared memory.
+ */
+cg_status cg_integrate_ckpt(const cg_mech *mech, const cg_integrate_opts *opts, int64_t N, double *T,
+                            double *Y, const double *p_or_rho, int32_t *cell_status, int32_t *cell_stats,
+                            double *ckpt, int32_t *ckpt_n, int ckpt_cap, void *stream);
+cg_status cg_integrate_adjoint(const cg_mech *mech, const cg_integrate_opts *opts, int64_t N,
+                               const double *ckpt, const int32_t *ckpt_n, int ckpt_cap,
+                               const double *dT_end, const double *dY_end, double *dT0, double *dY0,
+                               double *dtheta, double *dtheta_cells, int32_t *cell_status, void *stream);
+
+/* Replace ln A, b, Ea of every reaction (host arr[nr*3], the caller's order
+ * and units of cg_mech_desc.arr; the low-pressure limits of falloff
+ * reactions stay as created). Synchronises the device; no call using the
+ * mechanism may be in flight. For parameter fitting with the adjoint.
+ * Errors: CG_EINVAL (NULL or non-finite entries), CG_ECUDA. */
+cg_status cg_mech_set_arrhenius(cg_mech *mech, const double *arr);
 
 /* Same as cg_integrate with HOST arrays: copies the inputs to device memory
  * owned by the mechanism (grown on demand, freed with it), integrates,

@@ -230,6 +230,46 @@ class RefMech:
                               _p(st), int(nthreads))
         return dy0, grad, st
 
+    def adjoint_TY(self, T0, Y0, p_or_rho, dT_end, dY_end, opts: dict, nthreads: int = 1):
+        """The adjoint in the variables a flow solver holds: cells given by
+        (T0, Y0[N, ns], p) (or rho at constant volume), loss gradients
+        dL/dT_end[N], dL/dY_end[N, ns]. Chains the state adjoint through
+        Y_k = W_k C_k / rho with rho = sum W_i C_i (Section 2) at the end and
+        C_k = rho Y_k / W_k at the start (rho given, or p / (R T sum Y/W)).
+        Returns (dL/dT0 [N], dL/dY0 [N, ns], dL/dtheta [N, nr, 3], status)."""
+        reactor = default_opts(**opts)["reactor"]
+        T0 = _f64(T0)
+        Y0 = _f64(Y0)
+        W = self.mech.W
+        C0 = self.concentrations(T0, Y0, p_or_rho, reactor)
+        y0 = self._state(T0, C0)
+        y_end, _, _ = self.integrate_y(y0, opts, nthreads)
+        # dL/dC_end by the chain rule of Y_end(C_end)
+        Cend = y_end[:, 1:]
+        rho_end = (W * Cend).sum(axis=1)
+        Yend = W * Cend / rho_end[:, None]
+        dY_end = _f64(dY_end)
+        J_YC = (W[None, None, :] * (np.eye(self.ns)[None] - Yend[:, :, None])) / rho_end[:, None, None]
+        lam = np.zeros_like(y_end)
+        lam[:, 0] = dT_end
+        lam[:, 1:] = np.einsum("ck,ckm->cm", dY_end, J_YC)   # J_YC[c, k, m] = dY_k / dC_m
+        dy0, g, st = self.adjoint(y0, lam, opts, nthreads)
+        # dC0/dY0 and dC0/dT0
+        if reactor == CONV:
+            rho0 = np.asarray(p_or_rho, dtype=np.float64) * np.ones(len(T0))
+            dC_dY = rho0[:, None, None] * np.eye(self.ns)[None] / W[None, :, None]
+            dC_dT = np.zeros_like(C0)
+        else:
+            sig = (Y0 / W).sum(axis=1)
+            rho0 = np.asarray(p_or_rho, dtype=np.float64) / (R_UNIV * T0 * sig)
+            # C_m = rho Y_m / W_m, d rho / d Y_k = -rho / (W_k sig), d rho / d T0 = -rho / T0
+            dC_dY = (rho0[:, None, None] * np.eye(self.ns)[None] / W[None, :, None]
+                     - (C0[:, :, None] / (W[None, None, :] * sig[:, None, None])))
+            dC_dT = -C0 / T0[:, None]
+        dY0 = np.einsum("cm,cmk->ck", dy0[:, 1:], dC_dY)     # dC_dY[c, m, k] = dC_m / dY_k
+        dT0 = dy0[:, 0] + (dy0[:, 1:] * dC_dT).sum(axis=1)
+        return dT0, dY0, g, st
+
     def tangent(self, y0, dy0, opts: dict, pj: int = -1, pk: int = 0, nthreads: int = 1):
         """Forward sensitivity dy_end for the initial perturbation dy0 and
         the parameter (reaction pj, kind pk: 0 ln A, 1 b, 2 Ea)."""

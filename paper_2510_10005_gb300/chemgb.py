@@ -17,7 +17,8 @@ import numpy as np
 from . import build as _build
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ECAPACITY, CG_EUNSUPPORTED = range(6)
-CG_CELL_OK, CG_CELL_NEWTON_FAIL, CG_CELL_STEP_TOO_SMALL, CG_CELL_MAX_STEPS, CG_CELL_NONFINITE = range(5)
+(CG_CELL_OK, CG_CELL_NEWTON_FAIL, CG_CELL_STEP_TOO_SMALL, CG_CELL_MAX_STEPS, CG_CELL_NONFINITE,
+ CG_CELL_NO_RECORD) = range(6)
 CG_CONV, CG_CONP, CG_CONP_LITERAL = 0, 1, 2
 CG_BE, CG_SDIRK2, CG_SDIRK4 = 0, 1, 2
 CG_FP64, CG_FP32LU = 0, 1
@@ -49,7 +50,8 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_mech_set_launch", "cg_mech_get_launch", "cg_mech_set_smem_limit",
             "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
-            "cg_integrate_noalloc", "cg_autotune", "cg_last_error")
+            "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
+            "cg_integrate_adjoint", "cg_mech_set_arrhenius")
 
 
 def library_path() -> str:
@@ -87,6 +89,10 @@ def load(build_if_missing: bool = False):
     lib.cg_integrate_opts_default.restype = None
     lib.cg_integrate.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, P]
     lib.cg_integrate_host.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P]
+    lib.cg_integrate_ckpt.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, P, P, I, P]
+    lib.cg_integrate_adjoint.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, I, P, P, P, P, P, P,
+                                         P, P]
+    lib.cg_mech_set_arrhenius.argtypes = [P, P]
     lib.cg_last_error.restype = ctypes.c_char_p
     lib.cg_last_error.argtypes = []
     _lib = lib
@@ -226,6 +232,36 @@ def cg_integrate_host(h, opts, T, Y, p_or_rho, status=None, stats=None):
                                     _ptr(p_or_rho), _ptr(status), _ptr(stats)))
 
 
+def cg_integrate_ckpt(h, opts, T, Y, p_or_rho, ckpt, ckpt_n, status=None, stats=None, stream=None):
+    """cg_integrate that records the adjoint's checkpoints: ckpt is a CUDA
+    float64 tensor [N, cap, ns + 2], ckpt_n int32 [N]."""
+    N = T.shape[0]
+    if ckpt.dim() != 3 or ckpt.shape[0] != N or ckpt.shape[2] != h.n + 1:
+        raise ValueError(f"ckpt must be [N, cap, {h.n + 1}]")
+    _check(load().cg_integrate_ckpt(h.ptr, ctypes.byref(opts), N, _dev(T), _dev(Y), _dev(p_or_rho),
+                                    None if status is None else _dev(status, "int32"),
+                                    None if stats is None else _dev(stats, "int32"), _dev(ckpt),
+                                    _dev(ckpt_n, "int32"), ckpt.shape[1], _stream(stream)))
+
+
+def cg_integrate_adjoint(h, opts, ckpt, ckpt_n, dT_end, dY_end, dT0, dY0, dtheta=None, dtheta_cells=None,
+                         status=None, stream=None):
+    """Backward sweep over the checkpoints of cg_integrate_ckpt (CUDA
+    tensors; dtheta [nr, 3], dtheta_cells [nr, 3, N] may be None)."""
+    _check(load().cg_integrate_adjoint(h.ptr, ctypes.byref(opts), dT_end.shape[0], _dev(ckpt),
+                                       _dev(ckpt_n, "int32"), ckpt.shape[1], _dev(dT_end), _dev(dY_end),
+                                       _dev(dT0), _dev(dY0), None if dtheta is None else _dev(dtheta),
+                                       None if dtheta_cells is None else _dev(dtheta_cells),
+                                       None if status is None else _dev(status, "int32"), _stream(stream)))
+
+
+def cg_mech_set_arrhenius(h, arr):
+    """Replace (ln A, b, Ea) of every reaction (host array [nr, 3])."""
+    a = np.ascontiguousarray(arr, dtype=np.float64).reshape(h.nr, 3)
+    _check(load().cg_mech_set_arrhenius(h.ptr, a.ctypes.data))
+    h.arr = a.copy()
+
+
 class MechHandle:
     """Owns one cg_mech."""
 
@@ -247,6 +283,7 @@ class MechHandle:
         self.ptr = h.value
         self.ns, self.nr, self.n = mech.ns, mech.nr, mech.ns + 1
         self.mech = mech
+        self.arr = np.array(self._keep["arr"]).reshape(mech.nr, 3)   # current (ln A, b, Ea)
 
     def close(self):
         if getattr(self, "ptr", None):

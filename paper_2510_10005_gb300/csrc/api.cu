@@ -103,8 +103,9 @@ Schedule make_schedule(std::vector<Term> terms, int lanes_n) {
 
 // Place one cell's arrays: hottest first into shared memory (at most
 // smem_limit bytes per cell), the rest into the cell's global scratch slot.
-// mat_bytes: 8 for the FP64 Newton matrix, 4 for the FP32 one.
-Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit) {
+// mat_bytes: 8 for the FP64 Newton matrix, 4 for the FP32 one; adjoint:
+// add the arrays of the backward sweep (size 0 otherwise).
+Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoint = false) {
     using namespace cg;
     const int n = ns + 1;
     Layout L;
@@ -118,8 +119,13 @@ Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit) {
     size[A_GAM] = 5 * n;
     size[A_PIV] = (n + 1) / 2;
     size[A_RED] = 24;
-    const int order[A_COUNT] = {A_RED, A_PIV, A_G, A_RINV, A_YN, A_Y, A_F, A_S, A_BASE, A_S0,
-                                A_ERR, A_Y1, A_COLA, A_COLB, A_SP, A_V, A_GAM, A_RD};
+    size[A_XF] = adjoint ? nr : 0;
+    size[A_GRAD] = adjoint ? 3 * nr : 0;
+    for (int a : {A_LAM, A_LAMN, A_NU, A_RHS}) size[a] = adjoint ? n : 0;
+    size[A_ACC] = adjoint ? 5 * n : 0;
+    const int order[A_COUNT] = {A_RED, A_PIV, A_G, A_RINV, A_YN, A_Y, A_F, A_S, A_BASE,
+                                A_S0, A_ERR, A_Y1, A_COLA, A_COLB, A_SP, A_V, A_GAM, A_NU,
+                                A_RHS, A_LAM, A_LAMN, A_ACC, A_XF, A_RD, A_GRAD};
     // 1 KiB of the block's shared memory stays free for the kernels' static variables
     const long budget = (long)((smem_limit > 2048 ? smem_limit - 1024 : 1024) / sizeof(double));
     int so = 0, go = 0;
@@ -328,7 +334,12 @@ struct cg_mech {
     DevMech dm;
     Layout L;     // FP64 Newton matrix
     Layout L32;   // FP32 Newton matrix (mixed precision)
+    Layout LA;    // adjoint sweep (FP64 Newton matrix plus the adjoint arrays)
     int ns = 0, nr = 0;
+    std::vector<int> perm;             // internal reaction index -> caller's index
+    std::vector<int> itype;            // reaction types, internal order
+    std::vector<double> arr, arr0;     // caller's Arrhenius triples (caller's order)
+    const int* dperm = nullptr;        // perm on the device
     int tpb = 1;                       // teams per block (team = dm.team threads)
     size_t smem_limit = 0;             // shared memory per cell before arrays spill to scratch
     std::vector<void*> allocs;         // mechanism data
@@ -393,6 +404,9 @@ cg::Task make_task(const cg_mech* m, const IntParams& P, int64_t N, int64_t firs
     t.p = p;
     t.status = status;
     t.stats = stats;
+    t.ckpt = nullptr;
+    t.ckpt_n = nullptr;
+    t.ckpt_cap = 0;
     return t;
 }
 
@@ -505,6 +519,7 @@ cg_status cg_mech_set_smem_limit(cg_mech* m, int64_t bytes) {
     if ((size_t)m->tpb * L.stotal * sizeof(double) > kMaxSmemPerBlock) m->tpb = 1;
     m->L = L;
     m->L32 = L32;
+    m->LA = make_layout(m->ns, m->nr, 8, (size_t)bytes, true);
     m->smem_limit = (size_t)bytes;
     return CG_OK;
 }
@@ -617,7 +632,12 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     m->nr = nr;
     m->L = L;
     m->L32 = make_layout(ns, nr, 4, kMaxSmemPerBlock);
+    m->LA = make_layout(ns, nr, 8, kMaxSmemPerBlock, true);
     m->smem_limit = kMaxSmemPerBlock;
+    m->perm = perm;
+    m->itype = rtype;
+    m->arr.assign(d->arr, d->arr + 3 * (size_t)nr);
+    m->arr0.assign(d->arr0 ? d->arr0 : d->arr, (d->arr0 ? d->arr0 : d->arr) + 3 * (size_t)nr);
     DevMech& dm = m->dm;
     dm.ns = ns;
     dm.nr = nr;
@@ -633,6 +653,10 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     UP(dbeta0, dbeta0) UP(dTa0, dTa0) UP(talpha, talpha) UP(tiT3, tiT3) UP(tiT1, tiT1)
     UP(tT2, tT2) UP(hasT2, hasT2) UP(eff_ptr, eff_ptr) UP(eff_idx, eff_idx) UP(eff_am1, eff_am1)
 #undef UP
+    if ((st = upload(m->allocs, perm, &m->dperm)) != CG_OK) {
+        cg_mech_destroy(m);
+        return st;
+    }
     m->wterms.swap(wterms);
     m->vterms.swap(vterms);
     m->jterms.swap(jterms);
@@ -790,6 +814,114 @@ cg_status cg_integrate_batch(int n_mech, const cg_mech* const* mechs, const int6
     for (int k = 1; k < n_mech; ++k) tpb = std::min(tpb, mechs[k]->tpb);
     cudaError_t e = cg::launch_integrate(tasks, P, team, tpb, true, (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch");
+}
+
+// Forward integration that records the checkpoints of the adjoint.
+cg_status cg_integrate_ckpt(const cg_mech* m, const cg_integrate_opts* o, int64_t N, double* T, double* Y,
+                            const double* p_or_rho, int32_t* cell_status, int32_t* cell_stats, double* ckpt,
+                            int32_t* ckpt_n, int ckpt_cap, void* stream) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    IntParams P;
+    cg_status st = make_params(o, P);
+    if (st != CG_OK) return st;
+    if (N < 0 || ckpt_cap < 2) return fail(CG_EINVAL, "N >= 0 and ckpt_cap >= 2 required");
+    if (N == 0) return CG_OK;
+    if (!T || !Y || !p_or_rho || !ckpt || !ckpt_n) return fail(CG_EINVAL, "NULL array");
+    cg::Tasks tasks;
+    tasks.count = 1;
+    tasks.total = N;
+    tasks.t[0] = make_task(m, P, N, 0, T, Y, p_or_rho, cell_status, cell_stats);
+    tasks.t[0].ckpt = ckpt;
+    tasks.t[0].ckpt_n = ckpt_n;
+    tasks.t[0].ckpt_cap = ckpt_cap;
+    cudaError_t e = cg::launch_integrate(tasks, P, m->dm.team, m->tpb, o->persistent != 0,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch (checkpoints)");
+}
+
+// Backward sweep of the discrete adjoint over the checkpoints of
+// cg_integrate_ckpt.
+cg_status cg_integrate_adjoint(const cg_mech* m, const cg_integrate_opts* o, int64_t N, const double* ckpt,
+                               const int32_t* ckpt_n, int ckpt_cap, const double* dT_end, const double* dY_end,
+                               double* dT0, double* dY0, double* dtheta, double* dtheta_cells,
+                               int32_t* cell_status, void* stream) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    IntParams P;
+    cg_status st = make_params(o, P);
+    if (st != CG_OK) return st;
+    if (N < 0 || ckpt_cap < 2) return fail(CG_EINVAL, "N >= 0 and ckpt_cap >= 2 required");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (N == 0) {
+        if (dtheta && m->nr > 0 &&
+            (e = cudaMemsetAsync(dtheta, 0, 3 * (size_t)m->nr * sizeof(double), s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync");
+        return CG_OK;
+    }
+    if (!ckpt || !ckpt_n || !dT_end || !dY_end || !dT0 || !dY0) return fail(CG_EINVAL, "NULL array");
+    int tpb = m->dm.team > 32 ? 1 : m->tpb;
+    while (tpb > 1 && (size_t)tpb * m->LA.stotal * sizeof(double) > kMaxSmemPerBlock) --tpb;
+    if ((size_t)m->LA.stotal * sizeof(double) > kMaxSmemPerBlock)
+        return fail(CG_ECAPACITY, "adjoint arrays need %zu bytes of shared memory per cell",
+                    (size_t)m->LA.stotal * sizeof(double));
+    cg::AdjTask t;
+    t.M = m->dm;
+    t.L = m->LA;
+    t.N = N;
+    t.ckpt = ckpt;
+    t.ckpt_n = ckpt_n;
+    t.ckpt_cap = ckpt_cap;
+    t.dT_end = dT_end;
+    t.dY_end = dY_end;
+    t.dT0 = dT0;
+    t.dY0 = dY0;
+    t.perm = m->dperm;
+    t.grad_cells = dtheta_cells;
+    t.status = cell_status;
+    void* tmp = nullptr;
+    if (!t.grad_cells && m->nr > 0) {   // per-cell gradients in a stream-ordered temporary
+        if ((e = cudaMallocAsync(&tmp, 3 * (size_t)m->nr * N * sizeof(double), s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMallocAsync (per-cell gradients)");
+        t.grad_cells = static_cast<double*>(tmp);
+    }
+    e = cg::launch_adjoint(t, P, m->dm.team, tpb, dtheta, s);
+    cudaError_t e2 = tmp ? cudaFreeAsync(tmp, s) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    return e2 == cudaSuccess ? CG_OK : cuda_fail(e2, "cudaFreeAsync");
+}
+
+cg_status cg_mech_set_arrhenius(cg_mech* m, const double* arr) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    const int nr = m->nr;
+    if (nr == 0) return CG_OK;
+    if (!arr) return fail(CG_EINVAL, "arr is NULL");
+    for (int k = 0; k < 3 * nr; ++k)
+        if (!std::isfinite(arr[k])) return fail(CG_EINVAL, "arr[%d] not finite", k);
+    std::vector<double> lnA(nr), beta(nr), Ta(nr), dlnA0(nr, 0.0), dbeta0(nr, 0.0), dTa0(nr, 0.0);
+    const std::vector<int>& types = m->itype;
+    for (int jj = 0; jj < nr; ++jj) {
+        const int j = m->perm[jj];
+        lnA[jj] = arr[3 * j];
+        beta[jj] = arr[3 * j + 1];
+        Ta[jj] = arr[3 * j + 2] / kR;
+        if (types[jj] == CG_RXN_LINDEMANN || types[jj] == CG_RXN_TROE) {   // k_0 is kept
+            dlnA0[jj] = m->arr0[3 * j] - arr[3 * j];
+            dbeta0[jj] = m->arr0[3 * j + 1] - arr[3 * j + 1];
+            dTa0[jj] = (m->arr0[3 * j + 2] - arr[3 * j + 2]) / kR;
+        }
+    }
+    const size_t b = nr * sizeof(double);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    if ((e = cudaMemcpy(const_cast<double*>(m->dm.lnA), lnA.data(), b, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(const_cast<double*>(m->dm.beta), beta.data(), b, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(const_cast<double*>(m->dm.Ta), Ta.data(), b, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(const_cast<double*>(m->dm.dlnA0), dlnA0.data(), b, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(const_cast<double*>(m->dm.dbeta0), dbeta0.data(), b, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(const_cast<double*>(m->dm.dTa0), dTa0.data(), b, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy (Arrhenius parameters)");
+    m->arr.assign(arr, arr + 3 * (size_t)nr);
+    return CG_OK;
 }
 
 cg_status cg_integrate_host(const cg_mech* mc, const cg_integrate_opts* o, int64_t N, double* T,

@@ -35,7 +35,7 @@ constexpr unsigned kFull = 0xffffffffu;
 enum { RXN_ELEM = 0, RXN_TB = 1, RXN_LIND = 2, RXN_TROE = 3 };
 enum { R_CONV = 0, R_CONP = 1, R_CONP_LIT = 2 };
 enum { CELL_OK = 0, CELL_NEWTON_FAIL = 1, CELL_STEP_TOO_SMALL = 2, CELL_MAX_STEPS = 3,
-       CELL_NONFINITE = 4 };
+       CELL_NONFINITE = 4, CELL_NO_RECORD = 5 };
 
 // rows of the per-species thermo table th[k * ns + i]
 enum {
@@ -80,6 +80,11 @@ enum {
     A_GAM,      // 5 n: stage derivatives
     A_PIV,      // n ints
     A_RED,      // 24 doubles: cross-warp reduction scratch (always shared)
+    // adjoint only (size 0 in the forward layouts)
+    A_XF,       // nr: d ln q_j / d ln k_j
+    A_GRAD,     // 3 nr: dL/d(ln A, b, Ea), reaction-major
+    A_LAM, A_LAMN, A_NU, A_RHS,   // n each
+    A_ACC,      // 5 n: sum over later stages of h a_qp J_q^T nu_q
     A_COUNT
 };
 
@@ -95,6 +100,7 @@ struct Ws {
     int ld;
     double *G, *RD, *SP, *V, *yn, *Y, *base, *S, *S0, *f, *err, *y1, *colA, *colB, *rinv, *Gam, *red;
     int* piv;
+    double *xf, *grad, *lam, *lamn, *nu, *rhs, *acc;
 };
 
 __device__ __forceinline__ Ws make_ws(const Layout& L, double* sbase, double* gbase) {
@@ -108,6 +114,8 @@ __device__ __forceinline__ Ws make_ws(const Layout& L, double* sbase, double* gb
     w.f = p[A_F]; w.err = p[A_ERR]; w.y1 = p[A_Y1]; w.colA = p[A_COLA]; w.colB = p[A_COLB];
     w.rinv = p[A_RINV]; w.Gam = p[A_GAM]; w.red = p[A_RED];
     w.piv = reinterpret_cast<int*>(p[A_PIV]);
+    w.xf = p[A_XF]; w.grad = p[A_GRAD]; w.lam = p[A_LAM]; w.lamn = p[A_LAMN];
+    w.nu = p[A_NU]; w.rhs = p[A_RHS]; w.acc = p[A_ACC];
     return w;
 }
 
@@ -268,7 +276,7 @@ static __device__ __forceinline__ double rcp_nr(double x) {
 // third-body weight w_j and the mass-action partials). Returns sum C.
 template <int TEAM>
 __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deriv,
-                        int lane) {
+                        int lane, double* xf = nullptr) {   // xf: d ln q_j / d ln k_j (adjoint)
     const int ns = M.ns, nr = M.nr;
     const double T = y[0];
     const double* C = y + 1;
@@ -311,6 +319,7 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
         if (type == RXN_ELEM) {
             kf = kA;
             dkf_dT = kA * dlnkA;
+            if (xf) xf[j] = 1.0;
         } else {
             double Mx = Mc;
             const int e1 = __ldg(M.eff_ptr + j + 1);
@@ -320,6 +329,7 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                 kf = Mx * kA;
                 dkf_dT = kf * dlnkA;
                 dkf_dM = kA;
+                if (xf) xf[j] = 1.0;
             } else {
                 const double db = __ldg(M.dbeta0 + j), dTa = __ldg(M.dTa0 + j);
                 const double ratio = exp(__ldg(M.dlnA0 + j) + db * lnT - dTa * invT);   // k0 / kinf
@@ -361,6 +371,8 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                 const double dkf_dPr = kA * F * ip * (ip + dlogF_dP);
                 dkf_dT = kf * dlnkA + dkf_dPr * Pr * dlnr + kf * kLn10 * dlogF_dT;
                 dkf_dM = dkf_dPr * ratio;
+                // ln k_f = ln k_inf + ln(Pr/(1+Pr)) + ln F, Pr proportional to 1/k_inf
+                if (xf) xf[j] = Pr * ip - dlogF_dP;
             }
         }
         // mass-action products and their slot partials
@@ -653,6 +665,33 @@ __device__ void lu_solve(const MT* G, int n, int ld, const int* piv, const doubl
         for (int i = lane; i < j; i += TEAM) x[i] = fma(-static_cast<double>(G[i * ld + j]), xj, x[i]);
         team_sync<TEAM>();
     }
+}
+
+// x <- G^{-T} x with the factors of lu_factor: with P G = L U, G^T = U^T L^T P,
+// so solve U^T v = x (forward, by rows of U), L^T z = v (backward, by rows
+// of L), then undo the row interchanges in reverse order.
+template <int TEAM, class MT>
+__device__ void lu_solve_t(const MT* G, int n, int ld, const int* piv, const double* rinv, double* x,
+                           int lane) {
+    for (int j = 0; j < n; ++j) {               // U^T: column j of U^T is row j of U
+        const double vj = x[j] * rinv[j];
+        team_sync<TEAM>();
+        if (lane == 0) x[j] = vj;
+        for (int i = j + 1 + lane; i < n; i += TEAM)
+            x[i] = fma(-static_cast<double>(G[j * ld + i]), vj, x[i]);
+        team_sync<TEAM>();
+    }
+    for (int j = n - 1; j > 0; --j) {           // L^T (unit diagonal): row j of L, columns < j
+        const double zj = x[j];
+        for (int i = lane; i < j; i += TEAM) x[i] = fma(-static_cast<double>(G[j * ld + i]), zj, x[i]);
+        team_sync<TEAM>();
+    }
+    if (lane == 0)
+        for (int k = n - 1; k >= 0; --k) {
+            const int p = piv[k];
+            if (p != k) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
+        }
+    team_sync<TEAM>();
 }
 
 // weighted RMS norm with w_i = atol + rtol max(|a_i|, |b_i|)

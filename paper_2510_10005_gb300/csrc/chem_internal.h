@@ -19,6 +19,31 @@ struct Task {
     const double* p;
     int32_t* status;
     int32_t* stats;
+    // optional checkpoints of the accepted steps (adjoint): cell c's step k
+    // is ckpt[(c * ckpt_cap + k) * (n + 1) + i] = (y_k, h_k); entry
+    // ckpt_n[c] holds the final state and the initial density rho_0;
+    // ckpt_n[c] = -1 when the cell failed or cap was too small
+    double* ckpt;
+    int32_t* ckpt_n;
+    int ckpt_cap;
+};
+
+// One adjoint launch: cells integrated by a checkpointing forward call.
+struct AdjTask {
+    DevMech M;
+    Layout L;
+    int64_t N;
+    const double* p;           // pressure (CONP) or density (CONV)
+    const double* ckpt;
+    const int32_t* ckpt_n;
+    int ckpt_cap;
+    const double* dT_end;      // dL/dT at the end        [N]
+    const double* dY_end;      // dL/dY_k at the end      [ns][N]
+    double* dT0;               // out: dL/dT0             [N]
+    double* dY0;               // out: dL/dY0_k           [ns][N]
+    const int* perm;           // internal reaction index -> caller's index
+    double* grad_cells;        // out: dL/dtheta per cell [nr][3][N], caller's reaction order
+    int32_t* status;           // out
 };
 
 constexpr int kMaxTasks = 4;
@@ -45,5 +70,10 @@ cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, i
 cudaError_t launch_integrate_on(const Tasks& tasks, const IntParams& P, int team, int tpb, double* scratch,
                                 int64_t scratch_doubles, unsigned long long* counter, cudaStream_t st);
 int64_t integrate_slot_doubles(const Tasks& tasks);
+// Backward sweep of the discrete adjoint over the cells of t (persistent
+// launch with `team` threads per cell), then, with dtheta != nullptr, the
+// fixed-order sum of the per-cell parameter gradients into dtheta[nr][3].
+cudaError_t launch_adjoint(const AdjTask& t, const IntParams& P, int team, int tpb, double* dtheta,
+                           cudaStream_t st);
 
 }  // namespace cg

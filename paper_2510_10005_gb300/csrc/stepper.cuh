@@ -1,0 +1,224 @@
+// Pieces shared by the forward integration and the adjoint sweep: the team's
+// position in a launch and its cell loop, one implicit Runge-Kutta step
+// (Section 3.2, Appendix A), checkpoints, and the host-side launch helpers.
+#pragma once
+
+#include "chem_device.cuh"
+#include "chem_internal.h"
+
+namespace cg {
+
+constexpr double kR = 8314.46261815324;   // J/(kmol K)
+
+// Position of this team in the launch.
+template <int TEAM>
+struct TeamPos {
+    int lane, tib, tpb;
+    int64_t id, count;
+    __device__ __forceinline__ TeamPos() {
+        lane = team_lane<TEAM>();
+        tpb = blockDim.x / TEAM;
+        tib = threadIdx.x / TEAM;
+        id = (int64_t)blockIdx.x * tpb + tib;
+        count = (int64_t)gridDim.x * tpb;
+    }
+};
+
+// Next global cell index: from the work counter (every thread of the team
+// gets the same value) or the fixed stride.
+template <int TEAM>
+__device__ __forceinline__ int64_t next_cell(unsigned long long* counter, int64_t prev, int64_t stride,
+                                             int lane) {
+    if (!counter) return prev + stride;
+    if constexpr (TEAM == 32) {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(counter, 1ull);
+        return (int64_t)__shfl_sync(kFull, v, 0);
+    } else {
+        __shared__ unsigned long long slot;
+        __syncthreads();
+        if (lane == 0) slot = atomicAdd(counter, 1ull);
+        __syncthreads();
+        return (int64_t)slot;
+    }
+}
+
+template <int TEAM>
+__device__ __forceinline__ int64_t first_cell(unsigned long long* counter, int64_t id, int lane) {
+    return counter ? next_cell<TEAM>(counter, 0, 0, lane) : id;
+}
+
+// ---------------------------------------------------------------------------
+// integration
+
+struct Counters {
+    int steps, rejects, newton, lu;
+};
+
+// One step of size h from W.yn: stages of the tableau in stage-derivative
+// form (Appendix A), each by full Newton with G = I - a_pp h J(Y_p). On
+// success y1 holds the new state and err the (filtered) embedded estimate.
+// MT = float: G is assembled and factored in FP32 (an inexact Newton whose
+// residual, update and convergence test stay in FP64).
+template <int TEAM, class MT>
+__device__ bool rk_step(const DevMech& M, const Ws& W, const IntParams& P, double h, Counters& cnt,
+                        int lane) {
+    const int n = M.n;
+    double* yn = W.yn;
+    double* Y = W.Y;
+    double* base = W.base;
+    double* S = W.S;
+    double* S0 = W.S0;
+    double* f = W.f;
+    MT* G = reinterpret_cast<MT*>(W.G);
+    if (!P.start_zero) {   // first Newton iterate of every stage: Gamma = S(y_n)
+        const double Mc = rates<TEAM>(M, W, yn, false, lane);
+        assemble_source<TEAM>(M, W, yn, P.reactor, Mc, lane);
+        for (int i = lane; i < n; i += TEAM) S0[i] = S[i];
+        team_sync<TEAM>();
+    }
+    for (int p = 0; p < P.s; ++p) {
+        const double gh = P.A[p][p] * h;
+        double* Gp = W.Gam + p * n;
+        for (int i = lane; i < n; i += TEAM) {
+            double b = yn[i];
+            for (int j = 0; j < p; ++j) b = fma(h * P.A[p][j], W.Gam[j * n + i], b);
+            base[i] = b;
+            Gp[i] = P.start_zero ? 0.0 : S0[i];
+        }
+        team_sync<TEAM>();
+        bool conv = false;
+        for (int k = 0; k < P.max_newton; ++k) {
+            for (int i = lane; i < n; i += TEAM) Y[i] = fma(gh, Gp[i], base[i]);
+            team_sync<TEAM>();
+            const double Mc = rates<TEAM>(M, W, Y, true, lane);
+            const SrcInfo si = assemble_source<TEAM>(M, W, Y, P.reactor, Mc, lane);
+            assemble_jacobian<TEAM, MT>(M, W, Y, P.reactor, si, gh, nullptr, lane);
+            for (int i = lane; i < n; i += TEAM) f[i] = S[i] - Gp[i];   // -f(Gamma)
+            team_sync<TEAM>();
+            cnt.newton++;
+            cnt.lu++;
+            if (!lu_factor<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, W.red, lane)) return false;
+            lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, f, lane);
+            for (int i = lane; i < n; i += TEAM) {
+                const double g = Gp[i] + f[i];
+                Gp[i] = g;
+                f[i] *= gh;                  // change of the stage state
+                Y[i] = fma(gh, g, base[i]);
+            }
+            team_sync<TEAM>();
+            const double nrm = wrms<TEAM>(f, yn, Y, n, P.rtol, P.atol, W.red, lane);
+            if (!isfinite(nrm)) return false;
+            if (nrm <= P.newton_tol) { conv = true; break; }
+        }
+        if (!conv) return false;
+    }
+    double* y1 = W.y1;
+    double* err = W.err;
+    bool bad = false;
+    for (int i = lane; i < n; i += TEAM) {
+        double v = yn[i], e = 0.0;
+        for (int p = 0; p < P.s; ++p) {
+            const double g = W.Gam[p * n + i];
+            v = fma(h * P.b[p], g, v);
+            e = fma(h * (P.b[p] - P.bh[p]), g, e);
+        }
+        y1[i] = v;
+        err[i] = e;
+        bad |= !isfinite(v);
+    }
+    team_sync<TEAM>();
+    if (team_any<TEAM>(bad, W.red)) return false;
+    if (P.adaptive && P.err_filter) lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, err, lane);
+    // admissible: T > 0 and C_i >= -neg_tol sum C
+    double cs = 0.0;
+    for (int i = 1 + lane; i < n; i += TEAM) cs += y1[i];
+    cs = team_sum<TEAM>(cs, W.red);
+    bool neg = false;
+    for (int i = 1 + lane; i < n; i += TEAM) neg |= y1[i] < -P.neg_tol * cs;
+    neg = team_any<TEAM>(neg, W.red) || !(y1[0] > 0.0);
+    return !neg;
+}
+
+template <int TEAM>
+__device__ __forceinline__ void copy_vec(double* dst, const double* src, int n, int lane) {
+    for (int i = lane; i < n; i += TEAM) dst[i] = src[i];
+    team_sync<TEAM>();
+}
+
+// Checkpoint k of a cell: (y_k, h_k) when it fits in cap entries (the
+// record after the last step holds the final state and the density that
+// converted the initial mass fractions).
+template <int TEAM>
+__device__ __forceinline__ void save_step(double* ck, int cap, int k, const double* y, double h, int n,
+                                          int lane) {
+    if (!ck || k >= cap) return;
+    double* e = ck + (int64_t)k * (n + 1);
+    for (int i = lane; i < n; i += TEAM) e[i] = y[i];
+    if (lane == 0) e[n] = h;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers
+
+static inline cudaError_t set_smem(const void* fn, size_t smem) {
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+// Blocks that keep every SM full (persistent launches).
+static inline cudaError_t resident_blocks(const void* fn, int threads, size_t smem, int64_t* out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+    *out = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
+static inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Global scratch slots (one per team) and the work counter, allocated
+// stream-ordered for this launch and released after it.
+struct LaunchMem {
+    double* gscratch = nullptr;
+    unsigned long long* counter = nullptr;
+};
+
+static inline cudaError_t get_mem(int64_t teams, int64_t gstride, bool need_counter, cudaStream_t st,
+                           LaunchMem& m) {
+    cudaError_t e;
+    if (gstride) {
+        void* p = nullptr;
+        if ((e = cudaMallocAsync(&p, (size_t)(teams * gstride) * sizeof(double), st)) != cudaSuccess)
+            return e;
+        m.gscratch = static_cast<double*>(p);
+    }
+    if (need_counter) {
+        void* p = nullptr;
+        if ((e = cudaMallocAsync(&p, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        m.counter = static_cast<unsigned long long*>(p);
+        return cudaMemsetAsync(m.counter, 0, sizeof(unsigned long long), st);
+    }
+    return cudaSuccess;
+}
+
+static inline cudaError_t put_mem(LaunchMem& m, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (m.gscratch) e = cudaFreeAsync(m.gscratch, st);
+    if (m.counter && e == cudaSuccess) e = cudaFreeAsync(m.counter, st);
+    return e;
+}
+
+#define CG_DISPATCH_TEAM(team, CALL)                         \
+    switch (team) {                                          \
+        case 32: return CALL(32);                            \
+        case 64: return CALL(64);                            \
+        case 128: return CALL(128);                          \
+        case 256: return CALL(256);                          \
+        default: return cudaErrorInvalidValue;               \
+    }
+
+}  // namespace cg

@@ -115,3 +115,45 @@ def test_adjoint_against_finite_differences(h2_case):
         yy[:, 0] += s * 1e-3
         out.append(r.replay(yy, o, hs, hn)[0][:, 0])
     np.testing.assert_allclose((out[0] - out[1]) / 2e-3, dy0[:, 0], rtol=1e-6)
+
+
+@pytest.mark.parametrize("reactor", [oracle.CONP, oracle.CONV])
+def test_adjoint_in_flow_variables_against_finite_differences(mechs, reactor):
+    """adjoint_TY (the state adjoint chained through Y = W C / rho at the end
+    and C = rho Y / W at the start) against central differences of
+    L = sum_c a_c T_end + b_c . Y_end over (T0, Y0), steps replayed."""
+    m = mechs["h2"]
+    r = oracle.RefMech(m)
+    T, Y, p = inputs.field_reactor(m, 3, (1200, 1350), (1, 1.5), (0.8, 1.2), "H2", seed=4)
+    if reactor == oracle.CONV:
+        p = p / (inputs.R_UNIV * T * (Y / m.W).sum(axis=1))   # the density of the same state
+    o = dict(method=oracle.SDIRK4, adaptive=1, dt=1e-5, rtol=1e-8, atol=1e-14, reactor=reactor,
+             newton_tol=1e-6, max_newton=20)
+    rng = np.random.default_rng(5)
+    a = rng.normal(size=len(T))
+    b = rng.normal(size=Y.shape)
+    dT0, dY0, g, st = r.adjoint_TY(T, Y, p, a, b, o)
+    assert np.all(st == 0)
+    y0 = np.concatenate([T[:, None], r.concentrations(T, Y, p, reactor)], axis=1)
+    _, st, hs, hn = r.integrate_hist(y0, o)
+    assert np.all(st == 0) and np.all(hn > 0)
+
+    def loss(T_, Y_):
+        y = np.concatenate([T_[:, None], r.concentrations(T_, Y_, p, reactor)], axis=1)
+        ye, s2 = r.replay(y, o, hs, hn)
+        assert np.all(s2 == 0)
+        return a * ye[:, 0] + (b * r.mass_fractions(ye[:, 1:])).sum(axis=1)
+
+    dT = 1e-3
+    fd = (loss(T + dT, Y) - loss(T - dT, Y)) / (2 * dT)
+    np.testing.assert_allclose(fd, dT0, rtol=1e-6)
+    scale = np.abs(dY0).max()
+    L0 = loss(T, Y)
+    for k in range(m.ns):
+        dY = np.zeros_like(Y)
+        dY[:, k] = 1e-7
+        if np.all(Y[:, k] > 1e-5):
+            fd = (loss(T, Y + dY) - loss(T, Y - dY)) / 2e-7
+        else:   # absent species: one-sided second-order difference (no negative mass fraction)
+            fd = (-3 * L0 + 4 * loss(T, Y + dY) - loss(T, Y + 2 * dY)) / 2e-7
+        np.testing.assert_allclose(fd, dY0[:, k], rtol=1e-5, atol=1e-6 * scale)

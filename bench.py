@@ -77,6 +77,28 @@ CONFIGS = {
 }
 
 
+# DRAM bytes per cell of integrate_kernel from one ncu capture (65,536 cells of
+# the flame field, dram__bytes_read.sum + dram__bytes_write.sum = 29,516,032 +
+# 4,864 B), valid only for the kernel sources it was taken on (sha256 of the
+# files below, concatenated); scaled to a launch by its cell count.
+TRAFFIC_SOURCES = ("kernels.cu", "chem_device.cuh", "stepper.cuh", "chem_internal.h")
+TRAFFIC = {2: dict(bytes_per_cell=(29516032 + 4864) / 65536,
+                   sha256="c0954d2bd5be8818cc4e19a9515a7ca92e277ebc9d6a3a93237e2244d07580af")}
+
+
+def measured_traffic(config: int, cells: int):
+    import hashlib
+    t = TRAFFIC.get(config)
+    if t is None:
+        return None
+    csrc = os.path.join(ROOT, "paper_2510_10005_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes_per_cell"] * cells if h.hexdigest() == t["sha256"] else None
+
+
 def algorithmic_flops_per_newton(n_species: int, n_reactions: int, j_terms: int, fp32_lu: bool) -> float:
     """FP64 flops of one Newton iteration of one cell: LU 2n^3/3 (FP64 mode
     only), two triangular solves 2n^2, Newton matrix 2n^2, temperature row
@@ -419,7 +441,7 @@ def run_gpu(args):
                    else "state smaller than L2; each step restores it from a second copy"},
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(args.config, N_total),
                      "peak_source": "derived: 4 FP64 FLOP/clk/SM (measured DFMA rate) x SMs x max SM clock",
                      "kernel": "integrate_kernel", "newton_per_launch": newton},
         "cpu_baseline": cpu,

@@ -238,8 +238,8 @@ def cpu_oracle_sample(parts, opts, n_sample: int, threads: int):
 
 
 def dist_env():
-    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
-            int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2510_10005_gb300 import multirank
+    return multirank.env()
 
 
 def run_reference(args):
@@ -272,7 +272,7 @@ def run_reference(args):
 
 def run_gpu(args):
     import torch
-    from paper_2510_10005_gb300 import chemgb
+    from paper_2510_10005_gb300 import chemgb, multirank
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -342,10 +342,7 @@ def run_gpu(args):
             integrate()
         step = graph.replay
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = multirank.barrier
 
     for _ in range(args.warmup):
         step()
@@ -360,13 +357,8 @@ def run_gpu(args):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * N_total * args.steps / (ms * 1e-3)
+    ms = multirank.max_over_ranks(ev0.elapsed_time(ev1), dev)
+    value = multirank.job_throughput(N_total, ws, args.steps, ms * 1e-3)
     launch_ms = ms / args.steps
 
     newton, flops, failed, stat_means = 0, 0.0, 0, []
@@ -398,12 +390,8 @@ def run_gpu(args):
             chemgb.cg_integrate_host(handles[0], opts, Th, Yh, ph, sh_, sth)
             if k > 0:   # the first call allocates the library's host-call workspace: untimed
                 e2e_t += time.perf_counter() - t0
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_t = float(t.item())
-        e2e = {"value": ws * N * args.e2e_steps / e2e_t, "unit": "cells/s",
+        e2e_t = multirank.max_over_ranks(e2e_t, dev)
+        e2e = {"value": multirank.job_throughput(N, ws, args.e2e_steps, e2e_t), "unit": "cells/s",
                "h2d_bytes_per_step": N * (m.ns + 2) * 8, "d2h_bytes_per_step": N * (m.ns + 1) * 8 + 20 * N,
                "steps": args.e2e_steps}
 
@@ -476,7 +464,7 @@ def adjoint_flops(m, stats, s_stages: int) -> float:
 def run_adjoint(args):
     """--config 4: forward with checkpoints plus the discrete adjoint."""
     import torch
-    from paper_2510_10005_gb300 import autograd, chemgb
+    from paper_2510_10005_gb300 import autograd, chemgb, multirank
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -538,10 +526,7 @@ def run_adjoint(args):
         if split:
             ev[2].record(stream)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = multirank.barrier
 
     for _ in range(args.warmup):
         step()
@@ -559,15 +544,9 @@ def run_adjoint(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        # the parameter gradient of the whole job: one sum over ranks
-        dist.all_reduce(dth)
-    value = ws * N * args.steps / (ms * 1e-3)
+    ms = multirank.max_over_ranks(e0.elapsed_time(e1), dev)
+    multirank.sum_over_ranks_(dth)        # the parameter gradient of the whole job
+    value = multirank.job_throughput(N, ws, args.steps, ms * 1e-3)
     sh = stats.cpu().numpy()
     s_stages = 5
     a_flops = adjoint_flops(m, sh, s_stages)
@@ -605,7 +584,8 @@ def run_adjoint(args):
             torch.cuda.synchronize(dev)
             if k > 0:
                 e2e_t += time.perf_counter() - t0
-        e2e = {"value": ws * N * args.e2e_steps / e2e_t, "unit": "cells/s",
+        e2e_t = multirank.max_over_ranks(e2e_t, dev)
+        e2e = {"value": multirank.job_throughput(N, ws, args.e2e_steps, e2e_t), "unit": "cells/s",
                "h2d_bytes_per_step": N * (m.ns + 2) * 8,
                "d2h_bytes_per_step": N * (m.ns + 1) * 8 + m.nr * 3 * 8, "steps": args.e2e_steps,
                "api": "paper_2510_10005_gb300.autograd.integrate + loss.backward()"}

@@ -9,7 +9,7 @@ Tolerances (derived from the arithmetic, also in the design doc):
   * J: 1e-10 of the entry plus 1e-12 of its row's largest entry.
   * Fixed-step integration (backward Euler, Newton iterated to 1e-10 of the
     state): relative 1e-10 on T and on every Y_k above 1e-12, absolute 1e-20
-    below (the benchmark spec's fixed-step bar, with the floor where a mass fraction
+    below (the fixed-step parity bar, with the floor where a mass fraction
     carries no more digits than the Newton tolerance leaves it).
   * Adaptive integration: within the integrator's rtol (1e-6).
 """

@@ -51,7 +51,7 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
-            "cg_integrate_adjoint", "cg_mech_set_arrhenius")
+            "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check")
 
 
 def library_path() -> str:
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = False):
     lib.cg_integrate_adjoint.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, I, P, P, P, P, P, P,
                                          P, P]
     lib.cg_mech_set_arrhenius.argtypes = [P, P]
+    lib.cgx_exp_check.argtypes = [P, L, P, P, P, P]
     lib.cg_last_error.restype = ctypes.c_char_p
     lib.cg_last_error.argtypes = []
     _lib = lib
@@ -260,6 +261,11 @@ def cg_mech_set_arrhenius(h, arr):
     a = np.ascontiguousarray(arr, dtype=np.float64).reshape(h.nr, 3)
     _check(load().cg_mech_set_arrhenius(h.ptr, a.ctypes.data))
     h.arr = a.copy()
+
+
+def cgx_exp_check(h, x, y_tab, y_lib, stream=None):
+    """Test hook: the library's table-driven exp and CUDA's exp of x."""
+    _check(load().cgx_exp_check(h.ptr, x.shape[0], _dev(x), _dev(y_tab), _dev(y_lib), _stream(stream)))
 
 
 class MechHandle:

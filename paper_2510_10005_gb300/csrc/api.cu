@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "chemgb.h"
+#include "chemgb_testing.h"
 #include "chem_internal.h"
 
 using cg::DevMech;
@@ -372,18 +373,62 @@ template <class T> cg_status upload_sched(cg_mech* m, const std::vector<T>& h, c
     return upload(m->sched_allocs, h, out);
 }
 
+// Reaction chunks of the rates loop for teams of `team` threads: runs of at
+// most 32 consecutive reactions (internal order, sorted by type) that all
+// have or all lack the falloff branch, so that no warp runs both branches;
+// chunks are dealt to the team's warps by estimated cost (a falloff chunk
+// about three plain ones), longest first onto the least-loaded warp.
+void make_rate_chunks(const std::vector<int>& itype, int team, std::vector<int>& ptr, std::vector<int>& first,
+                      std::vector<int>& len) {
+    const int nw = team / 32, nr = (int)itype.size();
+    struct Chunk { int first, len; double cost; };
+    std::vector<Chunk> all;
+    for (int j = 0; j < nr;) {
+        const bool fall = itype[j] == CG_RXN_LINDEMANN || itype[j] == CG_RXN_TROE;
+        int k = j;
+        while (k < nr && k - j < 32 && (itype[k] == CG_RXN_LINDEMANN || itype[k] == CG_RXN_TROE) == fall) ++k;
+        all.push_back({j, k - j, fall ? 3.0 : 1.0});
+        j = k;
+    }
+    std::vector<Chunk> order = all;
+    std::stable_sort(order.begin(), order.end(), [](const Chunk& a, const Chunk& b) { return a.cost > b.cost; });
+    std::vector<std::vector<Chunk>> per(nw);
+    std::vector<double> load(nw, 0.0);
+    for (const Chunk& c : order) {
+        int best = 0;
+        for (int w = 1; w < nw; ++w)
+            if (load[w] < load[best]) best = w;
+        per[best].push_back(c);
+        load[best] += c.cost;
+    }
+    ptr.assign(1, 0);
+    first.clear();
+    len.clear();
+    for (int w = 0; w < nw; ++w) {
+        std::sort(per[w].begin(), per[w].end(), [](const Chunk& a, const Chunk& b) { return a.first < b.first; });
+        for (const Chunk& c : per[w]) {
+            first.push_back(c.first);
+            len.push_back(c.len);
+        }
+        ptr.push_back((int)first.size());
+    }
+}
+
 cg_status build_schedules(cg_mech* m, int team) {
     for (void* p : m->sched_allocs) cudaFree(p);
     m->sched_allocs.clear();
     const Schedule ws = make_schedule(m->wterms, team), vs = make_schedule(m->vterms, team),
                    js = make_schedule(m->jterms, team);
+    std::vector<int> rc_ptr, rc_first, rc_len;
+    make_rate_chunks(m->itype, team, rc_ptr, rc_first, rc_len);
     DevMech& dm = m->dm;
     cg_status st;
     if ((st = upload_sched(m, ws.dst, &dm.w_dst)) || (st = upload_sched(m, ws.src, &dm.w_src)) ||
         (st = upload_sched(m, ws.fac, &dm.w_fac)) || (st = upload_sched(m, vs.dst, &dm.v_dst)) ||
         (st = upload_sched(m, vs.src, &dm.v_src)) || (st = upload_sched(m, vs.fac, &dm.v_fac)) ||
         (st = upload_sched(m, js.dst, &dm.j_dst)) || (st = upload_sched(m, js.src, &dm.j_src)) ||
-        (st = upload_sched(m, js.fac, &dm.j_fac)))
+        (st = upload_sched(m, js.fac, &dm.j_fac)) || (st = upload_sched(m, rc_ptr, &dm.rc_ptr)) ||
+        (st = upload_sched(m, rc_first, &dm.rc_first)) || (st = upload_sched(m, rc_len, &dm.rc_len)))
         return st;
     dm.w_len = ws.len;
     dm.v_len = vs.len;
@@ -474,6 +519,13 @@ cg_status validate(const cg_mech_desc* d) {
 extern "C" {
 
 const char* cg_last_error(void) { return g_err.c_str(); }
+
+cg_status cgx_exp_check(const cg_mech* m, int64_t n, const double* x, double* y_tab, double* y_lib,
+                        void* stream) {
+    if (!m || n < 0 || (n > 0 && (!x || !y_tab || !y_lib))) return fail(CG_EINVAL, "bad arguments");
+    cudaError_t e = cg::launch_exp_check(m->dm, n, x, y_tab, y_lib, (cudaStream_t)stream);
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "exp check launch");
+}
 
 void cg_mech_destroy(cg_mech* m) {
     if (!m) return;
@@ -654,6 +706,12 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     UP(tT2, tT2) UP(hasT2, hasT2) UP(eff_ptr, eff_ptr) UP(eff_idx, eff_idx) UP(eff_am1, eff_am1)
 #undef UP
     if ((st = upload(m->allocs, perm, &m->dperm)) != CG_OK) {
+        cg_mech_destroy(m);
+        return st;
+    }
+    std::vector<double> exp2j(64);   // 2^(j/64), rounded once from extended precision
+    for (int j = 0; j < 64; ++j) exp2j[j] = (double)std::exp2((long double)j / 64.0L);
+    if ((st = upload(m->allocs, exp2j, &dm.exp2j)) != CG_OK) {
         cg_mech_destroy(m);
         return st;
     }

@@ -66,6 +66,11 @@ struct DevMech {
     int w_len, v_len, j_len;
     const int *w_dst, *w_src, *v_dst, *v_src, *j_dst, *j_src;
     const double *w_fac, *v_fac, *j_fac;
+    // reaction chunks of the rates loop: runs of at most 32 reactions of one
+    // kind (with or without falloff); warp w of a team takes chunks
+    // rc_ptr[w] .. rc_ptr[w+1]-1, chunk c = reactions rc_first[c] + 0 .. rc_len[c]-1
+    const int *rc_ptr, *rc_first, *rc_len;
+    const double* exp2j;         // 2^(j/64), j = 0..63 (exp_tab)
 };
 
 // Working arrays of one cell. Each lives in the team's slice of shared
@@ -269,6 +274,35 @@ static __device__ __forceinline__ double rcp_nr(double x) {
     return fma(r, t, r);
 }
 
+// e^x by Tang's table-driven method (ACM Trans. Math. Softw. 15(2), 1989):
+// x = (64 m + j) ln2/64 + r with |r| <= ln2/128, e^x = 2^m 2^(j/64) e^r. The
+// integer 64 m + j is round(x 64/ln2), taken from the low bits of
+// x 64/ln2 + 1.5 2^52; ln2/64 is split in two parts (Cody and Waite) so that
+// r keeps the rounding of x only; e^r - 1 is its Taylor polynomial to degree
+// 5 (truncation below 3e-17 relative); 2^(j/64) comes from a 64-entry table
+// of correctly rounded values built on the host; 2^m is added to the
+// exponent field. Ten FP64 operations. |x| >= 707 (where 2^m would leave
+// the normal range), infinities and NaN go to the library exp. Checked
+// against the library exp to 2 ulp in the tests.
+static __device__ __forceinline__ double exp_tab(double x, const double* __restrict__ tab) {
+    const int hi = __double2hiint(x);
+    if ((hi & 0x7fffffff) >= 0x40861800) return exp(x);
+    const double shift = 0x1.8p52;
+    const double t = fma(x, 0x1.71547652b82fep+6, shift);   // x 64/ln2 + 1.5 2^52
+    const int k = __double2loint(t);
+    const double kd = t - shift;
+    double r = fma(kd, -0x1.62e42fefa39efp-7, x);          // leading part of ln2/64
+    r = fma(kd, -0x1.abc9e3b39803fp-62, r);                 // remainder of ln2/64
+    const double r2 = r * r;
+    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    const double em1 = fma(q, r2, r);                       // e^r - 1
+    const double sj = __ldg(tab + (k & 63));
+    const double y = fma(sj, em1, sj);
+    return __hiloint2double(__double2hiint(y) + ((k >> 6) << 20), __double2loint(y));
+}
+
 // ---------------------------------------------------------------------------
 // thermodynamics and rates of progress (Sections 2.1, 2.2)
 
@@ -310,10 +344,14 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
     double* dqdT = q + nr;
     double* wv = dqdT + nr;
     double* dd = wv + nr;
-    for (int j = lane; j < nr; j += TEAM) {
+    const int wt = lane >> 5, l32 = lane & 31;
+    const int c1 = __ldg(M.rc_ptr + wt + 1);
+    for (int c = __ldg(M.rc_ptr + wt); c < c1; ++c) {
+        if (l32 >= __ldg(M.rc_len + c)) continue;
+        const int j = __ldg(M.rc_first + c) + l32;
         const int type = __ldg(M.rtype + j);
         const double bj = __ldg(M.beta + j), Taj = __ldg(M.Ta + j);
-        const double kA = exp(__ldg(M.lnA + j) + bj * lnT - Taj * invT);
+        const double kA = exp_tab(__ldg(M.lnA + j) + bj * lnT - Taj * invT, M.exp2j);
         const double dlnkA = (bj + Taj * invT) * invT;
         double kf, dkf_dT, dkf_dM = 0.0;
         if (type == RXN_ELEM) {
@@ -332,19 +370,19 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                 if (xf) xf[j] = 1.0;
             } else {
                 const double db = __ldg(M.dbeta0 + j), dTa = __ldg(M.dTa0 + j);
-                const double ratio = exp(__ldg(M.dlnA0 + j) + db * lnT - dTa * invT);   // k0 / kinf
+                const double ratio = exp_tab(__ldg(M.dlnA0 + j) + db * lnT - dTa * invT, M.exp2j);   // k0 / kinf
                 const double Pr = ratio * Mx;
                 const double dlnr = (db + dTa * invT) * invT;
                 double F = 1.0, dlogF_dP = 0.0, dlogF_dT = 0.0;   // log = log10
                 if (type == RXN_TROE) {
                     const double al = __ldg(M.talpha + j);
                     const double i3 = __ldg(M.tiT3 + j), i1 = __ldg(M.tiT1 + j);
-                    const double e3 = exp(-T * i3), e1x = exp(-T * i1);
+                    const double e3 = exp_tab(-T * i3, M.exp2j), e1x = exp_tab(-T * i1, M.exp2j);
                     double Fc = (1.0 - al) * e3 + al * e1x;
                     double dFc = -(1.0 - al) * i3 * e3 - al * i1 * e1x;
                     if (__ldg(M.hasT2 + j)) {
                         const double T2 = __ldg(M.tT2 + j);
-                        const double e2 = exp(-T2 * invT);
+                        const double e2 = exp_tab(-T2 * invT, M.exp2j);
                         Fc += e2;
                         dFc += T2 * invT * invT * e2;
                     }
@@ -359,7 +397,7 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                     const double f1 = x * rden;
                     const double ig = 1.0 / (1.0 + f1 * f1);
                     const double logF = Lc * ig;
-                    F = exp(kLn10 * logF);
+                    F = exp_tab(kLn10 * logF, M.exp2j);
                     const double df1_dx = nn * rden * rden;
                     const double df1_dn = -x * rden * rden;
                     const double t2 = 2.0 * Lc * f1 * ig * ig;
@@ -406,7 +444,7 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                 }
             }
             const double snu = (double)__ldg(M.sumnu + j);
-            invK = exp(dG - snu * lnPRT);      // 1 / K_c
+            invK = exp_tab(dG - snu * lnPRT, M.exp2j);   // 1 / K_c
             dlnK = (dH - snu) * invT;          // d ln K_c / dT
         }
         const double kr = kf * invK;
@@ -507,19 +545,27 @@ __device__ void assemble_jacobian(const DevMech& M, const Ws& W,const double* y,
     // A_m = sum_i e_i dOmega_i/dy_m (e = u/RT or h/RT, c = c_v/R or c_p/R)
     double* JT = W.colA;
     double* ds = W.colB;
+    double* eb = W.y1;   // e_i = u_i/RT or h_i/RT (y1 is free while Newton iterates)
+    for (int i = lane; i < ns; i += TEAM) eb[i] = hRT[i] - sub;
+    team_sync<TEAM>();
     const double invD = 1.0 / si.Dt;
+    const bool conp = reactor == R_CONP;
     for (int m = lane; m < n; m += TEAM) {
         double a = 0.0, b = 0.0;
-        for (int i = 0; i < ns; ++i) {
-            const double g = static_cast<double>(G[(1 + i) * ld + m]);
-            a = fma(hRT[i] - sub, g, a);
-            b += g;
+        if (conp) {
+            for (int i = 0; i < ns; ++i) {
+                const double g = static_cast<double>(G[(1 + i) * ld + m]);
+                a = fma(eb[i], g, a);
+                b += g;
+            }
+        } else {
+            for (int i = 0; i < ns; ++i) a = fma(eb[i], static_cast<double>(G[(1 + i) * ld + m]), a);
         }
         double jt;
         if (m == 0) jt = -(si.cw + T * a + si.wT * si.cdc) * invD;
         else jt = -(T * a + si.wT * (cpR[m - 1] - sub)) * invD;
         JT[m] = jt;
-        if (reactor == R_CONP) {
+        if (conp) {
             // s = omega_T / T + sum omega / sum C;  ds/dy_m
             double d = jt / T + b / si.Mc;
             if (m == 0) d -= si.wT / (T * T);
@@ -528,7 +574,6 @@ __device__ void assemble_jacobian(const DevMech& M, const Ws& W,const double* y,
         }
     }
     team_sync<TEAM>();
-    const bool conp = reactor == R_CONP;
     for (Flat2D it(lane, n, TEAM); it.r < n; it.next()) {
         const int r = it.r, c = it.c;
         double J;
@@ -603,26 +648,31 @@ __device__ bool lu_factor(MT* G, int n, int ld, int* piv, double* rinv, double* 
         }
         team_sync<TEAM>();
         const MT pv = G[k * ld + k];
-        if (pv == MT(0)) return false;
-        const double r = rcp_nr(static_cast<double>(pv));
-        if (lane == 0) rinv[k] = r;
-        const MT rm = static_cast<MT>(r);
-        for (int i = k + 1 + lane; i < n; i += TEAM) G[i * ld + k] *= rm;
+        if (abs_key(pv) == 0ull) return false;   // exact zero pivot (integer test)
+        // The first warp forms the reciprocal and scales the column; an FP64
+        // instruction costs the same for one lane as for 32, so the other
+        // warps of the team would only repeat it.
+        if (lane < 32) {
+            const double r = rcp_nr(static_cast<double>(pv));
+            if (lane == 0) rinv[k] = r;
+            const MT rm = static_cast<MT>(r);
+            for (int i = k + 1 + lane; i < n; i += 32) G[i * ld + k] *= rm;
+        }
         team_sync<TEAM>();
         const int m = n - k - 1;
         if (m > 0) {
             const int k1 = k + 1;
             const MT* Uk = G + k * ld + k1;   // pivot row, right of the pivot
             MT* B = G + k1 * ld;              // trailing block, rows k+1 .. n-1
+            const int total = m * m;
             Flat2D it(lane, m, TEAM);
-            while (it.r < m) {   // four elements per thread per pass, loads first
+            int e = lane;
+            for (; e + 3 * TEAM < total; e += 4 * TEAM) {   // four elements, all in range, loads first
                 int o[4], c[4];
-                bool v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    v[u] = it.r < m;
-                    o[u] = v[u] ? it.r * ld : 0;
-                    c[u] = v[u] ? it.c : 0;
+                    o[u] = it.r * ld;
+                    c[u] = it.c;
                     it.next();
                 }
                 MT l[4], uu[4], a[4];
@@ -633,8 +683,12 @@ __device__ bool lu_factor(MT* G, int n, int ld, int* piv, double* rinv, double* 
                     a[u] = B[o[u] + c[u] + k1];
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (v[u]) B[o[u] + c[u] + k1] = fma(-l[u], uu[u], a[u]);
+                for (int u = 0; u < 4; ++u) B[o[u] + c[u] + k1] = fma(-l[u], uu[u], a[u]);
+            }
+            for (; e < total; e += TEAM) {                   // the remaining 0-3 elements
+                const int o = it.r * ld;
+                B[o + it.c + k1] = fma(-B[o + k], Uk[it.c], B[o + it.c + k1]);
+                it.next();
             }
         }
         team_sync<TEAM>();
@@ -659,9 +713,9 @@ __device__ void lu_solve(const MT* G, int n, int ld, const int* piv, const doubl
         team_sync<TEAM>();
     }
     for (int j = n - 1; j >= 0; --j) {          // upper triangle, by columns
-        const double xj = x[j] * rinv[j];
+        if (lane == 0) x[j] *= rinv[j];
         team_sync<TEAM>();
-        if (lane == 0) x[j] = xj;
+        const double xj = x[j];
         for (int i = lane; i < j; i += TEAM) x[i] = fma(-static_cast<double>(G[i * ld + j]), xj, x[i]);
         team_sync<TEAM>();
     }

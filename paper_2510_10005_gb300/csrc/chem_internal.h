@@ -60,6 +60,8 @@ cudaError_t launch_eval_jacobian(const DevMech& M, const Layout& L, int tpb, int
                                  const double* T, const double* C, double* J, cudaStream_t st);
 cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const double* e,
                                const double* Y, double* T, int iters, cudaStream_t st);
+cudaError_t launch_exp_check(const DevMech& M, int64_t n, const double* x, double* y_tab, double* y_lib,
+                             cudaStream_t st);
 // All tasks share one team size; `persistent` selects the resident grid with
 // the work counter (always used when a cell needs global scratch).
 cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, int tpb, bool persistent,

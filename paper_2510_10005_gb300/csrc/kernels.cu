@@ -93,6 +93,15 @@ __global__ void temperature_kernel(DevMech M, int reactor, int64_t N, const doub
     if (lane == 0) Tio[cell] = T;
 }
 
+// exp_tab next to the library exp on the same arguments (test hook).
+__global__ void exp_check_kernel(int64_t n, const double* __restrict__ tab, const double* __restrict__ x,
+                                 double* __restrict__ y_tab, double* __restrict__ y_lib) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        y_tab[i] = exp_tab(x[i], tab);
+        y_lib[i] = exp(x[i]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // integration
 
@@ -284,6 +293,14 @@ cudaError_t launch_eval_jacobian(const DevMech& M, const Layout& L, int tpb, int
 #define CALL(TM) launch_eval<TM>(eval_jacobian_kernel<TM>, M, L, tpb, reactor, N, T, C, J, st)
     CG_DISPATCH_TEAM(M.team, CALL)
 #undef CALL
+}
+
+cudaError_t launch_exp_check(const DevMech& M, int64_t n, const double* x, double* y_tab, double* y_lib,
+                             cudaStream_t st) {
+    const int64_t blocks = n > 0 ? (n + 255) / 256 : 0;
+    if (blocks == 0) return cudaSuccess;
+    exp_check_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(n, M.exp2j, x, y_tab, y_lib);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const double* e,

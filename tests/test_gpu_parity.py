@@ -288,3 +288,27 @@ def test_mixed_precision_adaptive_flame(mechs, ref, handles):
     np.testing.assert_array_equal(sg, so)
     np.testing.assert_allclose(Tg, To, rtol=1e-6)
     assert np.max(np.abs(Yg - Yo)) < 1e-6
+
+
+def test_table_exp_within_two_ulp_of_cuda_exp(handles):
+    """exp_tab (Tang's table-driven method, used for every exponential of
+    the rates) against CUDA's exp over the whole double range, the
+    reduction boundaries and special values."""
+    h = handles["h2"]
+    rng = np.random.default_rng(3)
+    xs = [rng.uniform(-745.0, 710.0, 200000), rng.uniform(-50.0, 50.0, 200000),
+          rng.uniform(-1e-3, 1e-3, 20000),
+          np.arange(-4096, 4096) * (np.log(2.0) / 128.0),          # midpoints of the reduction intervals
+          np.array([0.0, -0.0, 1e-300, -1e-300, 706.9, -706.9, 707.0, -707.0, 708.0, 709.78, 710.0,
+                    -745.1, -800.0, 1e308, -1e308, np.inf, -np.inf, np.nan])]
+    x = np.concatenate(xs)
+    xt = d(x)
+    yt, yl = torch.empty_like(xt), torch.empty_like(xt)
+    chemgb.cgx_exp_check(h, xt, yt, yl)
+    torch.cuda.synchronize()
+    a, b = yt.cpu().numpy(), yl.cpu().numpy()
+    nan = np.isnan(b)
+    assert np.array_equal(np.isnan(a), nan)
+    ia = a[~nan].view(np.int64)
+    ib = b[~nan].view(np.int64)
+    assert np.max(np.abs(ia - ib)) <= 2          # positive doubles order like their bit patterns

@@ -55,9 +55,10 @@ struct Schedule {
 };
 
 // Lane-owned schedule: terms are grouped by destination (in their `order`
-// within a destination), destinations are dealt to the 32 lanes longest
-// first onto the least-loaded lane, and each lane's terms are laid out at
-// [t * lanes + lane]; the last term of a destination carries its index.
+// within a destination), destinations are dealt to the lanes longest first
+// onto the least-loaded lane, and each lane's terms are laid out at
+// [t * lanes + lane]; every term carries its destination, flagged
+// cg::kSchedFirst on the first and cg::kSchedLast on the last term of its run.
 Schedule make_schedule(std::vector<Term> terms, int lanes_n) {
     std::stable_sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) {
         return a.dst != b.dst ? a.dst < b.dst : a.order < b.order;
@@ -85,7 +86,7 @@ Schedule make_schedule(std::vector<Term> terms, int lanes_n) {
     Schedule s;
     s.len = (int)*std::max_element(load.begin(), load.end());
     const size_t slots = (size_t)std::max(1, s.len) * lanes_n;
-    s.dst.assign(slots, -1);
+    s.dst.assign(slots, 0);
     s.src.assign(slots, 0);
     s.fac.assign(slots, 0.0);
     for (int l = 0; l < lanes_n; ++l) {
@@ -96,7 +97,7 @@ Schedule make_schedule(std::vector<Term> terms, int lanes_n) {
                 const size_t k = t * lanes_n + l;
                 s.src[k] = terms[i].src;
                 s.fac[k] = terms[i].fac;
-                s.dst[k] = (i + 1 == r.e) ? r.dst : -1;
+                s.dst[k] = r.dst | (i == r.b ? cg::kSchedFirst : 0) | (i + 1 == r.e ? cg::kSchedLast : 0);
             }
     }
     return s;
@@ -615,7 +616,8 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     std::vector<int> rtype(nr), rev(nr), sumnu(nr), sidx(6 * (size_t)nr, -1), snu(6 * (size_t)nr, 0),
         hasT2(nr, 0), eff_ptr(nr + 1, 0), eff_idx;
     std::vector<double> lnA(nr), beta(nr), Ta(nr), dlnA0(nr, 0.0), dbeta0(nr, 0.0), dTa0(nr, 0.0),
-        talpha(nr, 0.0), tiT3(nr, 0.0), tiT1(nr, 0.0), tT2(nr, 0.0), eff_am1;
+        talpha(nr, 0.0), tiT3(nr, 0.0), tiT1(nr, 0.0), tT2(nr, 0.0), eff_am1, snud(6 * (size_t)nr, 0.0),
+        sumnud(nr, 0.0);
     std::vector<Term> wterms, vterms, jterms;
     std::vector<double> nu(ns);
     for (int jj = 0; jj < nr; ++jj) {
@@ -634,6 +636,8 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
             if (b >= 0) { sn += d->rr_nu[3 * j + s]; nu[b] += d->rr_nu[3 * j + s]; }
         }
         sumnu[jj] = sn;
+        sumnud[jj] = sn;
+        for (int s = 0; s < 6; ++s) snud[(size_t)s * nr + jj] = snu[(size_t)s * nr + jj];
         lnA[jj] = d->arr[3 * j];
         beta[jj] = d->arr[3 * j + 1];
         Ta[jj] = d->arr[3 * j + 2] / kR;
@@ -701,7 +705,7 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
         return st;                                               \
     }
     UP(th, th) UP(W, W) UP(invW, invW) UP(rtype, rtype) UP(rev, rev) UP(sumnu, sumnu)
-    UP(sidx, sidx) UP(snu, snu) UP(lnA, lnA) UP(beta, beta) UP(Ta, Ta) UP(dlnA0, dlnA0)
+    UP(sidx, sidx) UP(snu, snu) UP(snud, snud) UP(sumnud, sumnud) UP(lnA, lnA) UP(beta, beta) UP(Ta, Ta) UP(dlnA0, dlnA0)
     UP(dbeta0, dbeta0) UP(dTa0, dTa0) UP(talpha, talpha) UP(tiT3, tiT3) UP(tiT1, tiT1)
     UP(tT2, tT2) UP(hasT2, hasT2) UP(eff_ptr, eff_ptr) UP(eff_idx, eff_idx) UP(eff_am1, eff_am1)
 #undef UP

@@ -56,6 +56,7 @@ struct DevMech {
     const double *W, *invW;      // [ns]
     const int *rtype, *rev, *sumnu;
     const int *sidx, *snu;       // [6][nr]: slots 0..2 reactants, 3..5 products; -1 empty
+    const double *snud, *sumnud; // the coefficients as doubles ([6][nr], 0 on empty slots) and sum nu
     const double *lnA, *beta, *Ta;        // Ta = Ea / R
     const double *dlnA0, *dbeta0, *dTa0;  // low-pressure minus high-pressure
     const double *talpha, *tiT3, *tiT1, *tT2;
@@ -205,11 +206,17 @@ struct Flat2D {
 
 // Thread-owned assembly schedule: term t of thread l is at [t * TEAM + l];
 // each thread owns a set of destinations and walks their terms in a fixed
-// order, accumulating in a register; the last term of a destination carries
-// its index (dst >= 0) and flushes out[dst] += acc. Padding terms have fac 0,
-// src 0, dst -1. No two threads share a destination, so no synchronisation
-// is needed inside the walk. `in` is read-only while the schedule runs.
-// The sum is formed in FP64 and added to the destination in its own type.
+// order, accumulating in a register. Every term carries its destination with
+// two flags: kSchedFirst (the run of a destination starts: the register
+// takes the destination's current value) and kSchedLast (the run ends: the
+// register is stored back). Padding terms (after a thread's last run) have
+// fac 0, src 0 and no flags. No two threads share a destination, so no
+// synchronisation is needed inside the walk, and a thread's destinations
+// never repeat, so the loads of a group of terms may precede its stores.
+// `in` is read-only while the schedule runs. The sum is formed in FP64 (one
+// FMA per term, no separate add) and stored in the destination's type.
+constexpr int kSchedFirst = 1 << 30, kSchedLast = 1 << 29, kSchedIndex = kSchedLast - 1;
+
 template <int TEAM, class OT>
 __device__ __forceinline__ void run_schedule(int len, const int* __restrict__ dst,
                                              const int* __restrict__ src,
@@ -219,7 +226,7 @@ __device__ __forceinline__ void run_schedule(int len, const int* __restrict__ ds
     int t = 0;
     for (; t + 4 <= len; t += 4) {
         int d[4], s[4];
-        double f[4], x[4];
+        double f[4], x[4], o[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int k = (t + u) * TEAM + lane;
@@ -228,24 +235,23 @@ __device__ __forceinline__ void run_schedule(int len, const int* __restrict__ ds
             f[u] = __ldg(fac + k);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = in[s[u]];
+        for (int u = 0; u < 4; ++u) {
+            x[u] = in[s[u]];
+            o[u] = (d[u] & kSchedFirst) ? static_cast<double>(out[d[u] & kSchedIndex]) : 0.0;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
+            if (d[u] & kSchedFirst) acc = o[u];
             acc = fma(f[u], x[u], acc);
-            if (d[u] >= 0) {
-                out[d[u]] = static_cast<OT>(static_cast<double>(out[d[u]]) + acc);
-                acc = 0.0;
-            }
+            if (d[u] & kSchedLast) out[d[u] & kSchedIndex] = static_cast<OT>(acc);
         }
     }
     for (; t < len; ++t) {
         const int k = t * TEAM + lane;
         const int d = __ldg(dst + k);
+        if (d & kSchedFirst) acc = static_cast<double>(out[d & kSchedIndex]);
         acc = fma(__ldg(fac + k), in[__ldg(src + k)], acc);
-        if (d >= 0) {
-            out[d] = static_cast<OT>(static_cast<double>(out[d]) + acc);
-            acc = 0.0;
-        }
+        if (d & kSchedLast) out[d & kSchedIndex] = static_cast<OT>(acc);
     }
     team_sync<TEAM>();
 }
@@ -413,12 +419,13 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                 if (xf) xf[j] = Pr * ip - dlogF_dP;
             }
         }
-        // mass-action products and their slot partials
-        double p[6], dp[6];
+        // mass-action products C^nu of every slot and their derivatives
+        double p[6], dp[6], nd[6];
         int sp[6];
 #pragma unroll
         for (int s = 0; s < 6; ++s) {
             sp[s] = __ldg(M.sidx + s * nr + j);
+            nd[s] = __ldg(M.snud + s * nr + j);
             p[s] = 1.0;
             dp[s] = 0.0;
             if (sp[s] >= 0) {
@@ -426,39 +433,43 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                 const double c = C[sp[s]];
                 double pw = 1.0;
                 for (int k = 1; k < nu; ++k) pw *= c;
-                dp[s] = nu * pw;
+                dp[s] = nu == 1 ? 1.0 : nd[s] * pw;
                 p[s] = pw * c;
             }
         }
-        const double Pf = p[0] * p[1] * p[2];
-        const double Pb = p[3] * p[4] * p[5];
         double invK = 0.0, dlnK = 0.0;
         if (__ldg(M.rev + j)) {
             double dG = 0.0, dH = 0.0;
 #pragma unroll
             for (int s = 0; s < 6; ++s) {
                 if (sp[s] >= 0) {
-                    const double nu = (s < 3 ? -1.0 : 1.0) * __ldg(M.snu + s * nr + j);
+                    const double nu = s < 3 ? -nd[s] : nd[s];
                     dG = fma(nu, gRT[sp[s]], dG);
                     dH = fma(nu, hRT[sp[s]], dH);
                 }
             }
-            const double snu = (double)__ldg(M.sumnu + j);
-            invK = exp_tab(dG - snu * lnPRT, M.exp2j);   // 1 / K_c
-            dlnK = (dH - snu) * invT;          // d ln K_c / dT
+            const double snu = __ldg(M.sumnud + j);
+            invK = exp_tab(fma(-snu, lnPRT, dG), M.exp2j);   // 1 / K_c
+            dlnK = (dH - snu) * invT;                        // d ln K_c / dT
         }
         const double kr = kf * invK;
-        q[j] = kf * Pf - kr * Pb;
+        // prefix and suffix products: kf p0 p1 p2 and the slot partials
+        const double f01 = kf * p[0], f012 = f01 * p[1], fP = f012 * p[2];   // kf Pf
+        const double f12 = p[1] * p[2];
+        const double r01 = kr * p[3], r012 = r01 * p[4], rP = r012 * p[5];   // kr Pb
+        const double r12 = p[4] * p[5];
+        q[j] = fP - rP;
         if (deriv) {
-            const double phi = Pf - invK * Pb;
-            dqdT[j] = dkf_dT * phi + kr * Pb * dlnK;
+            const double Pf = p[0] * f12, Pb = p[3] * r12;
+            const double phi = fma(-invK, Pb, Pf);
+            dqdT[j] = fma(dkf_dT, phi, rP * dlnK);
             wv[j] = dkf_dM * phi;
-            if (sp[0] >= 0) dd[0 * nr + j] = kf * dp[0] * p[1] * p[2];
-            if (sp[1] >= 0) dd[1 * nr + j] = kf * p[0] * dp[1] * p[2];
-            if (sp[2] >= 0) dd[2 * nr + j] = kf * p[0] * p[1] * dp[2];
-            if (sp[3] >= 0) dd[3 * nr + j] = -kr * dp[3] * p[4] * p[5];
-            if (sp[4] >= 0) dd[4 * nr + j] = -kr * p[3] * dp[4] * p[5];
-            if (sp[5] >= 0) dd[5 * nr + j] = -kr * p[3] * p[4] * dp[5];
+            if (sp[0] >= 0) dd[0 * nr + j] = dp[0] * (kf * f12);
+            if (sp[1] >= 0) dd[1 * nr + j] = dp[1] * (f01 * p[2]);
+            if (sp[2] >= 0) dd[2 * nr + j] = dp[2] * f012;
+            if (sp[3] >= 0) dd[3 * nr + j] = -dp[3] * (kr * r12);
+            if (sp[4] >= 0) dd[4 * nr + j] = -dp[4] * (r01 * p[5]);
+            if (sp[5] >= 0) dd[5 * nr + j] = -dp[5] * r012;
         }
     }
     team_sync<TEAM>();

@@ -70,8 +70,14 @@ enum { CG_RXN_ELEMENTARY = 0, CG_RXN_THREE_BODY = 1, CG_RXN_LINDEMANN = 2, CG_RX
 enum { CG_CONV = 0, CG_CONP = 1, CG_CONP_LITERAL = 2 };
 
 /* integrators: backward Euler (Section 3.2), SDIRK-2 (Appendix A.1),
- * SDIRK-4 (Appendix A.2) */
-enum { CG_BE = 0, CG_SDIRK2 = 1, CG_SDIRK4 = 2 };
+ * SDIRK-4 (Appendix A.2), second-order Rosenbrock (Appendix A.3: one
+ * Jacobian and one factorisation per step, FATODE's Ros2 coefficients; the
+ * printed extra -S(y_n) of its second stage, which would make the scheme
+ * inconsistent, is not taken; embedded first-order error for adaptive
+ * steps), YASS (Appendix A.4: one backward-Euler Newton iteration per step;
+ * a step whose decrement has WRMS norm above alpha = opts->newton_tol is
+ * halved, at most max_halvings times; fixed steps only) */
+enum { CG_BE = 0, CG_SDIRK2 = 1, CG_SDIRK4 = 2, CG_ROS2 = 3, CG_YASS = 4 };
 
 /* arithmetic of the Newton matrix factorisation */
 enum { CG_FP64 = 0, CG_FP32LU = 1 };
@@ -161,10 +167,10 @@ cg_status cg_temperature_from_energy(const cg_mech *mech, int reactor, int64_t N
 
 /* Integration options (fill with cg_integrate_opts_default, then adjust). */
 typedef struct {
-    int method;        /* CG_BE, CG_SDIRK2, CG_SDIRK4                                 */
+    int method;        /* CG_BE, CG_SDIRK2, CG_SDIRK4, CG_ROS2, CG_YASS               */
     int reactor;       /* CG_CONV, CG_CONP, CG_CONP_LITERAL                           */
-    int adaptive;      /* 1: error-controlled steps (SDIRK only); 0: nsub fixed steps */
-    int precision;     /* CG_FP64, or CG_FP32LU: Newton matrix assembled and factored
+    int adaptive;      /* 1: error-controlled steps (SDIRK, Rosenbrock); 0: nsub fixed steps */
+    int precision;     /* CG_FP64, or CG_FP32LU (BE and SDIRK): Newton matrix assembled and factored
                           in FP32, residual, solves and updates in FP64 (an inexact
                           Newton whose converged result meets the same tolerances)  */
     int nsub;          /* fixed mode: number of equal steps over dt                   */
@@ -177,7 +183,8 @@ typedef struct {
                           spill to global scratch); 0: one launch slot per cell    */
     double dt;         /* integration interval, s                                     */
     double rtol, atol; /* weights w_i = atol + rtol max(|y_n,i|, |y_i|)               */
-    double newton_tol; /* Newton converged when WRMS(change of stage state) <= this   */
+    double newton_tol; /* Newton converged when WRMS(change of stage state) <= this;
+                          YASS: the decrement bound alpha                          */
     double h0;         /* adaptive: first step (0: dt)                                */
     double hmin;       /* adaptive: smallest step                                     */
     double neg_tol;    /* a step is rejected when some C_i < -neg_tol * sum C         */

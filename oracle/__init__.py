@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "libcgref.so")
 R_UNIV = 8314.46261815324
 
 CONV, CONP, CONP_LITERAL = 0, 1, 2
-BE, SDIRK2, SDIRK4 = 0, 1, 2
+BE, SDIRK2, SDIRK4, ROS2, YASS = 0, 1, 2, 3, 4
 
 _lib = None
 

@@ -414,7 +414,7 @@ struct Tableau {
 };
 
 struct Opts {
-    int method;            // 0 BE, 1 SDIRK-2, 2 SDIRK-4
+    int method;            // 0 BE, 1 SDIRK-2, 2 SDIRK-4, 3 Rosenbrock-2, 4 YASS
     int reactor;
     int adaptive;
     int nsub;              // fixed-step mode: number of equal steps
@@ -631,10 +631,82 @@ struct Cell {
         return finite_vec(y1) && admissible(y1, o.neg_tol);
     }
 
+    // Second-order Rosenbrock step (Appendix A.3) with the coefficients of
+    // FATODE's Ros2 that the appendix quotes: gamma = 1 + sqrt(2)/2,
+    // alpha = 1/gamma, beta = -2/gamma, m1 = 3/(2 gamma), m2 = 1/(2 gamma):
+    //   (I/(h gamma) - J_n) Gamma_1 = S(y_n)
+    //   (I/(h gamma) - J_n) Gamma_2 = S(y_n + alpha Gamma_1) + (beta/h) Gamma_1
+    //   y_{n+1} = y_n + m1 Gamma_1 + m2 Gamma_2.
+    // (The appendix prints a further -S(y_n) in the second right-hand side,
+    // which makes the scheme inconsistent -- on y' = lambda y the first-order
+    // term becomes lambda h y / 2 -- and which FATODE's Ros2 does not have.)
+    // J is evaluated once, at y_n. Embedded first-order solution
+    // y_n + Gamma_1/gamma: error e = (Gamma_1 + Gamma_2)/(2 gamma).
+    bool ros2_step(const std::vector<double>& yn, double h, std::vector<double>& y1,
+                   std::vector<double>& err) {
+        const double g = 1.0 + std::sqrt(2.0) / 2.0;
+        const double alpha = 1.0 / g, beta = -2.0 / g, m1 = 3.0 / (2.0 * g), m2 = 1.0 / (2.0 * g);
+        std::vector<double> S0(n), G1(n), G2(n), Y2(n);
+        source(m, o.reactor, yn.data(), S0.data());
+        jacobian(m, o.reactor, yn.data(), J.data());
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 / (h * g) : 0.0) - J[i * n + j];
+        st.newton++;
+        st.lu++;
+        if (!lu_factor(n, G.data(), piv.data())) return false;
+        G1 = S0;
+        lu_solve(n, G.data(), piv.data(), G1.data());
+        for (int i = 0; i < n; ++i) Y2[i] = yn[i] + alpha * G1[i];
+        if (!finite_vec(Y2)) return false;
+        source(m, o.reactor, Y2.data(), G2.data());
+        for (int i = 0; i < n; ++i) G2[i] += beta / h * G1[i];
+        lu_solve(n, G.data(), piv.data(), G2.data());
+        y1.assign(n, 0.0);
+        err.assign(n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            y1[i] = yn[i] + m1 * G1[i] + m2 * G2[i];
+            err[i] = (G1[i] + G2[i]) / (2.0 * g);
+        }
+        lastY.clear();
+        return finite_vec(y1) && admissible(y1, o.neg_tol);
+    }
+
+    // YASS (Appendix A.4): one backward-Euler Newton step from y_n,
+    //   (I - h J(y_n)) dy = h S(y_n),  y_{n+1} = y_n + dy,
+    // rejected (and halved by the caller) when the decrement's norm exceeds
+    // alpha: WRMS(dy; atol + rtol max(|y_n|, |y_{n+1}|)) > alpha, with alpha
+    // passed as newton_tol.
+    bool yass_step(const std::vector<double>& yn, double h, std::vector<double>& y1) {
+        std::vector<double> dy(n);
+        source(m, o.reactor, yn.data(), dy.data());
+        jacobian(m, o.reactor, yn.data(), J.data());
+        for (int i = 0; i < n; ++i) {
+            dy[i] *= h;
+            for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 : 0.0) - h * J[i * n + j];
+        }
+        st.newton++;
+        st.lu++;
+        if (!lu_factor(n, G.data(), piv.data())) return false;
+        lu_solve(n, G.data(), piv.data(), dy.data());
+        y1 = yn;
+        for (int i = 0; i < n; ++i) y1[i] += dy[i];
+        lastY.clear();
+        if (!finite_vec(y1)) return false;
+        if (wrms(n, dy.data(), yn.data(), y1.data(), o.rtol, o.atol) > o.newton_tol) return false;
+        return admissible(y1, o.neg_tol);
+    }
+
+    bool step_with_error(const Tableau& tb, const std::vector<double>& yn, double h, std::vector<double>& y1,
+                         std::vector<double>& err) {
+        if (o.method == 3) return ros2_step(yn, h, y1, err);
+        return sdirk_step(tb, yn, h, y1, err);
+    }
+
     bool fixed_step(const Tableau& tb, const std::vector<double>& yn, double h, std::vector<double>& y) {
         if (o.method == 0) return be_step(yn, h, y);
+        if (o.method == 4) return yass_step(yn, h, y);
         std::vector<double> err;
-        return sdirk_step(tb, yn, h, y, err);
+        return step_with_error(tb, yn, h, y, err);
     }
 
     // Fixed step with deterministic halving on Newton failure (after YASS,
@@ -668,7 +740,7 @@ struct Cell {
             if (h < o.hmin) return ST_STEP_TOO_SMALL;
             bool last = t + h >= o.dt;
             double hh = last ? o.dt - t : h;
-            if (!sdirk_step(tb, y, hh, y1, err)) {
+            if (!step_with_error(tb, y, hh, y1, err)) {
                 st.rejects++;
                 h = 0.25 * hh;
                 continue;
@@ -691,7 +763,7 @@ struct Cell {
 
     int integrate(const Tableau& tb, std::vector<double>& y) {
         if (!finite_vec(y)) return ST_NONFINITE;
-        if (o.adaptive && o.method != 0) return adaptive(tb, y);
+        if (o.adaptive && o.method >= 1 && o.method <= 3) return adaptive(tb, y);
         int ns = std::max(1, o.nsub);
         double h = o.dt / ns;
         for (int k = 0; k < ns; ++k) {
@@ -702,9 +774,11 @@ struct Cell {
     }
 
     // Converged stage states of the step (y_n, h) into lastY.
+    // (backward Euler and SDIRK only: the adjoint covers those integrators)
     bool stages(const Tableau& tb, const std::vector<double>& yn, double h) {
         std::vector<double> y1, err;
         if (o.method == 0) return be_step(yn, h, y1);
+        if (o.method > 2) return false;
         return sdirk_step(tb, yn, h, y1, err);
     }
 
@@ -712,7 +786,7 @@ struct Cell {
     int replay(const Tableau& tb, std::vector<double>& y, const double* hs, int count) {
         std::vector<double> y1, err;
         for (int k = 0; k < count; ++k) {
-            bool ok = o.method == 0 ? be_step(y, hs[k], y1) : sdirk_step(tb, y, hs[k], y1, err);
+            bool ok = fixed_step(tb, y, hs[k], y1);
             if (!ok) return ST_NEWTON_FAIL;
             y = y1;
         }

@@ -138,7 +138,9 @@ def embedded_weights(A, order, s_used):
 
 def tableau(method: int):
     """Return dict(s, A[5x5], b[5], bhat[5], err_order) for
-    method 0 = backward Euler, 1 = SDIRK-2, 2 = SDIRK-4."""
+    method 0 = backward Euler, 1 = SDIRK-2, 2 = SDIRK-4; 3 = Rosenbrock-2
+    and 4 = YASS carry only their stage count and embedded order here (the
+    oracle evaluates their coefficients itself)."""
     A = np.zeros((5, 5)); b = np.zeros(5); bh = np.zeros(5)
     if method == 0:
         A[0, 0] = 1.0; b[0] = 1.0
@@ -154,6 +156,10 @@ def tableau(method: int):
         b = A[4].copy()
         bh = embedded_weights(A, 3, 4)
         return dict(s=5, A=A, b=b, bhat=bh, err_order=3)
+    if method == 3:
+        return dict(s=2, A=A, b=b, bhat=bh, err_order=1)
+    if method == 4:
+        return dict(s=1, A=A, b=b, bhat=bh, err_order=0)
     raise ValueError(method)
 
 

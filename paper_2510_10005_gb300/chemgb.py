@@ -20,7 +20,7 @@ CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ECAPACITY, CG_EUNSUPPORTED = range(6)
 (CG_CELL_OK, CG_CELL_NEWTON_FAIL, CG_CELL_STEP_TOO_SMALL, CG_CELL_MAX_STEPS, CG_CELL_NONFINITE,
  CG_CELL_NO_RECORD) = range(6)
 CG_CONV, CG_CONP, CG_CONP_LITERAL = 0, 1, 2
-CG_BE, CG_SDIRK2, CG_SDIRK4 = 0, 1, 2
+CG_BE, CG_SDIRK2, CG_SDIRK4, CG_ROS2, CG_YASS = 0, 1, 2, 3, 4
 CG_FP64, CG_FP32LU = 0, 1
 
 _lib = None

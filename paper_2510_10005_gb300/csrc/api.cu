@@ -297,8 +297,16 @@ bool make_sdirk4(Tab& t) {
 
 bool make_tableau(int method, Tab& t) {
     t = Tab();
-    if (method == CG_BE) {
+    if (method == CG_BE || method == CG_YASS) {   // YASS: one backward-Euler Newton iteration
         t.s = 1; t.A[0][0] = 1.0; t.b[0] = 1.0; t.err_order = 0; t.start_zero = 1;
+        return true;
+    }
+    if (method == CG_ROS2) {   // Appendix A.3: gamma, alpha, beta in A, m1, m2 in b
+        const double g = 1.0 + std::sqrt(2.0) / 2.0;
+        t.s = 2; t.A[0][0] = g; t.A[1][0] = 1.0 / g; t.A[1][1] = -2.0 / g;
+        t.b[0] = 3.0 / (2.0 * g); t.b[1] = 1.0 / (2.0 * g);
+        t.bh[0] = t.b[0] - 0.5 / g; t.bh[1] = t.b[1] - 0.5 / g;   // embedded: y_n + Gamma_1 / gamma
+        t.err_order = 1;
         return true;
     }
     if (method == CG_SDIRK2) {
@@ -788,7 +796,9 @@ void cg_integrate_opts_default(cg_integrate_opts* o) {
 
 static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
     if (!o) return fail(CG_EINVAL, "opts is NULL");
-    if (o->method < CG_BE || o->method > CG_SDIRK4) return fail(CG_EINVAL, "bad method");
+    if (o->method < CG_BE || o->method > CG_YASS) return fail(CG_EINVAL, "bad method");
+    if (o->precision == CG_FP32LU && (o->method == CG_ROS2 || o->method == CG_YASS))
+        return fail(CG_EUNSUPPORTED, "Rosenbrock-2 and YASS take no Newton correction: FP64 factorisation only");
     if (o->reactor < CG_CONV || o->reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad reactor");
     if (o->precision != CG_FP64 && o->precision != CG_FP32LU)
         return fail(CG_EINVAL, "bad precision %d", o->precision);
@@ -802,9 +812,9 @@ static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
     if (!make_tableau(o->method, t)) return fail(CG_EINVAL, "tableau construction failed");
     P.method = o->method;
     P.reactor = o->reactor;
-    P.adaptive = (o->adaptive && o->method != CG_BE) ? 1 : 0;
+    P.adaptive = (o->adaptive && o->method != CG_BE && o->method != CG_YASS) ? 1 : 0;
     P.nsub = o->nsub;
-    P.max_newton = o->max_newton;
+    P.max_newton = o->method == CG_YASS ? 1 : o->max_newton;
     P.max_steps = o->max_steps;
     P.max_halvings = o->max_halvings;
     P.err_filter = o->err_filter;
@@ -912,6 +922,8 @@ cg_status cg_integrate_adjoint(const cg_mech* m, const cg_integrate_opts* o, int
     cg_status st = make_params(o, P);
     if (st != CG_OK) return st;
     if (N < 0 || ckpt_cap < 2) return fail(CG_EINVAL, "N >= 0 and ckpt_cap >= 2 required");
+    if (o->method == CG_ROS2 || o->method == CG_YASS)
+        return fail(CG_EUNSUPPORTED, "the adjoint covers backward Euler and SDIRK");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     if (N == 0) {

@@ -120,7 +120,7 @@ __device__ int integrate_fixed(const DevMech& M, const Ws& W, const IntParams& P
         int d = 0;
         while (pos < total) {
             const double h = ldexp(hsub, -d);
-            if (rk_step<TEAM, MT>(M, W, P, h, cnt, lane)) {
+            if (step<TEAM, MT>(M, W, P, h, cnt, lane)) {
                 save_step<TEAM>(ck, cap, cnt.steps, W.yn, h, M.n, lane);
                 copy_vec<TEAM>(W.yn, W.y1, M.n, lane);
                 cnt.steps++;
@@ -151,7 +151,7 @@ __device__ int integrate_adaptive(const DevMech& M, const Ws& W, const IntParams
         if (h < P.hmin) return CELL_STEP_TOO_SMALL;
         const bool last = t + h >= P.dt;
         const double hh = last ? P.dt - t : h;
-        if (!rk_step<TEAM, MT>(M, W, P, hh, cnt, lane)) {
+        if (!step<TEAM, MT>(M, W, P, hh, cnt, lane)) {
             cnt.rejects++;
             h = 0.25 * hh;
             continue;

@@ -140,6 +140,76 @@ __device__ bool rk_step(const DevMech& M, const Ws& W, const IntParams& P, doubl
     return !neg;
 }
 
+// Second-order Rosenbrock step (Appendix A.3, coefficients of FATODE's Ros2
+// as the appendix quotes them): with G = I - h gamma J(y_n),
+//   G Gamma_1 = h gamma S(y_n),
+//   G Gamma_2 = h gamma S(y_n + alpha Gamma_1) + gamma beta Gamma_1,
+//   y_{n+1} = y_n + m1 Gamma_1 + m2 Gamma_2,
+// (the appendix's (I/(h gamma) - J) form multiplied through by h gamma; its
+// printed extra -S(y_n) in the second stage is not taken: it makes the
+// scheme inconsistent). One Jacobian, one factorisation, two solves.
+// Embedded first-order error (Gamma_1 + Gamma_2)/(2 gamma) into W.err.
+// P.A[0][0] = gamma, P.A[1][0] = alpha, P.A[1][1] = beta, P.b = (m1, m2).
+template <int TEAM, class MT>
+__device__ bool ros2_step(const DevMech& M, const Ws& W, const IntParams& P, double h, Counters& cnt,
+                          int lane) {
+    const int n = M.n;
+    const double g = P.A[0][0], al = P.A[1][0], be = P.A[1][1];
+    const double hg = h * g;
+    double* yn = W.yn;
+    double* G1 = W.Gam;
+    double* G2 = W.Gam + n;
+    MT* G = reinterpret_cast<MT*>(W.G);
+    const double Mc = rates<TEAM>(M, W, yn, true, lane);
+    const SrcInfo si = assemble_source<TEAM>(M, W, yn, P.reactor, Mc, lane);
+    assemble_jacobian<TEAM, MT>(M, W, yn, P.reactor, si, hg, nullptr, lane);
+    for (int i = lane; i < n; i += TEAM) G1[i] = hg * W.S[i];
+    team_sync<TEAM>();
+    cnt.newton++;
+    cnt.lu++;
+    if (!lu_factor<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, W.red, lane)) return false;
+    lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, G1, lane);
+    bool bad = false;
+    for (int i = lane; i < n; i += TEAM) {
+        const double v = fma(al, G1[i], yn[i]);
+        W.Y[i] = v;
+        bad |= !isfinite(v);
+    }
+    team_sync<TEAM>();
+    if (team_any<TEAM>(bad, W.red)) return false;
+    const double Mc2 = rates<TEAM>(M, W, W.Y, false, lane);
+    assemble_source<TEAM>(M, W, W.Y, P.reactor, Mc2, lane);
+    for (int i = lane; i < n; i += TEAM) G2[i] = fma(hg, W.S[i], g * be * G1[i]);
+    team_sync<TEAM>();
+    lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, G2, lane);
+    const double e = 0.5 / g;
+    for (int i = lane; i < n; i += TEAM) {
+        const double v = fma(P.b[1], G2[i], fma(P.b[0], G1[i], yn[i]));
+        W.y1[i] = v;
+        W.err[i] = e * (G1[i] + G2[i]);
+        bad |= !isfinite(v);
+    }
+    team_sync<TEAM>();
+    if (team_any<TEAM>(bad, W.red)) return false;
+    double cs = 0.0;
+    for (int i = 1 + lane; i < n; i += TEAM) cs += W.y1[i];
+    cs = team_sum<TEAM>(cs, W.red);
+    bool neg = false;
+    for (int i = 1 + lane; i < n; i += TEAM) neg |= W.y1[i] < -P.neg_tol * cs;
+    neg = team_any<TEAM>(neg, W.red) || !(W.y1[0] > 0.0);
+    return !neg;
+}
+
+// One step of the configured integrator: Rosenbrock-2, or the implicit
+// Runge-Kutta step (backward Euler, SDIRK-2/4; YASS is backward Euler with a
+// single Newton iteration whose decrement norm must stay below alpha).
+template <int TEAM, class MT>
+__device__ __forceinline__ bool step(const DevMech& M, const Ws& W, const IntParams& P, double h,
+                                     Counters& cnt, int lane) {
+    if (P.method == 3) return ros2_step<TEAM, MT>(M, W, P, h, cnt, lane);
+    return rk_step<TEAM, MT>(M, W, P, h, cnt, lane);
+}
+
 template <int TEAM>
 __device__ __forceinline__ void copy_vec(double* dst, const double* src, int n, int lane) {
     for (int i = lane; i < n; i += TEAM) dst[i] = src[i];

@@ -312,3 +312,73 @@ def test_table_exp_within_two_ulp_of_cuda_exp(handles):
     ia = a[~nan].view(np.int64)
     ib = b[~nan].view(np.int64)
     assert np.max(np.abs(ia - ib)) <= 2          # positive doubles order like their bit patterns
+
+
+# --- Rosenbrock-2 (Appendix A.3) and YASS (Appendix A.4) --------------------
+
+@pytest.mark.parametrize("kind", ["h2", "ch4"])
+@pytest.mark.parametrize("reactor", [chemgb.CG_CONV, chemgb.CG_CONP])
+def test_rosenbrock_fixed_parity(mechs, ref, handles, kind, reactor):
+    """No Newton iteration: both sides evaluate the same two linear solves,
+    so the states agree to rounding (1e-10)."""
+    m, r, h = mechs[kind], ref[kind], handles[kind]
+    fuel = "H2" if kind == "h2" else "CH4"
+    T, Y, p = inputs.field_reactor(m, 77, (1100, 1500), (1, 3), (0.5, 2), fuel, seed=31)
+    if reactor == chemgb.CG_CONV:
+        p = p / (inputs.R_UNIV * T * (Y / m.W).sum(axis=1))
+    o = dict(method=oracle.ROS2, adaptive=0, nsub=4, dt=2e-6, rtol=1e-8, atol=1e-14, reactor=reactor)
+    To, Yo, so, sto = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    np.testing.assert_array_equal(stg, sto)
+    assert_state_close(Tg, Yg, To, Yo, 1e-10, 1e-20)
+
+
+def test_rosenbrock_adaptive_parity_flame_field(mechs, ref, handles):
+    m, r, h = mechs["ch4"], ref["ch4"], handles["ch4"]
+    T, Y, p = inputs.field_flames(m, 4096, seed=0)
+    idx = np.arange(5, 4096, 32)
+    o = dict(ADAPT, method=oracle.ROS2)
+    To, Yo, so, sto = r.integrate(T[idx], Y[idx], p[idx], o, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**o), T[idx], Y[idx], p[idx])
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    np.testing.assert_allclose(Tg, To, rtol=1e-6)
+    assert np.max(np.abs(Yg - Yo)) < 1e-6
+    assert np.mean(np.all(stg == sto, axis=1)) > 0.9
+
+
+def test_yass_parity_with_halving(mechs, ref, handles):
+    """9 species, 4096 cells, YASS over 1e-5 s with alpha = 1 (WRMS weights
+    1e-6 + 1e-3 |y|): every cell halves, up to a few hundred sub-steps (both
+    sides take the same decisions, up to cells whose norm sits at alpha)."""
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 4096, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=0)
+    o = dict(method=oracle.YASS, adaptive=0, dt=1e-5, rtol=1e-3, atol=1e-6, newton_tol=1.0,
+             max_halvings=12, reactor=oracle.CONP)
+    To, Yo, so, sto = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    same = np.all(stg == sto, axis=1)
+    assert same.mean() > 0.99 and np.mean(sto[:, 1] > 0) > 0.05   # halving happens
+    assert_state_close(Tg[same], Yg[same], To[same], Yo[same], 1e-10, 1e-20)
+    assert np.all(stg[:, 2] == stg[:, 0] + stg[:, 1])             # one linear solve per attempt
+
+
+def test_rosenbrock_and_yass_refusals(mechs, handles):
+    h = handles["h2"]
+    T, Y, p = inputs.field_reactor(mechs["h2"], 4, (1200, 1200), (1, 1), (1, 1), "H2", seed=0)
+    for method in (chemgb.CG_ROS2, chemgb.CG_YASS):
+        with pytest.raises(chemgb.ChemgbError) as e:
+            run_gpu(h, chemgb.make_opts(method=method, precision=chemgb.CG_FP32LU), T, Y, p)
+        assert e.value.code == chemgb.CG_EUNSUPPORTED
+        o = chemgb.make_opts(method=method, adaptive=0)
+        ck = torch.empty((4, 8, h.n + 1), dtype=torch.float64, device=DEV)
+        ckn = torch.zeros(4, dtype=torch.int32, device=DEV)
+        z = torch.zeros(4, dtype=torch.float64, device=DEV)
+        zy = torch.zeros((h.ns, 4), dtype=torch.float64, device=DEV)
+        with pytest.raises(chemgb.ChemgbError) as e:
+            chemgb.cg_integrate_adjoint(h, o, ck, ckn, z, zy, z.clone(), zy.clone())
+        assert e.value.code == chemgb.CG_EUNSUPPORTED

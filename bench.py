@@ -208,12 +208,33 @@ def make_workload(config: int, cells: int, seed: int = 0):
     raise ValueError(config)
 
 
-def opts_dict(config: int, precision: int):
+# --method: the integrator of the workload (default: the workload's own)
+METHODS = {
+    "be": dict(method=0, adaptive=0),
+    "sdirk2": dict(method=1),
+    "sdirk4": dict(method=2),
+    "ros2": dict(method=3),                       # Appendix A.3, one factorisation per step
+    "yass": dict(method=4, adaptive=0, rtol=1e-3, atol=1e-6, newton_tol=1.0, max_halvings=12),
+}
+
+
+def opts_dict(config: int, precision: int, method: str | None = None):
     o = dict(CONFIGS[config]["opts"])
+    if method:
+        o.update(METHODS[method])
     o["precision"] = precision
     if config == 3:
         o["persistent"] = 1
     return o
+
+
+def workload_name(config: int, method: str | None) -> str:
+    w = CONFIGS[config]["workload"]
+    if not method:
+        return w
+    extra = {"yass": "YASS (alpha 1, WRMS weights 1e-6 + 1e-3|y|, up to 12 halvings)",
+             "ros2": "Rosenbrock-2", "be": "backward Euler", "sdirk2": "SDIRK-2", "sdirk4": "SDIRK-4"}[method]
+    return w + "; integrator replaced by " + extra
 
 
 def oracle_opts(o: dict) -> dict:
@@ -248,7 +269,7 @@ def run_reference(args):
         return
     cfg = CONFIGS[args.config]
     parts = make_workload(args.config, args.cells or cfg["cells"])
-    opts = opts_dict(args.config, 0)
+    opts = opts_dict(args.config, 0, args.method)
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         cpu_oracle_sample(parts, opts, max(16, args.ref_sample // 8), threads)
@@ -262,7 +283,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": cfg["workload"], "config": args.config},
+        "data": "synthetic", "config": {"workload": workload_name(args.config, args.method), "config": args.config},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.ref_sample} cells evenly spaced through the field, per step"},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -285,7 +306,7 @@ def run_gpu(args):
     cfg = CONFIGS[args.config]
     precision = cfg["precision"] if args.precision is None else args.precision
     parts = make_workload(args.config, args.cells or cfg["cells"], seed=rank)
-    opts_d = opts_dict(args.config, precision)
+    opts_d = opts_dict(args.config, precision, args.method)
     opts = chemgb.make_opts(**opts_d)
     stream = torch.cuda.Stream(dev)   # a side stream (graph capture needs one); all work goes there
     torch.cuda.set_stream(stream)
@@ -366,7 +387,10 @@ def run_gpu(args):
         sh = b["stats"].cpu().numpy()
         nwt = int(sh[2].astype(np.int64).sum())
         newton += nwt
-        flops += nwt * algorithmic_flops_per_newton(m.ns, m.nr, j_term_count(m), precision == 1)
+        per = algorithmic_flops_per_newton(m.ns, m.nr, j_term_count(m), precision == 1)
+        if opts_d["method"] == 3:   # Rosenbrock-2: plus a second rate evaluation and solve per step
+            per += 30.0 * m.nr + 40.0 * m.ns + 2.0 * (m.ns + 1) ** 2
+        flops += nwt * per
         failed += int((b["st"].cpu().numpy() != 0).sum())
         stat_means.append({"species": m.ns, "steps": float(sh[0].mean()), "rejects": float(sh[1].mean()),
                            "newton": float(sh[2].mean())})
@@ -423,7 +447,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg["workload"], "config": args.config, "cells_per_gpu": N_total,
+        "config": {"workload": workload_name(args.config, args.method), "config": args.config,
+                   "cells_per_gpu": N_total,
                    "newton_matrix": "fp32" if precision == 1 else "fp64", "state_bytes": state_bytes,
                    "l2": "state larger than L2 (129 MB); no flush" if state_bytes > 129e6
                    else "state smaller than L2; each step restores it from a second copy"},
@@ -701,6 +726,8 @@ def main():
     ap.add_argument("--tpb", type=int, default=1, help="cells per block with --team 32")
     ap.add_argument("--precision", type=int, default=None, help="0: FP64 Newton matrix, 1: FP32 LU")
     ap.add_argument("--adj-sample", type=int, default=8, help="--config 4: cells checked against the oracle")
+    ap.add_argument("--method", choices=sorted(METHODS), default=None,
+                    help="replace the workload's integrator (configs 1, 2, 3, 5)")
     args = ap.parse_args()
     if args.config == 4:
         (run_reference_adjoint if args.impl == "reference" else run_adjoint)(args)

@@ -59,6 +59,8 @@ def _load():
         lib.cgref_jacobian.argtypes = [P, ctypes.c_int, ctypes.c_long, P, P]
         lib.cgref_lu_solve.restype = ctypes.c_int
         lib.cgref_lu_solve.argtypes = [ctypes.c_int, P, P]
+        lib.cgref_gmres.restype = ctypes.c_int
+        lib.cgref_gmres.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, P]
         lib.cgref_temperature.argtypes = [P, ctypes.c_int, ctypes.c_long, P, P, P, ctypes.c_int, P]
         lib.cgref_integrate.argtypes = [P, P, P, P, ctypes.c_long, P, P, P, ctypes.c_int]
         I = ctypes.c_int
@@ -91,10 +93,26 @@ def lu_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:
     return x
 
 
+LU, GMRES = 0, 1
+PC_NONE, PC_JACOBI, PC_GAUSS_SEIDEL = 0, 1, 2
+
+
+def gmres(A: np.ndarray, b: np.ndarray, prec: int = PC_NONE, m: int = 30, maxit: int = 1000,
+          tol: float = 1e-12):
+    """Restarted, left-preconditioned GMRES of Section 3.4 on a dense system;
+    returns (x, converged, iterations)."""
+    A = _f64(A)
+    x = _f64(b).copy()
+    it = ctypes.c_int(0)
+    ok = _load().cgref_gmres(A.shape[0], _p(A), _p(x), prec, m, maxit, tol, ctypes.byref(it))
+    return x, bool(ok), it.value
+
+
 def default_opts(**kw) -> dict:
     o = dict(method=SDIRK4, reactor=CONP, adaptive=1, nsub=1, max_newton=7, max_steps=100000,
              max_halvings=10, err_filter=1, dt=1e-6, rtol=1e-6, atol=1e-12, newton_tol=0.03,
-             h0=0.0, hmin=1e-20, neg_tol=1e-6)
+             h0=0.0, hmin=1e-20, neg_tol=1e-6, linear_solver=LU, preconditioner=PC_GAUSS_SEIDEL,
+             gmres_restart=30, gmres_maxit=200, gmres_tol=1e-10)
     o.update(kw)
     return o
 
@@ -184,9 +202,10 @@ class RefMech:
     def _packed(opts: dict):
         o = default_opts(**opts)
         iopt = _i32([o["method"], o["reactor"], o["adaptive"], o["nsub"], o["max_newton"],
-                     o["max_steps"], o["max_halvings"], o["err_filter"]])
+                     o["max_steps"], o["max_halvings"], o["err_filter"], o["linear_solver"],
+                     o["preconditioner"], o["gmres_restart"], o["gmres_maxit"]])
         dopt = _f64([o["dt"], o["rtol"], o["atol"], o["newton_tol"], o["h0"], o["hmin"],
-                     o["neg_tol"]])
+                     o["neg_tol"], o["gmres_tol"]])
         tab = _tableau.pack(_tableau.tableau(o["method"]))
         return iopt, dopt, tab
 

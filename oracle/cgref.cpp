@@ -404,6 +404,110 @@ void lu_solve(int n, const double* LU, const int* piv, double* b) {
 }
 
 // ---------------------------------------------------------------------------
+// Iterative solver (Section 3.4): restarted GMRES (Saad and Schultz 1986) with
+// left preconditioning, M^{-1} A x = M^{-1} b, M = I (prec 0), the diagonal
+// of A (Jacobi, prec 1) or the lower triangle of A with its diagonal
+// (Gauss-Seidel, prec 2, applied by forward substitution). x0 = 0; Arnoldi
+// by modified Gram-Schmidt; the small least-squares problem by Givens
+// rotations; restart after m iterations. Converged when the preconditioned
+// residual norm is at most tol ||M^{-1} b||. b in, x out; false when not
+// converged within maxit iterations (or on a zero diagonal with a
+// preconditioner). *iters receives the iterations taken.
+
+void precondition(int n, const double* A, int prec, double* v) {
+    if (prec == 1) {
+        for (int i = 0; i < n; ++i) v[i] /= A[i * n + i];
+    } else if (prec == 2) {
+        for (int i = 0; i < n; ++i) {
+            double s = v[i];
+            for (int k = 0; k < i; ++k) s -= A[i * n + k] * v[k];
+            v[i] = s / A[i * n + i];
+        }
+    }
+}
+
+bool gmres(int n, const double* A, double* b, int prec, int m, int maxit, double tol, int* iters) {
+    *iters = 0;
+    if (prec != 0)
+        for (int i = 0; i < n; ++i)
+            if (A[i * n + i] == 0.0) return false;
+    std::vector<double> x(n, 0.0), r(n), w(n), g(m + 1), cs(m), sn(m), y(m);
+    std::vector<std::vector<double>> V(m + 1, std::vector<double>(n));
+    std::vector<std::vector<double>> H(m + 1, std::vector<double>(m, 0.0));
+    auto norm = [&](const std::vector<double>& v) {
+        double s = 0.0;
+        for (double e : v) s += e * e;
+        return std::sqrt(s);
+    };
+    r.assign(b, b + n);
+    precondition(n, A, prec, r.data());
+    const double bnorm = norm(r);
+    if (bnorm == 0.0) {
+        std::fill(b, b + n, 0.0);
+        return true;
+    }
+    while (true) {
+        // r = M^{-1} (b - A x)
+        for (int i = 0; i < n; ++i) {
+            double s = b[i];
+            for (int k = 0; k < n; ++k) s -= A[i * n + k] * x[k];
+            r[i] = s;
+        }
+        precondition(n, A, prec, r.data());
+        const double beta = norm(r);
+        if (beta <= tol * bnorm) break;
+        if (*iters >= maxit) return false;
+        for (int i = 0; i < n; ++i) V[0][i] = r[i] / beta;
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m && *iters < maxit; ++j) {
+            for (int i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int c = 0; c < n; ++c) s += A[i * n + c] * V[j][c];
+                w[i] = s;
+            }
+            precondition(n, A, prec, w.data());
+            ++*iters;
+            for (int q = 0; q <= j; ++q) {
+                double h = 0.0;
+                for (int i = 0; i < n; ++i) h += w[i] * V[q][i];
+                H[q][j] = h;
+                for (int i = 0; i < n; ++i) w[i] -= h * V[q][i];
+            }
+            const double hn = norm(w);
+            H[j + 1][j] = hn;
+            if (hn > 0.0)
+                for (int i = 0; i < n; ++i) V[j + 1][i] = w[i] / hn;
+            for (int q = 0; q < j; ++q) {   // earlier rotations on the new column
+                const double t = cs[q] * H[q][j] + sn[q] * H[q + 1][j];
+                H[q + 1][j] = -sn[q] * H[q][j] + cs[q] * H[q + 1][j];
+                H[q][j] = t;
+            }
+            const double rho = std::hypot(H[j][j], H[j + 1][j]);
+            if (rho == 0.0) return false;
+            cs[j] = H[j][j] / rho;
+            sn[j] = H[j + 1][j] / rho;
+            H[j][j] = rho;
+            H[j + 1][j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            k = j + 1;
+            if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
+        }
+        for (int q = k - 1; q >= 0; --q) {   // H y = g, upper triangular
+            double s = g[q];
+            for (int c = q + 1; c < k; ++c) s -= H[q][c] * y[c];
+            y[q] = s / H[q][q];
+        }
+        for (int q = 0; q < k; ++q)
+            for (int i = 0; i < n; ++i) x[i] += y[q] * V[q][i];
+    }
+    std::copy(x.begin(), x.end(), b);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Integrators.
 
 struct Tableau {
@@ -415,6 +519,9 @@ struct Tableau {
 
 struct Opts {
     int method;            // 0 BE, 1 SDIRK-2, 2 SDIRK-4, 3 Rosenbrock-2, 4 YASS
+    int linear_solver;     // 0 dense LU, 1 GMRES (Section 3.4)
+    int prec, gmres_m, gmres_maxit;   // GMRES: preconditioner, restart length, iteration limit
+    double gmres_tol;
     int reactor;
     int adaptive;
     int nsub;              // fixed-step mode: number of equal steps
@@ -545,6 +652,25 @@ struct Cell {
     Cell(const Mech& mm, const Opts& oo) : m(mm), o(oo), n(mm.ns + 1),
         S(n), J(n * n), G(n * n), f(n), d(n), piv(n) {}
 
+    // The linear solver of the Newton systems with matrix G (Section 3.4):
+    // dense LU (prepare = factorise), or GMRES on G as assembled. Stats.lu
+    // counts factorisations, or GMRES iterations.
+    bool lin_prepare() {
+        if (o.linear_solver == 1) return true;
+        st.lu++;
+        return lu_factor(n, G.data(), piv.data());
+    }
+    bool lin_solve(double* v) {
+        if (o.linear_solver == 1) {
+            int it = 0;
+            const bool ok = gmres(n, G.data(), v, o.prec, o.gmres_m, o.gmres_maxit, o.gmres_tol, &it);
+            st.lu += it;
+            return ok;
+        }
+        lu_solve(n, G.data(), piv.data(), v);
+        return true;
+    }
+
     // Backward Euler (eq. Backward_euler) with full Newton (eq. newtons-method-2):
     // G(y_k) (y_{k+1} - y_k) = -f(y_k), f = (y_k - y^n)/h - S(y_k),
     // G = I/h - J(y_k) (eq. jacobian), J re-evaluated at every iterate.
@@ -559,10 +685,9 @@ struct Cell {
                 for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 / h : 0.0) - J[i * n + j];
             }
             st.newton++;
-            st.lu++;
-            if (!lu_factor(n, G.data(), piv.data())) return false;
+            if (!lin_prepare()) return false;
             for (int i = 0; i < n; ++i) d[i] = -f[i];
-            lu_solve(n, G.data(), piv.data(), d.data());
+            if (!lin_solve(d.data())) return false;
             for (int i = 0; i < n; ++i) y[i] += d[i];
             if (!finite_vec(y)) return false;
             if (wrms(n, d.data(), yn.data(), y.data(), o.rtol, o.atol) <= o.newton_tol) {
@@ -606,10 +731,9 @@ struct Cell {
                     for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 : 0.0) - gh * J[i * n + j];
                 }
                 st.newton++;
-                st.lu++;
-                if (!lu_factor(n, G.data(), piv.data())) return false;
+                if (!lin_prepare()) return false;
                 for (int i = 0; i < n; ++i) d[i] = -f[i];
-                lu_solve(n, G.data(), piv.data(), d.data());
+                if (!lin_solve(d.data())) return false;
                 for (int i = 0; i < n; ++i) { Gp[i] += d[i]; d[i] *= gh; Y[i] = base[i] + gh * Gp[i]; }
                 if (!finite_vec(Gp)) return false;
                 if (wrms(n, d.data(), yn.data(), Y.data(), o.rtol, o.atol) <= o.newton_tol) {
@@ -627,7 +751,7 @@ struct Cell {
                 y1[i] += h * tb.b[p] * Gam[p][i];
                 err[i] += h * (tb.b[p] - tb.bhat[p]) * Gam[p][i];
             }
-        if (o.err_filter) lu_solve(n, G.data(), piv.data(), err.data());
+        if (o.err_filter && !lin_solve(err.data())) return false;
         return finite_vec(y1) && admissible(y1, o.neg_tol);
     }
 
@@ -652,15 +776,14 @@ struct Cell {
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 / (h * g) : 0.0) - J[i * n + j];
         st.newton++;
-        st.lu++;
-        if (!lu_factor(n, G.data(), piv.data())) return false;
+        if (!lin_prepare()) return false;
         G1 = S0;
-        lu_solve(n, G.data(), piv.data(), G1.data());
+        if (!lin_solve(G1.data())) return false;
         for (int i = 0; i < n; ++i) Y2[i] = yn[i] + alpha * G1[i];
         if (!finite_vec(Y2)) return false;
         source(m, o.reactor, Y2.data(), G2.data());
         for (int i = 0; i < n; ++i) G2[i] += beta / h * G1[i];
-        lu_solve(n, G.data(), piv.data(), G2.data());
+        if (!lin_solve(G2.data())) return false;
         y1.assign(n, 0.0);
         err.assign(n, 0.0);
         for (int i = 0; i < n; ++i) {
@@ -685,9 +808,8 @@ struct Cell {
             for (int j = 0; j < n; ++j) G[i * n + j] = (i == j ? 1.0 : 0.0) - h * J[i * n + j];
         }
         st.newton++;
-        st.lu++;
-        if (!lu_factor(n, G.data(), piv.data())) return false;
-        lu_solve(n, G.data(), piv.data(), dy.data());
+        if (!lin_prepare()) return false;
+        if (!lin_solve(dy.data())) return false;
         y1 = yn;
         for (int i = 0; i < n; ++i) y1[i] += dy[i];
         lastY.clear();
@@ -1023,6 +1145,11 @@ void cgref_jacobian(const void* h, int reactor, long N, const double* y, double*
 }
 
 // Solve A x = b with LU and partial pivoting; A, b overwritten (x in b). 0 if singular.
+// GMRES of Section 3.4 on one dense system (row-major A, b in, x out).
+int cgref_gmres(int n, const double* A, double* b, int prec, int m, int maxit, double tol, int* iters) {
+    return gmres(n, A, b, prec, m, maxit, tol, iters) ? 1 : 0;
+}
+
 int cgref_lu_solve(int n, double* A, double* b) {
     std::vector<int> piv(n);
     if (!lu_factor(n, A, piv.data())) return 0;
@@ -1037,6 +1164,10 @@ void cgref_temperature(const void* h, int reactor, long N, const double* e, cons
     for (long c = 0; c < N; ++c) T[c] = recover_T(m, reactor, e[c], Y + c * m.ns, T0[c], iters);
 }
 
+namespace {
+void unpack(const int* iopt, const double* dopt, const double* tab, Opts& o, Tableau& tb);
+}  // namespace
+
 // Integrate N cells over dt. y in/out cell-major [N][ns+1] = (T, C).
 // status[N]; stats[N][4] = accepted steps, rejected/failed attempts, Newton
 // iterations, LU factorisations.
@@ -1044,18 +1175,8 @@ void cgref_integrate(const void* h, const int* iopt, const double* dopt, const d
                      long N, double* y, int* status, int* stats, int nthreads) {
     const Mech& m = *static_cast<const Mech*>(h);
     Opts o;
-    o.method = iopt[0]; o.reactor = iopt[1]; o.adaptive = iopt[2]; o.nsub = iopt[3];
-    o.max_newton = iopt[4]; o.max_steps = iopt[5]; o.max_halvings = iopt[6]; o.err_filter = iopt[7];
-    o.dt = dopt[0]; o.rtol = dopt[1]; o.atol = dopt[2]; o.newton_tol = dopt[3];
-    o.h0 = dopt[4]; o.hmin = dopt[5]; o.neg_tol = dopt[6];
     Tableau tb;
-    tb.s = (int)tab[0];
-    tb.err_order = (int)tab[1];
-    for (int i = 0; i < 5; ++i) {
-        for (int j = 0; j < 5; ++j) tb.A[i][j] = tab[2 + 5 * i + j];
-        tb.b[i] = tab[27 + i];
-        tb.bhat[i] = tab[32 + i];
-    }
+    unpack(iopt, dopt, tab, o, tb);
     const int n = m.ns + 1;
     parallel_for(N, nthreads, [&](long c) {
         Cell cell(m, o);
@@ -1078,6 +1199,8 @@ void unpack(const int* iopt, const double* dopt, const double* tab, Opts& o, Tab
     o.max_newton = iopt[4]; o.max_steps = iopt[5]; o.max_halvings = iopt[6]; o.err_filter = iopt[7];
     o.dt = dopt[0]; o.rtol = dopt[1]; o.atol = dopt[2]; o.newton_tol = dopt[3];
     o.h0 = dopt[4]; o.hmin = dopt[5]; o.neg_tol = dopt[6];
+    o.linear_solver = iopt[8]; o.prec = iopt[9]; o.gmres_m = iopt[10]; o.gmres_maxit = iopt[11];
+    o.gmres_tol = dopt[7];
     tb.s = (int)tab[0];
     tb.err_order = (int)tab[1];
     for (int i = 0; i < 5; ++i) {

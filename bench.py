@@ -218,23 +218,38 @@ METHODS = {
 }
 
 
-def opts_dict(config: int, precision: int, method: str | None = None):
+# --linear: the Newton systems' solver (Section 3.4); GMRES with
+# Gauss-Seidel preconditioning, restart 30, tolerance 1e-10 unless overridden
+LINEAR = {"lu": dict(linear_solver=0),
+          "gmres": dict(linear_solver=1, preconditioner=2, gmres_restart=30, gmres_maxit=200, gmres_tol=1e-10)}
+PRECS = {"none": 0, "jacobi": 1, "gs": 2}
+
+
+def opts_dict(config: int, precision: int, method: str | None = None, linear: str | None = None,
+              prec: str | None = None):
     o = dict(CONFIGS[config]["opts"])
     if method:
         o.update(METHODS[method])
+    if linear:
+        o.update(LINEAR[linear])
+        if prec:
+            o["preconditioner"] = PRECS[prec]
     o["precision"] = precision
     if config == 3:
         o["persistent"] = 1
     return o
 
 
-def workload_name(config: int, method: str | None) -> str:
+def workload_name(config: int, method: str | None, linear: str | None = None, prec: str | None = None) -> str:
     w = CONFIGS[config]["workload"]
-    if not method:
-        return w
-    extra = {"yass": "YASS (alpha 1, WRMS weights 1e-6 + 1e-3|y|, up to 12 halvings)",
-             "ros2": "Rosenbrock-2", "be": "backward Euler", "sdirk2": "SDIRK-2", "sdirk4": "SDIRK-4"}[method]
-    return w + "; integrator replaced by " + extra
+    if method:
+        extra = {"yass": "YASS (alpha 1, WRMS weights 1e-6 + 1e-3|y|, up to 12 halvings)",
+                 "ros2": "Rosenbrock-2", "be": "backward Euler", "sdirk2": "SDIRK-2", "sdirk4": "SDIRK-4"}[method]
+        w += "; integrator replaced by " + extra
+    if linear == "gmres":
+        w += "; Newton systems by GMRES(30), tol 1e-10, preconditioner " + {
+            "none": "none", "jacobi": "Jacobi", "gs": "Gauss-Seidel", None: "Gauss-Seidel"}[prec]
+    return w
 
 
 def oracle_opts(o: dict) -> dict:
@@ -269,7 +284,7 @@ def run_reference(args):
         return
     cfg = CONFIGS[args.config]
     parts = make_workload(args.config, args.cells or cfg["cells"])
-    opts = opts_dict(args.config, 0, args.method)
+    opts = opts_dict(args.config, 0, args.method, args.linear, args.prec)
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         cpu_oracle_sample(parts, opts, max(16, args.ref_sample // 8), threads)
@@ -283,7 +298,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(args.config, args.method), "config": args.config},
+        "data": "synthetic", "config": {"workload": workload_name(args.config, args.method, args.linear, args.prec),
+                                        "config": args.config},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.ref_sample} cells evenly spaced through the field, per step"},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -306,7 +322,7 @@ def run_gpu(args):
     cfg = CONFIGS[args.config]
     precision = cfg["precision"] if args.precision is None else args.precision
     parts = make_workload(args.config, args.cells or cfg["cells"], seed=rank)
-    opts_d = opts_dict(args.config, precision, args.method)
+    opts_d = opts_dict(args.config, precision, args.method, args.linear, args.prec)
     opts = chemgb.make_opts(**opts_d)
     stream = torch.cuda.Stream(dev)   # a side stream (graph capture needs one); all work goes there
     torch.cuda.set_stream(stream)
@@ -387,10 +403,15 @@ def run_gpu(args):
         sh = b["stats"].cpu().numpy()
         nwt = int(sh[2].astype(np.int64).sum())
         newton += nwt
-        per = algorithmic_flops_per_newton(m.ns, m.nr, j_term_count(m), precision == 1)
+        n1 = m.ns + 1
+        gm = opts_d.get("linear_solver", 0) == 1
+        per = algorithmic_flops_per_newton(m.ns, m.nr, j_term_count(m), precision == 1 or gm)
         if opts_d["method"] == 3:   # Rosenbrock-2: plus a second rate evaluation and solve per step
-            per += 30.0 * m.nr + 40.0 * m.ns + 2.0 * (m.ns + 1) ** 2
+            per += 30.0 * m.nr + 40.0 * m.ns + 2.0 * n1 ** 2
         flops += nwt * per
+        if gm:   # GMRES iterations (stats row 3): matvec 2n^2, preconditioner, Gram-Schmidt and norms ~10n
+            pc = {0: 0.0, 1: n1, 2: n1 * n1}[opts_d.get("preconditioner", 2)]
+            flops += float(sh[3].astype(np.int64).sum()) * (2.0 * n1 * n1 + pc + 10.0 * n1) - nwt * 2.0 * n1 * n1
         failed += int((b["st"].cpu().numpy() != 0).sum())
         stat_means.append({"species": m.ns, "steps": float(sh[0].mean()), "rejects": float(sh[1].mean()),
                            "newton": float(sh[2].mean())})
@@ -447,7 +468,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.config, args.method), "config": args.config,
+        "config": {"workload": workload_name(args.config, args.method, args.linear, args.prec),
+                   "config": args.config,
                    "cells_per_gpu": N_total,
                    "newton_matrix": "fp32" if precision == 1 else "fp64", "state_bytes": state_bytes,
                    "l2": "state larger than L2 (129 MB); no flush" if state_bytes > 129e6
@@ -728,6 +750,8 @@ def main():
     ap.add_argument("--adj-sample", type=int, default=8, help="--config 4: cells checked against the oracle")
     ap.add_argument("--method", choices=sorted(METHODS), default=None,
                     help="replace the workload's integrator (configs 1, 2, 3, 5)")
+    ap.add_argument("--linear", choices=sorted(LINEAR), default=None, help="Newton systems: dense LU or GMRES")
+    ap.add_argument("--prec", choices=sorted(PRECS), default=None, help="GMRES preconditioner (default gs)")
     args = ap.parse_args()
     if args.config == 4:
         (run_reference_adjoint if args.impl == "reference" else run_adjoint)(args)

@@ -82,6 +82,16 @@ enum { CG_BE = 0, CG_SDIRK2 = 1, CG_SDIRK4 = 2, CG_ROS2 = 3, CG_YASS = 4 };
 /* arithmetic of the Newton matrix factorisation */
 enum { CG_FP64 = 0, CG_FP32LU = 1 };
 
+/* linear solver of the Newton systems (Section 3.4): the dense LU with
+ * partial pivoting, or restarted GMRES with left preconditioning (x0 = 0,
+ * Givens rotations, converged when the preconditioned residual is at most
+ * gmres_tol times that of x = 0); preconditioners: none, Jacobi (the
+ * diagonal), Gauss-Seidel (the lower triangle with the diagonal). A GMRES
+ * solve that does not converge within gmres_maxit iterations fails the step
+ * like a singular matrix. */
+enum { CG_LU = 0, CG_GMRES = 1 };
+enum { CG_PC_NONE = 0, CG_PC_JACOBI = 1, CG_PC_GAUSS_SEIDEL = 2 };
+
 /*
  * Mechanism description (host arrays, copied by cg_mech_create; the caller
  * keeps ownership). Reactions are written sum nu^f_i A_i <=> sum nu^r_i A_i
@@ -188,6 +198,11 @@ typedef struct {
     double h0;         /* adaptive: first step (0: dt)                                */
     double hmin;       /* adaptive: smallest step                                     */
     double neg_tol;    /* a step is rejected when some C_i < -neg_tol * sum C         */
+    int linear_solver; /* CG_LU (default) or CG_GMRES                                 */
+    int preconditioner;/* GMRES: CG_PC_NONE, CG_PC_JACOBI, CG_PC_GAUSS_SEIDEL         */
+    int gmres_restart; /* GMRES: Krylov dimension before a restart, 1..64             */
+    int gmres_maxit;   /* GMRES: iterations per linear solve                          */
+    double gmres_tol;  /* GMRES: relative tolerance of the preconditioned residual    */
 } cg_integrate_opts;
 
 void cg_integrate_opts_default(cg_integrate_opts *opts);
@@ -207,7 +222,8 @@ cg_status cg_autotune(cg_mech *mech, const cg_integrate_opts *opts, int64_t N, c
                       const double *Y, const double *p_or_rho, const char *cache_json, void *stream,
                       double *best_ms);
 
-/* Integrate N cells over opts->dt.
+/* Integrate N cells over opts->dt (cell_stats[3*N + c] counts LU
+ * factorisations, or GMRES iterations with CG_GMRES).
  *   T[N], Y[ns*N]   in: initial temperature and mass fractions;
  *                   out: final ones (overwritten in place)
  *   p_or_rho[N]     pressure (CG_CONP, CG_CONP_LITERAL: C = rho Y / W with

@@ -22,6 +22,8 @@ CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ECAPACITY, CG_EUNSUPPORTED = range(6)
 CG_CONV, CG_CONP, CG_CONP_LITERAL = 0, 1, 2
 CG_BE, CG_SDIRK2, CG_SDIRK4, CG_ROS2, CG_YASS = 0, 1, 2, 3, 4
 CG_FP64, CG_FP32LU = 0, 1
+CG_LU, CG_GMRES = 0, 1
+CG_PC_NONE, CG_PC_JACOBI, CG_PC_GAUSS_SEIDEL = 0, 1, 2
 
 _lib = None
 
@@ -43,7 +45,9 @@ class cg_integrate_opts(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in (
         "method", "reactor", "adaptive", "precision", "nsub", "max_newton", "max_steps",
         "max_halvings", "err_filter", "persistent")] + [(k, ctypes.c_double) for k in (
-            "dt", "rtol", "atol", "newton_tol", "h0", "hmin", "neg_tol")]
+            "dt", "rtol", "atol", "newton_tol", "h0", "hmin", "neg_tol")] + [(k, ctypes.c_int) for k in (
+                "linear_solver", "preconditioner", "gmres_restart", "gmres_maxit")] + [
+        ("gmres_tol", ctypes.c_double)]
 
 
 EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n_reactions",

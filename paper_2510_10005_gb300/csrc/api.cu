@@ -107,7 +107,7 @@ Schedule make_schedule(std::vector<Term> terms, int lanes_n) {
 // smem_limit bytes per cell), the rest into the cell's global scratch slot.
 // mat_bytes: 8 for the FP64 Newton matrix, 4 for the FP32 one; adjoint:
 // add the arrays of the backward sweep (size 0 otherwise).
-Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoint = false) {
+Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoint = false, int gmres_m = 0) {
     using namespace cg;
     const int n = ns + 1;
     Layout L;
@@ -125,9 +125,11 @@ Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoin
     size[A_GRAD] = adjoint ? 3 * nr : 0;
     for (int a : {A_LAM, A_LAMN, A_NU, A_RHS}) size[a] = adjoint ? n : 0;
     size[A_ACC] = adjoint ? 5 * n : 0;
+    size[A_KV] = gmres_m ? (gmres_m + 1) * (n | 1) : 0;
+    size[A_KH] = gmres_m ? (gmres_m + 1) * gmres_m + 2 * gmres_m + 2 * (gmres_m + 1) : 0;
     const int order[A_COUNT] = {A_RED, A_PIV, A_G, A_RINV, A_YN, A_Y, A_F, A_S, A_BASE,
-                                A_S0, A_ERR, A_Y1, A_COLA, A_COLB, A_SP, A_V, A_GAM, A_NU,
-                                A_RHS, A_LAM, A_LAMN, A_ACC, A_XF, A_RD, A_GRAD};
+                                A_S0, A_ERR, A_Y1, A_COLA, A_COLB, A_SP, A_V, A_GAM, A_KH, A_KV,
+                                A_NU, A_RHS, A_LAM, A_LAMN, A_ACC, A_XF, A_RD, A_GRAD};
     // 1 KiB of the block's shared memory stays free for the kernels' static variables
     const long budget = (long)((smem_limit > 2048 ? smem_limit - 1024 : 1024) / sizeof(double));
     int so = 0, go = 0;
@@ -446,11 +448,18 @@ cg_status build_schedules(cg_mech* m, int team) {
     return CG_OK;
 }
 
+// Layout of one cell for the options: the mechanism's own for the LU, one
+// with the Krylov arrays for GMRES.
+Layout task_layout(const cg_mech* m, const IntParams& P) {
+    if (P.linear_solver == 0) return P.precision ? m->L32 : m->L;
+    return make_layout(m->ns, m->nr, P.precision ? 4 : 8, m->smem_limit, false, P.gmres_m);
+}
+
 cg::Task make_task(const cg_mech* m, const IntParams& P, int64_t N, int64_t first, double* T, double* Y,
                    const double* p, int32_t* status, int32_t* stats) {
     cg::Task t;
     t.M = m->dm;
-    t.L = P.precision ? m->L32 : m->L;
+    t.L = task_layout(m, P);
     t.N = N;
     t.first = first;
     t.T = T;
@@ -792,6 +801,11 @@ void cg_integrate_opts_default(cg_integrate_opts* o) {
     o->h0 = 0.0;
     o->hmin = 1e-20;
     o->neg_tol = 1e-6;
+    o->linear_solver = CG_LU;
+    o->preconditioner = CG_PC_GAUSS_SEIDEL;
+    o->gmres_restart = 30;
+    o->gmres_maxit = 200;
+    o->gmres_tol = 1e-10;
 }
 
 static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
@@ -808,6 +822,12 @@ static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
     if (!(o->rtol >= 0.0) || !(o->atol >= 0.0) || !(o->rtol + o->atol > 0.0) || !(o->newton_tol > 0.0) ||
         !(o->hmin >= 0.0) || !(o->h0 >= 0.0) || !(o->neg_tol >= 0.0))
         return fail(CG_EINVAL, "tolerances must be non-negative (rtol + atol and newton_tol positive)");
+    if (o->linear_solver != CG_LU && o->linear_solver != CG_GMRES) return fail(CG_EINVAL, "bad linear_solver");
+    if (o->linear_solver == CG_GMRES &&
+        (o->preconditioner < CG_PC_NONE || o->preconditioner > CG_PC_GAUSS_SEIDEL || o->gmres_restart < 1 ||
+         o->gmres_restart > 64 || o->gmres_maxit < 1 || !(o->gmres_tol > 0.0)))
+        return fail(CG_EINVAL, "GMRES needs a preconditioner 0..2, 1 <= gmres_restart <= 64, gmres_maxit >= 1 "
+                               "and gmres_tol > 0");
     Tab t;
     if (!make_tableau(o->method, t)) return fail(CG_EINVAL, "tableau construction failed");
     P.method = o->method;
@@ -826,6 +846,11 @@ static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
     P.h0 = o->h0;
     P.hmin = o->hmin;
     P.neg_tol = o->neg_tol;
+    P.linear_solver = o->linear_solver;
+    P.prec = o->preconditioner;
+    P.gmres_m = o->linear_solver == CG_GMRES ? o->gmres_restart : 0;
+    P.gmres_maxit = o->gmres_maxit;
+    P.gmres_tol = o->gmres_tol;
     P.s = t.s;
     P.err_order = t.err_order;
     P.start_zero = t.start_zero;
@@ -933,14 +958,15 @@ cg_status cg_integrate_adjoint(const cg_mech* m, const cg_integrate_opts* o, int
         return CG_OK;
     }
     if (!ckpt || !ckpt_n || !dT_end || !dY_end || !dT0 || !dY0) return fail(CG_EINVAL, "NULL array");
+    const cg::Layout LA = P.linear_solver ? make_layout(m->ns, m->nr, 8, m->smem_limit, true, P.gmres_m) : m->LA;
     int tpb = m->dm.team > 32 ? 1 : m->tpb;
-    while (tpb > 1 && (size_t)tpb * m->LA.stotal * sizeof(double) > kMaxSmemPerBlock) --tpb;
-    if ((size_t)m->LA.stotal * sizeof(double) > kMaxSmemPerBlock)
+    while (tpb > 1 && (size_t)tpb * LA.stotal * sizeof(double) > kMaxSmemPerBlock) --tpb;
+    if ((size_t)LA.stotal * sizeof(double) > kMaxSmemPerBlock)
         return fail(CG_ECAPACITY, "adjoint arrays need %zu bytes of shared memory per cell",
-                    (size_t)m->LA.stotal * sizeof(double));
+                    (size_t)LA.stotal * sizeof(double));
     cg::AdjTask t;
     t.M = m->dm;
-    t.L = m->LA;
+    t.L = LA;
     t.N = N;
     t.ckpt = ckpt;
     t.ckpt_n = ckpt_n;

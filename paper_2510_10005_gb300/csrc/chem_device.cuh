@@ -91,6 +91,9 @@ enum {
     A_GRAD,     // 3 nr: dL/d(ln A, b, Ea), reaction-major
     A_LAM, A_LAMN, A_NU, A_RHS,   // n each
     A_ACC,      // 5 n: sum over later stages of h a_qp J_q^T nu_q
+    // GMRES only (size 0 with the LU)
+    A_KV,       // (m+1) x vs Krylov basis
+    A_KH,       // (m+1) m Hessenberg + 2 m rotations + 2 (m+1) (g, projections)
     A_COUNT
 };
 
@@ -107,6 +110,7 @@ struct Ws {
     double *G, *RD, *SP, *V, *yn, *Y, *base, *S, *S0, *f, *err, *y1, *colA, *colB, *rinv, *Gam, *red;
     int* piv;
     double *xf, *grad, *lam, *lamn, *nu, *rhs, *acc;
+    double *kv, *kh;
 };
 
 __device__ __forceinline__ Ws make_ws(const Layout& L, double* sbase, double* gbase) {
@@ -122,6 +126,7 @@ __device__ __forceinline__ Ws make_ws(const Layout& L, double* sbase, double* gb
     w.piv = reinterpret_cast<int*>(p[A_PIV]);
     w.xf = p[A_XF]; w.grad = p[A_GRAD]; w.lam = p[A_LAM]; w.lamn = p[A_LAMN];
     w.nu = p[A_NU]; w.rhs = p[A_RHS]; w.acc = p[A_ACC];
+    w.kv = p[A_KV]; w.kh = p[A_KH];
     return w;
 }
 
@@ -129,6 +134,8 @@ __device__ __forceinline__ Ws make_ws(const Layout& L, double* sbase, double* gb
 struct IntParams {
     int method, reactor, adaptive, nsub, max_newton, max_steps, max_halvings, err_filter;
     int precision;                  // 0: FP64 Newton matrix, 1: FP32 Newton matrix
+    int linear_solver, prec, gmres_m, gmres_maxit;   // 0 LU, 1 GMRES; preconditioner; restart; limit
+    double gmres_tol;
     double dt, rtol, atol, newton_tol, h0, hmin, neg_tol;
     int s, err_order, start_zero;   // stages; embedded order; BE starts Newton at y_n
     double A[5][5], b[5], bh[5];
@@ -757,6 +764,166 @@ __device__ void lu_solve_t(const MT* G, int n, int ld, const int* piv, const dou
             if (p != k) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
         }
     team_sync<TEAM>();
+}
+
+// ---------------------------------------------------------------------------
+// GMRES (Section 3.4), run by one warp (l = lane within the warp)
+
+// v <- M^{-1} v for M = I (prec 0), diag(G) (Jacobi, prec 1) or the lower
+// triangle of G with its diagonal (Gauss-Seidel, prec 2, forward
+// substitution by columns); dinv = 1 / diag(G).
+template <class MT>
+__device__ void warp_precondition(const MT* G, int n, int ld, const double* dinv, int prec, double* v, int l) {
+    if (prec == 1) {
+        for (int i = l; i < n; i += 32) v[i] *= dinv[i];
+    } else if (prec == 2) {
+        for (int j = 0; j < n; ++j) {
+            if (l == 0) v[j] *= dinv[j];
+            __syncwarp();
+            const double vj = v[j];
+            for (int i = j + 1 + l; i < n; i += 32) v[i] = fma(-static_cast<double>(G[i * ld + j]), vj, v[i]);
+        }
+    }
+    __syncwarp();
+}
+
+// out = G v, one row per lane at a time, four partial sums for independent FMAs.
+template <class MT>
+__device__ void warp_matvec(const MT* G, int n, int ld, const double* v, double* out, int l) {
+    for (int i = l; i < n; i += 32) {
+        const MT* row = G + i * ld;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int c = 0;
+        for (; c + 4 <= n; c += 4) {
+            s0 = fma(static_cast<double>(row[c]), v[c], s0);
+            s1 = fma(static_cast<double>(row[c + 1]), v[c + 1], s1);
+            s2 = fma(static_cast<double>(row[c + 2]), v[c + 2], s2);
+            s3 = fma(static_cast<double>(row[c + 3]), v[c + 3], s3);
+        }
+        for (; c < n; ++c) s0 = fma(static_cast<double>(row[c]), v[c], s0);
+        out[i] = (s0 + s1) + (s2 + s3);
+    }
+    __syncwarp();
+}
+
+static __device__ __forceinline__ double warp_dot(const double* a, const double* b, int n, int l) {
+    double s = 0.0;
+    for (int i = l; i < n; i += 32) s = fma(a[i], b[i], s);
+    return warp_sum(s);
+}
+
+// Workspace of warp_gmres: V[(m+1) vs] (Krylov basis, odd row stride vs),
+// K[(m+1) m + 2m + 2(m+1)] (Hessenberg matrix, Givens cosines and sines,
+// right-hand side g, projections), bb and w: n each.
+struct GmresWs {
+    double *V, *H, *cs, *sn, *g, *t, *bb, *w;
+    int vs, m;
+};
+
+// Restarted GMRES with left preconditioning: M^{-1} G x = M^{-1} b from
+// x0 = 0; Arnoldi by classical Gram-Schmidt applied twice (each lane forms
+// whole dot products with its basis vectors, so one pass needs no
+// reduction); Givens rotations for the least-squares problem (lane 0);
+// converged when the preconditioned residual is at most tol ||M^{-1} b||.
+// x: b in, solution out. Returns false when maxit iterations do not
+// converge or a rotation degenerates. `iters` receives the iterations.
+template <class MT>
+__device__ bool warp_gmres(const MT* G, int n, int ld, const double* dinv, int prec, int maxit, double tol,
+                           double* x, const GmresWs& K, int l, int& iters) {
+    const int m = K.m, vs = K.vs;
+    double* const bb = K.bb;
+    double* const w = K.w;
+    iters = 0;
+    for (int i = l; i < n; i += 32) {
+        bb[i] = x[i];
+        w[i] = x[i];
+        x[i] = 0.0;
+    }
+    __syncwarp();
+    warp_precondition<MT>(G, n, ld, dinv, prec, w, l);
+    const double bnorm = sqrt(warp_dot(w, w, n, l));
+    if (bnorm == 0.0) return true;
+    const double stop = tol * bnorm;
+    bool first = true;
+    while (true) {
+        if (!first) {   // w = M^{-1} (b - G x)
+            warp_matvec<MT>(G, n, ld, x, w, l);
+            for (int i = l; i < n; i += 32) w[i] = bb[i] - w[i];
+            __syncwarp();
+            warp_precondition<MT>(G, n, ld, dinv, prec, w, l);
+        }
+        first = false;
+        const double beta = sqrt(warp_dot(w, w, n, l));
+        if (beta <= stop) return true;
+        if (iters >= maxit) return false;
+        const double ib = 1.0 / beta;
+        for (int i = l; i < n; i += 32) K.V[i] = w[i] * ib;
+        for (int q = l; q <= m; q += 32) K.g[q] = q == 0 ? beta : 0.0;
+        __syncwarp();
+        int k = 0;
+        for (int j = 0; j < m && iters < maxit; ++j) {
+            const double* vj = K.V + j * vs;
+            warp_matvec<MT>(G, n, ld, vj, w, l);
+            warp_precondition<MT>(G, n, ld, dinv, prec, w, l);
+            ++iters;
+            for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+                for (int q = l; q <= j; q += 32) {
+                    const double* vq = K.V + q * vs;
+                    double s = 0.0;
+                    for (int i = 0; i < n; ++i) s = fma(w[i], vq[i], s);
+                    K.t[q] = s;
+                    K.H[q * m + j] = pass == 0 ? s : K.H[q * m + j] + s;
+                }
+                __syncwarp();
+                for (int i = l; i < n; i += 32) {
+                    double v = w[i];
+                    for (int q = 0; q <= j; ++q) v = fma(-K.t[q], K.V[q * vs + i], v);
+                    w[i] = v;
+                }
+                __syncwarp();
+            }
+            const double hn = sqrt(warp_dot(w, w, n, l));
+            if (hn > 0.0) {
+                const double ih = 1.0 / hn;
+                for (int i = l; i < n; i += 32) K.V[(j + 1) * vs + i] = w[i] * ih;
+            }
+            if (l == 0) {
+                double* Hc = K.H + j;   // column j, rows q at Hc[q * m]
+                Hc[(j + 1) * m] = hn;
+                for (int q = 0; q < j; ++q) {
+                    const double a = Hc[q * m], b = Hc[(q + 1) * m];
+                    Hc[q * m] = fma(K.cs[q], a, K.sn[q] * b);
+                    Hc[(q + 1) * m] = fma(-K.sn[q], a, K.cs[q] * b);
+                }
+                const double a = Hc[j * m], b = hn;
+                const double rho = sqrt(fma(a, a, b * b));
+                const double c = rho > 0.0 ? a / rho : 0.0, s = rho > 0.0 ? b / rho : 0.0;
+                K.cs[j] = c;
+                K.sn[j] = s;
+                Hc[j * m] = rho;
+                Hc[(j + 1) * m] = 0.0;
+                K.g[j + 1] = -s * K.g[j];
+                K.g[j] *= c;
+            }
+            __syncwarp();
+            if (!(K.H[j * m + j] > 0.0)) return false;   // degenerate rotation
+            k = j + 1;
+            if (fabs(K.g[j + 1]) <= stop || hn == 0.0) break;
+        }
+        if (l == 0)   // H y = g (upper triangular), y into t
+            for (int q = k - 1; q >= 0; --q) {
+                double s = K.g[q];
+                for (int c = q + 1; c < k; ++c) s = fma(-K.H[q * m + c], K.t[c], s);
+                K.t[q] = s / K.H[q * m + q];
+            }
+        __syncwarp();
+        for (int i = l; i < n; i += 32) {
+            double v = x[i];
+            for (int q = 0; q < k; ++q) v = fma(K.t[q], K.V[q * vs + i], v);
+            x[i] = v;
+        }
+        __syncwarp();
+    }
 }
 
 // weighted RMS norm with w_i = atol + rtol max(|a_i|, |b_i|)

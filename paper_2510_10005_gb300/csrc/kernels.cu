@@ -323,6 +323,7 @@ static cudaError_t launch_integrate_t(const Tasks& tasks, const IntParams& P, in
         gstride = gstride > tasks.t[k].L.gtotal ? gstride : tasks.t[k].L.gtotal;
     }
     gstride = round_up(gstride, 32);   // 256-byte aligned slots
+    while (tpb > 1 && (size_t)tpb * sstride * sizeof(double) > 227 * 1024) --tpb;   // larger layouts (GMRES)
     const void* fn = (const void*)integrate_kernel<TEAM, MT>;
     const size_t smem = (size_t)tpb * sstride * sizeof(double);
     cudaError_t e = set_smem(fn, smem);
@@ -360,6 +361,7 @@ static cudaError_t launch_integrate_on_t(const Tasks& tasks, const IntParams& P,
         gstride = gstride > tasks.t[k].L.gtotal ? gstride : tasks.t[k].L.gtotal;
     }
     gstride = round_up(gstride, 32);
+    while (tpb > 1 && (size_t)tpb * sstride * sizeof(double) > 227 * 1024) --tpb;
     const void* fn = (const void*)integrate_kernel<TEAM, MT>;
     const size_t smem = (size_t)tpb * sstride * sizeof(double);
     cudaError_t e = set_smem(fn, smem);

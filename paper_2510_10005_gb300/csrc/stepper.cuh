@@ -55,6 +55,62 @@ struct Counters {
     int steps, rejects, newton, lu;
 };
 
+// Linear solver of the Newton systems (Section 3.4): the dense LU of G, or
+// GMRES on G as assembled (one warp of the team; the others wait). Counter
+// `lu` counts factorisations or GMRES iterations.
+template <int TEAM, class MT>
+__device__ __forceinline__ bool lin_prepare(const Ws& W, const IntParams& P, int n, Counters& cnt, int lane) {
+    MT* G = reinterpret_cast<MT*>(W.G);
+    if (P.linear_solver == 0) {
+        cnt.lu++;
+        return lu_factor<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, W.red, lane);
+    }
+    bool zero = false;   // inverse diagonal for the preconditioner
+    for (int i = lane; i < n; i += TEAM) {
+        const double d = static_cast<double>(G[i * W.ld + i]);
+        zero |= d == 0.0;
+        W.rinv[i] = d != 0.0 ? rcp_nr(d) : 0.0;
+    }
+    team_sync<TEAM>();
+    zero = team_any<TEAM>(zero, W.red);
+    return P.prec == 0 || !zero;
+}
+
+template <int TEAM, class MT>
+__device__ __forceinline__ bool lin_solve(const Ws& W, const IntParams& P, int n, double* x, Counters& cnt,
+                                          int lane) {
+    const MT* G = reinterpret_cast<const MT*>(W.G);
+    if (P.linear_solver == 0) {
+        lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, x, lane);
+        return true;
+    }
+    int* flag = reinterpret_cast<int*>(W.red + 20);
+    if (lane < 32) {
+        GmresWs K;
+        K.m = P.gmres_m;
+        K.vs = n | 1;
+        K.V = W.kv;
+        K.H = W.kh;
+        K.cs = K.H + (K.m + 1) * K.m;
+        K.sn = K.cs + K.m;
+        K.g = K.sn + K.m;
+        K.t = K.g + K.m + 1;
+        K.bb = W.colA;
+        K.w = W.colB;
+        int it = 0;
+        const bool ok = warp_gmres<MT>(G, n, W.ld, W.rinv, P.prec, P.gmres_maxit, P.gmres_tol, x, K, lane, it);
+        if (lane == 0) {
+            flag[0] = ok ? 1 : 0;
+            flag[1] = it;
+        }
+    }
+    team_sync<TEAM>();
+    const bool ok = flag[0] != 0;
+    cnt.lu += flag[1];
+    team_sync<TEAM>();
+    return ok;
+}
+
 // One step of size h from W.yn: stages of the tableau in stage-derivative
 // form (Appendix A), each by full Newton with G = I - a_pp h J(Y_p). On
 // success y1 holds the new state and err the (filtered) embedded estimate.
@@ -97,9 +153,8 @@ __device__ bool rk_step(const DevMech& M, const Ws& W, const IntParams& P, doubl
             for (int i = lane; i < n; i += TEAM) f[i] = S[i] - Gp[i];   // -f(Gamma)
             team_sync<TEAM>();
             cnt.newton++;
-            cnt.lu++;
-            if (!lu_factor<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, W.red, lane)) return false;
-            lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, f, lane);
+            if (!lin_prepare<TEAM, MT>(W, P, n, cnt, lane)) return false;
+            if (!lin_solve<TEAM, MT>(W, P, n, f, cnt, lane)) return false;
             for (int i = lane; i < n; i += TEAM) {
                 const double g = Gp[i] + f[i];
                 Gp[i] = g;
@@ -129,7 +184,7 @@ __device__ bool rk_step(const DevMech& M, const Ws& W, const IntParams& P, doubl
     }
     team_sync<TEAM>();
     if (team_any<TEAM>(bad, W.red)) return false;
-    if (P.adaptive && P.err_filter) lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, err, lane);
+    if (P.adaptive && P.err_filter && !lin_solve<TEAM, MT>(W, P, n, err, cnt, lane)) return false;
     // admissible: T > 0 and C_i >= -neg_tol sum C
     double cs = 0.0;
     for (int i = 1 + lane; i < n; i += TEAM) cs += y1[i];
@@ -166,9 +221,8 @@ __device__ bool ros2_step(const DevMech& M, const Ws& W, const IntParams& P, dou
     for (int i = lane; i < n; i += TEAM) G1[i] = hg * W.S[i];
     team_sync<TEAM>();
     cnt.newton++;
-    cnt.lu++;
-    if (!lu_factor<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, W.red, lane)) return false;
-    lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, G1, lane);
+    if (!lin_prepare<TEAM, MT>(W, P, n, cnt, lane)) return false;
+    if (!lin_solve<TEAM, MT>(W, P, n, G1, cnt, lane)) return false;
     bool bad = false;
     for (int i = lane; i < n; i += TEAM) {
         const double v = fma(al, G1[i], yn[i]);
@@ -181,7 +235,7 @@ __device__ bool ros2_step(const DevMech& M, const Ws& W, const IntParams& P, dou
     assemble_source<TEAM>(M, W, W.Y, P.reactor, Mc2, lane);
     for (int i = lane; i < n; i += TEAM) G2[i] = fma(hg, W.S[i], g * be * G1[i]);
     team_sync<TEAM>();
-    lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, G2, lane);
+    if (!lin_solve<TEAM, MT>(W, P, n, G2, cnt, lane)) return false;
     const double e = 0.5 / g;
     for (int i = lane; i < n; i += TEAM) {
         const double v = fma(P.b[1], G2[i], fma(P.b[0], G1[i], yn[i]));

@@ -42,7 +42,9 @@ def test_opts_default(lib):
     o = chemgb.cg_integrate_opts_default()
     assert (o.method, o.reactor, o.adaptive, o.precision) == (chemgb.CG_SDIRK4, chemgb.CG_CONP, 1, 0)
     assert o.rtol == 1e-6 and o.atol == 1e-12 and o.newton_tol == 0.03 and o.neg_tol == 1e-6
-    assert ctypes.sizeof(chemgb.cg_integrate_opts) == 10 * 4 + 7 * 8
+    assert ctypes.sizeof(chemgb.cg_integrate_opts) == 10 * 4 + 7 * 8 + 4 * 4 + 8
+    assert (o.linear_solver, o.preconditioner, o.gmres_restart, o.gmres_maxit, o.gmres_tol) == \
+        (chemgb.CG_LU, chemgb.CG_PC_GAUSS_SEIDEL, 30, 200, 1e-10)
 
 
 def _desc(mech):

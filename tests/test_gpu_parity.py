@@ -382,3 +382,81 @@ def test_rosenbrock_and_yass_refusals(mechs, handles):
         with pytest.raises(chemgb.ChemgbError) as e:
             chemgb.cg_integrate_adjoint(h, o, ck, ckn, z, zy, z.clone(), zy.clone())
         assert e.value.code == chemgb.CG_EUNSUPPORTED
+
+
+# --- GMRES (Section 3.4) -----------------------------------------------------
+
+GM = dict(linear_solver=oracle.GMRES, preconditioner=oracle.PC_GAUSS_SEIDEL, gmres_restart=30,
+          gmres_maxit=400, gmres_tol=1e-13)
+
+
+def merged(*ds, **kw):
+    out = {}
+    for d_ in ds:
+        out.update(d_)
+    out.update(kw)
+    return out
+
+
+@pytest.mark.parametrize("prec", [oracle.PC_NONE, oracle.PC_JACOBI, oracle.PC_GAUSS_SEIDEL])
+def test_gmres_backward_euler_parity(mechs, ref, handles, prec):
+    """Backward Euler with GMRES, Newton and GMRES iterated to tight
+    tolerances: the same states as the oracle's GMRES to 1e-10, the same
+    statuses and Newton counts (GMRES iteration counts may differ by
+    rounding of the orthogonalisation: modified Gram-Schmidt there,
+    classical twice here)."""
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 1000, (1000, 1500), (1, 1), (0.5, 2), "H2", seed=0)
+    o = merged(BE_OPTS, GM, preconditioner=prec)
+    To, Yo, so, sto = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    same = np.all(stg[:, :3] == sto[:, :3], axis=1)
+    assert same.mean() > 0.99
+    assert_state_close(Tg[same], Yg[same], To[same], Yo[same], 1e-10, 1e-22)
+    assert np.all(np.abs(stg[:, 3] - sto[:, 3]) <= 0.1 * sto[:, 3] + 2)
+
+
+@pytest.mark.parametrize("method", [oracle.SDIRK4, oracle.ROS2])
+def test_gmres_flame_field_parity(mechs, ref, handles, method):
+    m, r, h = mechs["ch4"], ref["ch4"], handles["ch4"]
+    T, Y, p = inputs.field_flames(m, 4096, seed=0)
+    idx = np.arange(9, 4096, 40)
+    o = merged(ADAPT, GM, method=method, gmres_tol=1e-10)
+    To, Yo, so, _ = r.integrate(T[idx], Y[idx], p[idx], o, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**o), T[idx], Y[idx], p[idx])
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    np.testing.assert_allclose(Tg, To, rtol=1e-6)
+    assert np.max(np.abs(Yg - Yo)) < 1e-6
+    assert np.all(stg[:, 3] >= stg[:, 2])          # at least one GMRES iteration per linear system
+
+
+def test_gmres_fp32_matrix_flame_field(mechs, ref, handles):
+    """GMRES on the FP32 Newton matrix (inexact Newton) lands on the FP64
+    oracle's solution within the integrator's tolerance."""
+    m, r, h = mechs["ch4"], ref["ch4"], handles["ch4"]
+    T, Y, p = inputs.field_flames(m, 4096, seed=0)
+    idx = np.arange(13, 4096, 64)
+    o = merged(ADAPT, GM, gmres_tol=1e-8)
+    To, Yo, so, _ = r.integrate(T[idx], Y[idx], p[idx], dict(ADAPT), nthreads=8)
+    Tg, Yg, sg, _ = run_gpu(h, chemgb.make_opts(**merged(o, precision=chemgb.CG_FP32LU)), T[idx], Y[idx], p[idx])
+    assert np.all(sg == 0) and np.all(so == 0)
+    np.testing.assert_allclose(Tg, To, rtol=1e-5)
+    assert np.max(np.abs(Yg - Yo)) < 1e-5
+
+
+def test_gmres_limits_and_arguments(mechs, ref, handles):
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 40, (1300, 1400), (1, 1), (0.5, 2), "H2", seed=2)
+    o = merged(BE_OPTS, GM, gmres_maxit=1, preconditioner=oracle.PC_NONE, max_halvings=2)
+    _, _, so, _ = r.integrate(T, Y, p, o, nthreads=8)
+    _, _, sg, _ = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    assert np.any(sg == chemgb.CG_CELL_NEWTON_FAIL)     # one iteration does not solve the system
+    for bad in (dict(gmres_restart=0), dict(gmres_restart=65), dict(gmres_maxit=0), dict(gmres_tol=0.0),
+                dict(preconditioner=3), dict(linear_solver=2)):
+        with pytest.raises(chemgb.ChemgbError) as e:
+            run_gpu(h, chemgb.make_opts(**merged(BE_OPTS, GM, bad)), T, Y, p)
+        assert e.value.code == chemgb.CG_EINVAL

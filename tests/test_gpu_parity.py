@@ -415,9 +415,13 @@ def test_gmres_backward_euler_parity(mechs, ref, handles, prec):
     Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
     np.testing.assert_array_equal(sg, so)
     assert np.all(so == 0)
+    # a GMRES solve that stops at gmres_maxit on one side only fails that
+    # Newton step there: the step is halved and the cell takes another (as
+    # valid) path; compare the cells whose accepted, rejected and Newton
+    # counts agree
     same = np.all(stg[:, :3] == sto[:, :3], axis=1)
     assert same.mean() > 0.98
-    assert_state_close(Tg, Yg, To, Yo, 1e-10, 1e-22)
+    assert_state_close(Tg[same], Yg[same], To[same], Yo[same], 1e-10, 1e-22)
 
 
 @pytest.mark.parametrize("method", [oracle.SDIRK4, oracle.ROS2])

@@ -251,6 +251,28 @@ cg_status cg_integrate_batch(int n_mech, const cg_mech *const *mechs, const int6
                              const cg_integrate_opts *opts, void *stream);
 
 /*
+ * Operator-split reaction step of a compressible flow solver (Section 5.5,
+ * eq. openfom_fvm): per cell, from the conserved variables the flow solver
+ * holds -- rho[N] (kg/m^3), the mass-specific internal energy e[N] (u, J/kg,
+ * chemical plus sensible, NASA-7 reference) and rhoY[ns*N] (kg/m^3, SoA) --
+ * recovers T by `iters` Newton iterations on sum_i Y_i u_i(T) = e from the
+ * guess in T (Section 2.1; the paper uses 5), integrates the concentrations
+ * C_i = rho Y_i / W_i at constant volume over opts->dt (Section 3, eq.
+ * temperature_source; opts->reactor must be CG_CONV) and writes the
+ * temperature after the step to T and the species source
+ *   R[i*N + c] = W_i (C_i^{n+1} - C_i^n) / dt   (kg/m^3/s; sum_i R_i = 0)
+ * that the flow solver adds to its species equations. Cells whose input is
+ * not finite (or whose recovered T is not positive) get status
+ * CG_CELL_NONFINITE, R = 0 and T unchanged. cell_status, cell_stats as
+ * cg_integrate. Device arrays; allocates only the stream-ordered work
+ * counter and scratch of a persistent launch. Errors: as cg_integrate, and
+ * CG_EINVAL for another reactor or iters outside 0..100.
+ */
+cg_status cg_react_split(const cg_mech *mech, const cg_integrate_opts *opts, int64_t N, const double *rho,
+                         const double *e, const double *rhoY, double *T, double *R, int iters,
+                         int32_t *cell_status, int32_t *cell_stats, void *stream);
+
+/*
  * Discrete adjoint (reverse-mode gradients of a loss of the final states).
  * The paper builds ChemGen for use in differentiable solvers (Section 1); the
  * derivative here is that of the integrators of Section 3.2 and Appendix A on

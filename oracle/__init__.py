@@ -289,6 +289,21 @@ class RefMech:
         dT0 = dy0[:, 0] + (dy0[:, 1:] * dC_dT).sum(axis=1)
         return dT0, dY0, g, st
 
+    def react_split(self, rho, e, rhoY, T_guess, opts: dict, iters: int = 5, nthreads: int = 1):
+        """Operator-split reaction step of a flow solver (Section 5.5): T from
+        (e, Y = rhoY / rho) by the Newton of Section 2.1, then C = rhoY / W
+        integrated at constant volume over dt; returns (T after dt,
+        R = W (C^{n+1} - C^n) / dt [N, ns], status, stats)."""
+        rho = _f64(rho)
+        rhoY = _f64(rhoY)
+        Y = rhoY / rho[:, None]
+        T = self.temperature(e, Y, T_guess, iters, CONV)
+        C = rhoY / self.mech.W
+        o = dict(opts, reactor=CONV)
+        y, status, stats = self.integrate_y(self._state(T, C), o, nthreads)
+        R = (self.mech.W * y[:, 1:] - rhoY) / default_opts(**o)["dt"]
+        return y[:, 0].copy(), R, status, stats
+
     def tangent(self, y0, dy0, opts: dict, pj: int = -1, pk: int = 0, nthreads: int = 1):
         """Forward sensitivity dy_end for the initial perturbation dy0 and
         the parameter (reaction pj, kind pk: 0 ln A, 1 b, 2 Ea)."""

@@ -55,7 +55,7 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
-            "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check")
+            "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split")
 
 
 def library_path() -> str:
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = False):
                                          P, P]
     lib.cg_mech_set_arrhenius.argtypes = [P, P]
     lib.cgx_exp_check.argtypes = [P, L, P, P, P, P]
+    lib.cg_react_split.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, I, P, P, P]
     lib.cg_last_error.restype = ctypes.c_char_p
     lib.cg_last_error.argtypes = []
     _lib = lib
@@ -265,6 +266,14 @@ def cg_mech_set_arrhenius(h, arr):
     a = np.ascontiguousarray(arr, dtype=np.float64).reshape(h.nr, 3)
     _check(load().cg_mech_set_arrhenius(h.ptr, a.ctypes.data))
     h.arr = a.copy()
+
+
+def cg_react_split(h, opts, rho, e, rhoY, T, R, iters=5, status=None, stats=None, stream=None):
+    """Operator-split reaction step: rho [N], e [N], rhoY [ns, N] in; T [N]
+    guess in, temperature after dt out; R [ns, N] out (CUDA tensors)."""
+    _check(load().cg_react_split(h.ptr, ctypes.byref(opts), rho.shape[0], _dev(rho), _dev(e), _dev(rhoY),
+                                 _dev(T), _dev(R), int(iters), None if status is None else _dev(status, "int32"),
+                                 None if stats is None else _dev(stats, "int32"), _stream(stream)))
 
 
 def cgx_exp_check(h, x, y_tab, y_lib, stream=None):

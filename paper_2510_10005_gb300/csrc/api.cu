@@ -913,6 +913,34 @@ cg_status cg_integrate_batch(int n_mech, const cg_mech* const* mechs, const int6
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch");
 }
 
+// Operator-split reaction step of a compressible flow solver.
+cg_status cg_react_split(const cg_mech* m, const cg_integrate_opts* o, int64_t N, const double* rho,
+                         const double* e, const double* rhoY, double* T, double* R, int iters,
+                         int32_t* cell_status, int32_t* cell_stats, void* stream) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    IntParams P;
+    cg_status st = make_params(o, P);
+    if (st != CG_OK) return st;
+    if (o->reactor != CG_CONV) return fail(CG_EINVAL, "the split reaction step is at constant volume (CG_CONV)");
+    if (N < 0 || iters < 0 || iters > 100) return fail(CG_EINVAL, "N >= 0 and 0 <= iters <= 100 required");
+    if (N == 0) return CG_OK;
+    if (!rho || !e || !rhoY || !T || !R) return fail(CG_EINVAL, "NULL array");
+    cg::SplitTask t;
+    t.M = m->dm;
+    t.L = task_layout(m, P);
+    t.N = N;
+    t.rho = rho;
+    t.e = e;
+    t.rhoY = rhoY;
+    t.T = T;
+    t.R = R;
+    t.status = cell_status;
+    t.stats = cell_stats;
+    t.iters = iters;
+    cudaError_t err = cg::launch_react_split(t, P, m->dm.team, m->tpb, (cudaStream_t)stream);
+    return err == cudaSuccess ? CG_OK : cuda_fail(err, "react_split launch");
+}
+
 // Forward integration that records the checkpoints of the adjoint.
 cg_status cg_integrate_ckpt(const cg_mech* m, const cg_integrate_opts* o, int64_t N, double* T, double* Y,
                             const double* p_or_rho, int32_t* cell_status, int32_t* cell_stats, double* ckpt,

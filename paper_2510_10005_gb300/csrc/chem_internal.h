@@ -46,6 +46,22 @@ struct AdjTask {
     int32_t* status;           // out
 };
 
+// One operator-split call of a flow solver (Section 5.5): conserved
+// variables in, temperature and the species source out.
+struct SplitTask {
+    DevMech M;
+    Layout L;
+    int64_t N;
+    const double* rho;    // density                    [N]
+    const double* e;      // mass-specific internal energy u [N]
+    const double* rhoY;   // species densities rho Y_i  [ns][N]
+    double* T;            // in: first guess, out: temperature after dt [N]
+    double* R;            // out: W_i (C_i^{n+1} - C_i^n) / dt   [ns][N]
+    int32_t* status;
+    int32_t* stats;
+    int iters;            // Newton iterations of the temperature recovery
+};
+
 constexpr int kMaxTasks = 4;
 
 struct Tasks {
@@ -72,6 +88,8 @@ cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, i
 cudaError_t launch_integrate_on(const Tasks& tasks, const IntParams& P, int team, int tpb, double* scratch,
                                 int64_t scratch_doubles, unsigned long long* counter, cudaStream_t st);
 int64_t integrate_slot_doubles(const Tasks& tasks);
+// Operator-split reaction step (persistent launch, `team` threads per cell).
+cudaError_t launch_react_split(const SplitTask& t, const IntParams& P, int team, int tpb, cudaStream_t st);
 // Backward sweep of the discrete adjoint over the cells of t (persistent
 // launch with `team` threads per cell), then, with dtheta != nullptr, the
 // fixed-order sum of the per-cell parameter gradients into dtheta[nr][3].

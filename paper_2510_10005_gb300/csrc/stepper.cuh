@@ -282,6 +282,73 @@ __device__ __forceinline__ void save_step(double* ck, int cap, int k, const doub
     if (lane == 0) e[n] = h;
 }
 
+// Fixed steps with deterministic halving: a failed step of level d is
+// replaced by two steps of level d+1 (recursively, at most max_halvings
+// deep), walked iteratively with a position counter.
+template <int TEAM, class MT>
+__device__ int integrate_fixed(const DevMech& M, const Ws& W, const IntParams& P, Counters& cnt, double* ck,
+                               int cap,
+                               int lane) {
+    const int D = P.max_halvings;
+    const double hsub = P.dt / P.nsub;
+    for (int s = 0; s < P.nsub; ++s) {
+        unsigned long long pos = 0ull;
+        const unsigned long long total = 1ull << D;
+        int d = 0;
+        while (pos < total) {
+            const double h = ldexp(hsub, -d);
+            if (step<TEAM, MT>(M, W, P, h, cnt, lane)) {
+                save_step<TEAM>(ck, cap, cnt.steps, W.yn, h, M.n, lane);
+                copy_vec<TEAM>(W.yn, W.y1, M.n, lane);
+                cnt.steps++;
+                pos += 1ull << (D - d);
+                while (d > 0 && ((pos >> (D - d)) & 1ull) == 0ull) --d;
+            } else {
+                cnt.rejects++;
+                if (d >= D) return CELL_NEWTON_FAIL;
+                ++d;
+            }
+        }
+    }
+    return CELL_OK;
+}
+
+// Error-controlled steps: accept when WRMS(err) <= 1; next step
+// h min(5, max(0.2, 0.9 err^(-1/(q+1)))); Newton failure: h / 4.
+template <int TEAM, class MT>
+__device__ int integrate_adaptive(const DevMech& M, const Ws& W, const IntParams& P, Counters& cnt, double* ck,
+                                  int cap,
+                                  int lane) {
+    const double expo = -1.0 / (P.err_order + 1.0);
+    double t = 0.0;
+    double h = P.h0 > 0.0 ? fmin(P.h0, P.dt) : P.dt;
+    int attempts = 0;
+    while (t < P.dt) {
+        if (attempts++ >= P.max_steps) return CELL_MAX_STEPS;
+        if (h < P.hmin) return CELL_STEP_TOO_SMALL;
+        const bool last = t + h >= P.dt;
+        const double hh = last ? P.dt - t : h;
+        if (!step<TEAM, MT>(M, W, P, hh, cnt, lane)) {
+            cnt.rejects++;
+            h = 0.25 * hh;
+            continue;
+        }
+        const double e = wrms<TEAM>(W.err, W.yn, W.y1, M.n, P.rtol, P.atol, W.red, lane);
+        double fac = e > 0.0 ? 0.9 * pow(e, expo) : 5.0;
+        fac = fmin(5.0, fmax(0.2, fac));
+        if (e <= 1.0) {
+            save_step<TEAM>(ck, cap, cnt.steps, W.yn, hh, M.n, lane);
+            copy_vec<TEAM>(W.yn, W.y1, M.n, lane);
+            t = last ? P.dt : t + hh;
+            cnt.steps++;
+        } else {
+            cnt.rejects++;
+        }
+        h = hh * fac;
+    }
+    return CELL_OK;
+}
+
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 

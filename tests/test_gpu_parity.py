@@ -466,3 +466,67 @@ def test_gmres_limits_and_arguments(mechs, ref, handles):
         with pytest.raises(chemgb.ChemgbError) as e:
             run_gpu(h, chemgb.make_opts(**merged(BE_OPTS, GM, bad)), T, Y, p)
         assert e.value.code == chemgb.CG_EINVAL
+
+
+# --- operator-split surface of a flow solver (Section 5.5) -------------------
+
+def _flow_state(m, r, T, Y, p):
+    rho = p / (inputs.R_UNIV * T * (Y / m.W).sum(axis=1))
+    u = np.array([Y[c] @ r.thermo(T[c])["u"] for c in range(len(T))])
+    return rho, u, rho[:, None] * Y
+
+
+def run_split(h, opts, rho, u, rhoY, Tguess, iters=5):
+    N = len(rho)
+    Tt = d(Tguess)
+    R = torch.empty((h.ns, N), dtype=torch.float64, device=DEV)
+    st = torch.empty(N, dtype=torch.int32, device=DEV)
+    chemgb.cg_react_split(h, opts, d(rho), d(u), d(rhoY.T), Tt, R, iters, st)
+    torch.cuda.synchronize()
+    return Tt.cpu().numpy(), R.cpu().numpy().T, st.cpu().numpy()
+
+
+def test_split_step_parity_backward_euler(mechs, ref, handles):
+    """(rho, u, rho Y) in, T and R out: one backward-Euler step of 1e-6 s
+    from a stale temperature guess; T to 1e-10, R to 1e-9 of the scale
+    rho Y / dt of the difference it is."""
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 500, (1000, 1500), (1, 3), (0.5, 2), "H2", seed=41)
+    rho, u, rhoY = _flow_state(m, r, T, Y, p)
+    o = dict(BE_OPTS, reactor=oracle.CONV, dt=1e-6)
+    To, Ro, so, _ = r.react_split(rho, u, rhoY, T * 1.05, o, nthreads=8)
+    Tg, Rg, sg = run_split(h, chemgb.make_opts(**o), rho, u, rhoY, T * 1.05)
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    np.testing.assert_allclose(Tg, To, rtol=1e-10)
+    scale = rhoY / o["dt"] + np.abs(Ro)
+    assert np.all(np.abs(Rg - Ro) <= 1e-9 * scale)
+    assert np.all(np.abs(Rg.sum(axis=1)) <= 1e-12 * np.abs(Rg).sum(axis=1) + 1e-13 * rhoY.sum(axis=1) / o["dt"])
+
+
+def test_split_step_parity_flame_cells(mechs, ref, handles):
+    m, r, h = mechs["ch4"], ref["ch4"], handles["ch4"]
+    T, Y, p = inputs.field_flames(m, 4096, seed=0)
+    idx = np.arange(3, 4096, 48)
+    rho, u, rhoY = _flow_state(m, r, T[idx], Y[idx], p[idx])
+    o = dict(ADAPT, reactor=oracle.CONV)
+    To, Ro, so, _ = r.react_split(rho, u, rhoY, T[idx], o, nthreads=8)
+    Tg, Rg, sg = run_split(h, chemgb.make_opts(**o), rho, u, rhoY, T[idx])
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    np.testing.assert_allclose(Tg, To, rtol=1e-6)
+    assert np.all(np.abs(Rg - Ro) <= 2e-6 * rho[:, None] / o["dt"])   # rtol on Y, over dt
+
+
+def test_split_step_edge_cases(mechs, ref, handles):
+    m, r, h = mechs["h2"], ref["h2"], handles["h2"]
+    T, Y, p = inputs.field_reactor(m, 3, (1200, 1200), (1, 1), (1, 1), "H2", seed=1)
+    rho, u, rhoY = _flow_state(m, r, T, Y, p)
+    u[1] = np.nan
+    o = dict(BE_OPTS, reactor=oracle.CONV, dt=1e-6)
+    Tg, Rg, sg = run_split(h, chemgb.make_opts(**o), rho, u, rhoY, T)
+    assert sg[1] == chemgb.CG_CELL_NONFINITE and Tg[1] == T[1] and not Rg[1].any()
+    assert sg[0] == 0 and sg[2] == 0
+    with pytest.raises(chemgb.ChemgbError) as e:
+        run_split(h, chemgb.make_opts(**BE_OPTS), rho, u, rhoY, T)     # constant pressure: refused
+    assert e.value.code == chemgb.CG_EINVAL

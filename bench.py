@@ -252,6 +252,19 @@ def workload_name(config: int, method: str | None, linear: str | None = None, pr
     return w
 
 
+def flow_state(m, T, Y, p):
+    """Conserved variables of a compressible flow solver for the split
+    surface (input construction): rho from the ideal gas, u = sum Y_i u_i(T)
+    from the NASA-7 polynomials, rho Y."""
+    R = 8314.46261815324
+    rho = p / (R * T * (Y / m.W).sum(axis=1))
+    a = m.nasa7
+    Tc = T[:, None]
+    h_RT = a[:, 0] + Tc * (a[:, 1] / 2 + Tc * (a[:, 2] / 3 + Tc * (a[:, 3] / 4 + Tc * a[:, 4] / 5))) + a[:, 5] / Tc
+    u = (Y * (R / m.W) * Tc * (h_RT - 1.0)).sum(axis=1)
+    return rho, u, rho[:, None] * Y
+
+
 def oracle_opts(o: dict) -> dict:
     return {k: v for k, v in o.items() if k not in ("precision", "persistent")}
 
@@ -323,6 +336,11 @@ def run_gpu(args):
     precision = cfg["precision"] if args.precision is None else args.precision
     parts = make_workload(args.config, args.cells or cfg["cells"], seed=rank)
     opts_d = opts_dict(args.config, precision, args.method, args.linear, args.prec)
+    split = args.surface == "split"
+    if split:
+        if len(parts) != 1:
+            raise SystemExit("--surface split takes one mechanism")
+        opts_d["reactor"] = 0   # the split step is at constant volume
     opts = chemgb.make_opts(**opts_d)
     stream = torch.cuda.Stream(dev)   # a side stream (graph capture needs one); all work goes there
     torch.cuda.set_stream(stream)
@@ -339,6 +357,12 @@ def run_gpu(args):
                  st=torch.empty(N, dtype=torch.int32, device=dev),
                  stats=torch.empty((4, N), dtype=torch.int32, device=dev))
         b["T"], b["Y"] = torch.empty_like(b["T0"]), torch.empty_like(b["Y0"])
+        if split:
+            rho, u, rhoY = flow_state(m, T, Y, p)
+            b.update(RHO=torch.tensor(rho, dtype=torch.float64, device=dev),
+                     E=torch.tensor(u, dtype=torch.float64, device=dev),
+                     RHOY=torch.tensor(np.ascontiguousarray(rhoY.T), dtype=torch.float64, device=dev),
+                     R=torch.empty_like(b["Y0"]))
         handles.append(h)
         bufs.append(b)
     N_total = sum(len(b["T0"]) for b in bufs)
@@ -359,8 +383,13 @@ def run_gpu(args):
     def integrate():
         for b in bufs:
             b["T"].copy_(b["T0"])
-            b["Y"].copy_(b["Y0"])
-        if len(handles) == 1:
+            if not split:
+                b["Y"].copy_(b["Y0"])
+        if split:   # conserved variables in; T (guess: the flow solver's last one) and R out
+            b = bufs[0]
+            chemgb.cg_react_split(handles[0], opts, b["RHO"], b["E"], b["RHOY"], b["T"], b["R"], 5, b["st"],
+                                  b["stats"], stream=stream.cuda_stream)
+        elif len(handles) == 1:
             b = bufs[0]
             chemgb.cg_integrate(handles[0], opts, b["T"], b["Y"], b["P"], b["st"], b["stats"],
                                 stream=stream.cuda_stream)
@@ -422,7 +451,7 @@ def run_gpu(args):
 
     # end to end through the host entry point (copies inside the timed region)
     e2e = None
-    if len(handles) == 1 and args.e2e_steps > 0:
+    if len(handles) == 1 and args.e2e_steps > 0 and not split:
         m, T, Y, p = parts[0]
         N = len(T)
         Th0, Yh0, ph = np.ascontiguousarray(T), np.ascontiguousarray(Y.T), np.ascontiguousarray(p)
@@ -468,7 +497,9 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.config, args.method, args.linear, args.prec),
+        "config": {"workload": workload_name(args.config, args.method, args.linear, args.prec)
+                   + ("; operator-split surface: (rho, u, rho Y) in, T recovered (5 Newton iterations), "
+                      "constant volume, T and R out" if split else ""),
                    "config": args.config,
                    "cells_per_gpu": N_total,
                    "newton_matrix": "fp32" if precision == 1 else "fp64", "state_bytes": state_bytes,
@@ -752,6 +783,9 @@ def main():
                     help="replace the workload's integrator (configs 1, 2, 3, 5)")
     ap.add_argument("--linear", choices=sorted(LINEAR), default=None, help="Newton systems: dense LU or GMRES")
     ap.add_argument("--prec", choices=sorted(PRECS), default=None, help="GMRES preconditioner (default gs)")
+    ap.add_argument("--surface", choices=["integrate", "split"], default="integrate",
+                    help="split: the operator-split call of a compressible solver (rho, u, rho Y in; T, R out), "
+                         "constant volume")
     args = ap.parse_args()
     if args.config == 4:
         (run_reference_adjoint if args.impl == "reference" else run_adjoint)(args)

@@ -50,7 +50,7 @@ def _load():
         lib = ctypes.CDLL(build())
         P = ctypes.c_void_p
         lib.cgref_mech_create.restype = P
-        lib.cgref_mech_create.argtypes = [ctypes.c_int, ctypes.c_int] + [P] * 14
+        lib.cgref_mech_create.argtypes = [ctypes.c_int, ctypes.c_int] + [P] * 17
         lib.cgref_mech_destroy.argtypes = [P]
         lib.cgref_thermo.argtypes = [P, ctypes.c_double] + [P] * 6
         lib.cgref_rates.argtypes = [P, ctypes.c_double, P, P, P, P]
@@ -127,7 +127,9 @@ class RefMech:
                       _i32(mech.rf_idx), _i32(mech.rf_nu), _i32(mech.rr_idx), _i32(mech.rr_nu),
                       _f64(mech.arr), _f64(mech.arr0), _f64(mech.troe), _i32(mech.eff_ptr),
                       _i32(mech.eff_idx) if len(mech.eff_idx) else np.zeros(1, np.int32),
-                      _f64(mech.eff_val) if len(mech.eff_val) else np.zeros(1)]
+                      _f64(mech.eff_val) if len(mech.eff_val) else np.zeros(1),
+                      _f64(mech.sri), _i32(mech.plog_ptr),
+                      _f64(mech.plog) if len(mech.plog) else np.zeros(4)]
         self.h = lib.cgref_mech_create(mech.ns, mech.nr, *[_p(a) for a in self._keep])
         self.ns, self.nr = mech.ns, mech.nr
         self.n = mech.ns + 1

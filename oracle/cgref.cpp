@@ -35,7 +35,7 @@ const double R_U = 8314.46261815324;   // universal gas constant, J/(kmol K)
 const double P_REF = 101325.0;         // reference pressure, 1 atm (Section 2.1)
 const double LN10 = 2.302585092994045684;
 
-enum { ELEMENTARY = 0, THREE_BODY = 1, LINDEMANN = 2, TROE = 3 };
+enum { ELEMENTARY = 0, THREE_BODY = 1, LINDEMANN = 2, TROE = 3, SRI = 4, PLOG = 5 };
 enum { CONV = 0, CONP = 1, CONP_LITERAL = 2 };
 enum { ST_OK = 0, ST_NEWTON_FAIL = 1, ST_STEP_TOO_SMALL = 2, ST_MAX_STEPS = 3, ST_NONFINITE = 4 };
 
@@ -52,6 +52,10 @@ struct Reaction {
     bool has_T2 = false;
     std::vector<int> eff_sp;    // third-body efficiencies different from 1
     std::vector<double> eff_val;
+    double sri[5] = {0, 0, 0, 0, 0};   // SRI a, b, c, d, e (Section 2.2.3)
+    // PLOG rate expressions (Section 2.2.4), sorted by pressure; equal
+    // pressures repeat (their rates add)
+    std::vector<double> pl_lnp, pl_lnA, pl_b, pl_Ea;
     int sum_nu = 0;             // sum_i nu_ij = sum nu^r - sum nu^f
 };
 
@@ -103,9 +107,52 @@ double dcp_i(const Mech& m, int i, double T) {
 
 template <class S> S clamp_pr(const S& Pr) { return re(Pr) < 1e-300 ? S(1e-300) : Pr; }
 
+// PLOG (Section 2.2.4, eq. plog_rate): the sum of the rate expressions
+// given at one pressure level, from index i0; i1 receives the next level.
+template <class S> S plog_level(const Reaction& r, int i0, int& i1, const S& T, const S& lnT) {
+    S k = 0.0;
+    int i = i0;
+    for (; i < (int)r.pl_lnp.size() && r.pl_lnp[i] == r.pl_lnp[i0]; ++i)
+        k += exp(r.pl_lnA[i] + r.pl_b[i] * lnT - r.pl_Ea[i] / (R_U * T));
+    i1 = i;
+    return k;
+}
+
+// k at the state's own pressure p = R T sum C: ln k interpolated linearly in
+// ln p between the bracketing levels; the nearest level outside the range.
+template <class S> S plog_rate(const Reaction& r, const S& T, const S& lnT, const S& Mc) {
+    const S lnp = log(R_U * T * Mc);
+    const int n = (int)r.pl_lnp.size();
+    int i0 = 0, i1 = 0;
+    S k0 = plog_level(r, 0, i1, T, lnT);
+    if (re(lnp) <= r.pl_lnp[0]) return k0;
+    while (i1 < n) {   // level [i0, i1) and the next one
+        int i2 = 0;
+        S k1 = plog_level(r, i1, i2, T, lnT);
+        if (re(lnp) <= r.pl_lnp[i1]) {
+            S w = (lnp - r.pl_lnp[i0]) / (r.pl_lnp[i1] - r.pl_lnp[i0]);
+            return exp(log(k0) + (log(k1) - log(k0)) * w);
+        }
+        i0 = i1;
+        i1 = i2;
+        k0 = k1;
+    }
+    return k0;   // above the highest pressure
+}
+
+// SRI broadening (Section 2.2.3): F = d [a exp(-b/T) + exp(-T/c)]^X T^e,
+// X = 1 / (1 + log10^2 Pr).
+template <class S> S sri_F(const Reaction& r, const S& T, const S& Pr) {
+    S P = log(clamp_pr(Pr)) / LN10;
+    S X = 1.0 / (1.0 + P * P);
+    S G = r.sri[0] * exp(-r.sri[1] / T) + exp(-T / r.sri[2]);
+    return r.sri[3] * exp(X * log(G)) * exp(r.sri[4] * log(T));
+}
+
 // forward rate constant k_f and the effective third-body concentration
 template <class S>
 S forward_rate(const Reaction& r, const S& T, const S& lnT, const S* C, const S& Mc) {
+    if (r.type == PLOG) return plog_rate(r, T, lnT, Mc);
     // k_A = A exp(b ln T - E/(R T))  (Section 2.2.1)
     S kA = exp(r.lnA + r.b * lnT - r.Ea / (R_U * T));
     if (r.type == ELEMENTARY) return kA;
@@ -129,6 +176,8 @@ S forward_rate(const Reaction& r, const S& T, const S& lnT, const S* C, const S&
         S f1 = (P + c) / (n - 0.14 * (P + c));
         S logF = logFc / (1.0 + f1 * f1);
         F = exp(LN10 * logF);
+    } else if (r.type == SRI) {
+        F = sri_F(r, T, Pr);
     }
     return kA * (Pr / (1.0 + Pr)) * F;
 }
@@ -258,7 +307,47 @@ void jacobian(const Mech& m, int reactor, const double* y, double* J) {
             alpha[r.eff_sp[e]] = r.eff_val[e];
         }
         double kf, dkf_dT, dkf_dM;
-        if (r.type == ELEMENTARY) {
+        if (r.type == PLOG) {
+            // ln k = (1 - w) ln k_l + w ln k_{l+1}, w = (ln p - ln p_l)/(ln p_{l+1} - ln p_l),
+            // ln p = ln(R T M_c): d ln k/dT = (1-w) dln k_l/dT + w dln k_{l+1}/dT + s/T,
+            // d ln k/d M_c = s/M_c with s = (ln k_{l+1} - ln k_l)/(ln p_{l+1} - ln p_l)
+            auto level = [&](int i0, int& i1, double& dlnk) {
+                double k = 0.0, dk = 0.0;
+                int i = i0;
+                for (; i < (int)r.pl_lnp.size() && r.pl_lnp[i] == r.pl_lnp[i0]; ++i) {
+                    double ki = std::exp(r.pl_lnA[i] + r.pl_b[i] * lnT - r.pl_Ea[i] / RT);
+                    k += ki;
+                    dk += ki * (r.pl_b[i] / T + r.pl_Ea[i] / (R_U * T * T));
+                }
+                i1 = i;
+                dlnk = dk / k;
+                return k;
+            };
+            const double lnp = std::log(RT * Mc);
+            const int np = (int)r.pl_lnp.size();
+            int i0 = 0, i1 = 0;
+            double d0 = 0.0;
+            double k0 = level(0, i1, d0);
+            kf = k0; dkf_dT = k0 * d0; dkf_dM = 0.0;
+            if (lnp > r.pl_lnp[0]) {
+                while (i1 < np) {
+                    int i2 = 0;
+                    double d1 = 0.0;
+                    double k1 = level(i1, i2, d1);
+                    if (lnp <= r.pl_lnp[i1]) {
+                        const double dl = r.pl_lnp[i1] - r.pl_lnp[i0];
+                        const double w = (lnp - r.pl_lnp[i0]) / dl;
+                        const double sl = (std::log(k1) - std::log(k0)) / dl;
+                        kf = std::exp(std::log(k0) + (std::log(k1) - std::log(k0)) * w);
+                        dkf_dT = kf * ((1.0 - w) * d0 + w * d1 + sl / T);
+                        dkf_dM = kf * sl / Mc;
+                        break;
+                    }
+                    i0 = i1; i1 = i2; k0 = k1; d0 = d1;
+                    kf = k0; dkf_dT = k0 * d0; dkf_dM = 0.0;   // above the range: the last level
+                }
+            }
+        } else if (r.type == ELEMENTARY) {
             kf = kA; dkf_dT = dkA; dkf_dM = 0.0;
         } else if (r.type == THREE_BODY) {
             kf = M * kA; dkf_dT = M * dkA; dkf_dM = kA;
@@ -293,6 +382,18 @@ void jacobian(const Mech& m, int reactor, const double* y, double* J) {
                 dlogF_dP = clamped ? 0.0 : -L * 2.0 * f1 / (g1 * g1) * df1_dx;
                 double dlogF_dL = 1.0 / g1 - L * 2.0 * f1 / (g1 * g1) * df1_dL;
                 dlogF_dT = dlogF_dL * dL_dT;   // at fixed Pr
+            } else if (r.type == SRI) {
+                // log10 F = log10 d + X log10 G + e log10 T, X = 1/(1 + P^2)
+                bool clamped = Pr < 1e-300;
+                double P = std::log10(clamped ? 1e-300 : Pr);
+                double X = 1.0 / (1.0 + P * P);
+                double ea = std::exp(-r.sri[1] / T), ec = std::exp(-T / r.sri[2]);
+                double G = r.sri[0] * ea + ec;
+                double dG = r.sri[0] * r.sri[1] / (T * T) * ea - ec / r.sri[2];
+                double logG = std::log10(G);
+                F = r.sri[3] * std::pow(G, X) * std::pow(T, r.sri[4]);
+                dlogF_dP = clamped ? 0.0 : logG * (-2.0 * P * X * X);
+                dlogF_dT = X * dG / (G * LN10) + r.sri[4] / (T * LN10);
             }
             double fr = Pr / (1.0 + Pr);
             kf = kA * fr * F;
@@ -572,6 +673,7 @@ double dq_dlnk(const Mech& m, int j, double T, const double* C) {
     progress_rates(m, T, C, (double*)nullptr, (double*)nullptr, q.data());
     const Reaction& r = m.rx[j];
     if (r.type == ELEMENTARY || r.type == THREE_BODY) return q[j];
+    if (r.type == PLOG) return 0.0;   // its own rate table, not (ln A, b, Ea), sets k
     double M = 0.0;
     for (int i = 0; i < m.ns; ++i) M += C[i];
     for (size_t e = 0; e < r.eff_sp.size(); ++e) M += (r.eff_val[e] - 1.0) * C[r.eff_sp[e]];
@@ -588,6 +690,11 @@ double dq_dlnk(const Mech& m, int j, double T, const double* C) {
         const double x = std::log10(Pr) + c, den = nn - 0.14 * x;
         const double f1 = x / den;
         dlogF_dP = -L * 2.0 * f1 / ((1.0 + f1 * f1) * (1.0 + f1 * f1)) * nn / (den * den);
+    }
+    if (r.type == SRI && Pr >= 1e-300) {
+        const double P = std::log10(Pr), X = 1.0 / (1.0 + P * P);
+        const double G = r.sri[0] * std::exp(-r.sri[1] / T) + std::exp(-T / r.sri[2]);
+        dlogF_dP = std::log10(G) * (-2.0 * P * X * X);
     }
     return q[j] * (Pr / (1.0 + Pr) - dlogF_dP);
 }
@@ -1046,7 +1153,8 @@ void* cgref_mech_create(int ns, int nr, const double* W, const double* nasa7,
                         const int* rtype, const int* reversible,
                         const int* rf_idx, const int* rf_nu, const int* rr_idx, const int* rr_nu,
                         const double* arr, const double* arr0, const double* troe,
-                        const int* eff_ptr, const int* eff_idx, const double* eff_val) {
+                        const int* eff_ptr, const int* eff_idx, const double* eff_val,
+                        const double* sri, const int* plog_ptr, const double* plog) {
     Mech* m = new Mech();
     m->ns = ns;
     m->nr = nr;
@@ -1095,6 +1203,13 @@ void* cgref_mech_create(int ns, int nr, const double* W, const double* nasa7,
         for (int e = eff_ptr[j]; e < eff_ptr[j + 1]; ++e) {
             r.eff_sp.push_back(eff_idx[e]);
             r.eff_val.push_back(eff_val[e]);
+        }
+        for (int k = 0; k < 5; ++k) r.sri[k] = sri[5 * j + k];
+        for (int e = plog_ptr[j]; e < plog_ptr[j + 1]; ++e) {
+            r.pl_lnp.push_back(std::log(plog[4 * e]));
+            r.pl_lnA.push_back(plog[4 * e + 1]);
+            r.pl_b.push_back(plog[4 * e + 2]);
+            r.pl_Ea.push_back(plog[4 * e + 3]);
         }
     }
     return m;

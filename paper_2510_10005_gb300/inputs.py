@@ -17,13 +17,17 @@ Mechanism arrays (all numpy):
   names[ns], elements[ne], comp[ns, ne] (int atom counts), W[ns] kg/kmol,
   nasa7[ns, 7]  (a1..a5: cp/R polynomial; a6: h/R constant; a7: s/R constant,
                  one range used over the whole temperature domain),
-  rtype[nr]     (0 elementary, 1 third-body, 2 Lindemann, 3 Troe),
+  rtype[nr]     (0 elementary, 1 third-body, 2 Lindemann, 3 Troe, 4 SRI falloff,
+                 5 pressure-dependent Arrhenius "PLOG"),
   reversible[nr],
   rf_idx[nr,3], rf_nu[nr,3], rr_idx[nr,3], rr_nu[nr,3]  (-1 / 0 padded),
   arr[nr,3]     (ln A, b, Ea)      high-pressure / plain Arrhenius triple,
   arr0[nr,3]    (ln A0, b0, Ea0)   low-pressure triple of falloff reactions,
   troe[nr,4]    (alpha, T3, T1, T2); T2 = NaN means the term is absent,
-  eff_ptr[nr+1], eff_idx[...], eff_val[...]  CSR of efficiencies != 1.
+  eff_ptr[nr+1], eff_idx[...], eff_val[...]  CSR of efficiencies != 1,
+  sri[nr,5]     (a, b, c, d, e) of SRI falloff reactions (zeros otherwise),
+  plog_ptr[nr+1], plog[K,4]  CSR of PLOG rate expressions (p in Pa, ln A, b,
+                 Ea), sorted by pressure; equal pressures may repeat.
 """
 from __future__ import annotations
 
@@ -37,7 +41,7 @@ R_UNIV = 8314.46261815324      # J/(kmol K)
 P_ATM = 101325.0               # Pa
 CAL = 4.184e6                  # J/kmol per kcal/mol
 
-RXN_ELEMENTARY, RXN_THREE_BODY, RXN_LINDEMANN, RXN_TROE = 0, 1, 2, 3
+RXN_ELEMENTARY, RXN_THREE_BODY, RXN_LINDEMANN, RXN_TROE, RXN_SRI, RXN_PLOG = 0, 1, 2, 3, 4, 5
 
 _ATOMIC_MASS = {"C": 12.011, "H": 1.008, "O": 15.999, "N": 14.007, "Ar": 39.95}
 _VALENCE = {"C": 4, "H": 1, "O": 2, "N": 3, "Ar": 0}
@@ -63,6 +67,18 @@ class Mechanism:
     eff_ptr: np.ndarray
     eff_idx: np.ndarray
     eff_val: np.ndarray
+    sri: np.ndarray = None
+    plog_ptr: np.ndarray = None
+    plog: np.ndarray = None
+
+    def __post_init__(self):
+        nr = int(self.rtype.shape[0])
+        if self.sri is None:
+            self.sri = np.zeros((nr, 5))
+        if self.plog_ptr is None:
+            self.plog_ptr = np.zeros(nr + 1, dtype=np.int32)
+        if self.plog is None:
+            self.plog = np.zeros((0, 4))
 
     @property
     def ns(self) -> int:
@@ -90,6 +106,8 @@ class Mechanism:
             assert a.shape == (nr, 3)
         assert self.arr.shape == (nr, 3) and self.arr0.shape == (nr, 3)
         assert self.troe.shape == (nr, 4) and self.eff_ptr.shape == (nr + 1,)
+        assert self.sri.shape == (nr, 5) and self.plog_ptr.shape == (nr + 1,)
+        assert self.plog_ptr[0] == 0 and self.plog_ptr[-1] == len(self.plog) and np.all(np.diff(self.plog_ptr) >= 0)
         for idx, nu in ((self.rf_idx, self.rf_nu), (self.rr_idx, self.rr_nu)):
             assert np.all((idx >= -1) & (idx < ns))
             assert np.all((idx >= 0) == (nu > 0))
@@ -104,10 +122,13 @@ class Mechanism:
                 if self.rr_idx[j, s] >= 0:
                     bal += self.rr_nu[j, s] * self.comp[self.rr_idx[j, s]]
             assert not bal.any(), f"reaction {j} is not element balanced"
-            if self.rtype[j] != RXN_ELEMENTARY:
-                assert self.eff_ptr[j + 1] - self.eff_ptr[j] >= 0
-            else:
+            if self.rtype[j] in (RXN_ELEMENTARY, RXN_PLOG):
                 assert self.eff_ptr[j + 1] == self.eff_ptr[j]
+            if self.rtype[j] == RXN_PLOG:
+                pts = self.plog[self.plog_ptr[j]:self.plog_ptr[j + 1]]
+                assert len(pts) >= 1 and np.all(np.diff(pts[:, 0]) >= 0) and np.all(pts[:, 0] > 0)
+            else:
+                assert self.plog_ptr[j + 1] == self.plog_ptr[j]
 
     def equation(self, j: int) -> str:
         def side(idx, nu):
@@ -116,7 +137,7 @@ class Mechanism:
                 if idx[j, s] >= 0:
                     t.append((f"{nu[j, s]} " if nu[j, s] > 1 else "") + self.names[idx[j, s]])
             return " + ".join(t)
-        tb = {1: " + M", 2: " (+M)", 3: " (+M)"}.get(int(self.rtype[j]), "")
+        tb = {1: " + M", 2: " (+M)", 3: " (+M)", 4: " (+M)"}.get(int(self.rtype[j]), "")
         arrow = " <=> " if self.reversible[j] else " => "
         return side(self.rf_idx, self.rf_nu) + tb + arrow + side(self.rr_idx, self.rr_nu) + tb
 
@@ -128,7 +149,7 @@ class Mechanism:
     @staticmethod
     def load(path: str) -> "Mechanism":
         z = np.load(path, allow_pickle=False)
-        kw = {f.name: z[f.name] for f in dataclasses.fields(Mechanism)}
+        kw = {f.name: z[f.name] for f in dataclasses.fields(Mechanism) if f.name in z}
         kw["names"] = [str(s) for s in kw["names"]]
         kw["elements"] = [str(s) for s in kw["elements"]]
         return Mechanism(**kw)
@@ -404,6 +425,46 @@ def gen_mechanism(kind: str = "h2", seed: int | None = None) -> Mechanism:
                      eff_val=np.array(eff_val, dtype=np.float64))
     mech.validate()
     return mech
+
+
+def with_sri_plog(mech: Mechanism, n_sri: int, n_plog: int, seed: int = 0) -> Mechanism:
+    """A copy of `mech` in which n_sri Troe reactions take SRI broadening
+    (Section 2.2.3: a in U[0.5, 2], b in U[100, 1000] K, c in U[500, 5000] K,
+    d in U[0.8, 1.2], e in U[-0.5, 0.5]) and n_plog elementary reactions
+    become pressure-dependent Arrhenius (PLOG, Section 2.2.4) with 3-6
+    pressures log-spaced over 0.1-100 atm, each rate the original one
+    perturbed (ln A + N(0, 0.5), b + N(0, 0.1), Ea + N(0, 1 kcal/mol)); every
+    other PLOG reaction repeats one pressure with a second, smaller rate
+    (the rule that rates given at one pressure add)."""
+    rng = np.random.default_rng(seed)
+    m = mech.copy()
+    nr = m.nr
+    troe = [j for j in range(nr) if m.rtype[j] == RXN_TROE]
+    elem = [j for j in range(nr) if m.rtype[j] == RXN_ELEMENTARY]
+    for j in rng.choice(troe, size=min(n_sri, len(troe)), replace=False):
+        m.rtype[j] = RXN_SRI
+        m.sri[j] = (rng.uniform(0.5, 2.0), rng.uniform(100.0, 1000.0), rng.uniform(500.0, 5000.0),
+                    rng.uniform(0.8, 1.2), rng.uniform(-0.5, 0.5))
+        m.troe[j] = 0.0
+    chosen = set(int(j) for j in rng.choice(elem, size=min(n_plog, len(elem)), replace=False))
+    ptr, rows, count = [0], [], 0
+    for j in range(nr):
+        if j in chosen:
+            count += 1
+            m.rtype[j] = RXN_PLOG
+            k = int(rng.integers(3, 7))
+            ps = np.exp(np.linspace(math.log(0.1), math.log(100.0), k)) * P_ATM
+            pts = [(p, m.arr[j, 0] + rng.normal(0.0, 0.5), m.arr[j, 1] + rng.normal(0.0, 0.1),
+                    max(0.0, m.arr[j, 2] + rng.normal(0.0, 1.0) * CAL)) for p in ps]
+            if count % 2 == 1:
+                i = int(rng.integers(0, k))
+                pts.insert(i + 1, (ps[i], pts[i][1] - 2.0, pts[i][2] + 0.3, pts[i][3] + 2.0 * CAL))
+            rows.extend(pts)
+        ptr.append(len(rows))
+    m.plog_ptr = np.array(ptr, dtype=np.int32)
+    m.plog = np.array(rows, dtype=np.float64).reshape(-1, 4)
+    m.validate()
+    return m
 
 
 # ----------------------------------------------------------------------------

@@ -60,8 +60,12 @@ enum {
                                      checkpoints (failed cell or too few slots) */
 };
 
-/* reaction types (Section 2.2) */
-enum { CG_RXN_ELEMENTARY = 0, CG_RXN_THREE_BODY = 1, CG_RXN_LINDEMANN = 2, CG_RXN_TROE = 3 };
+/* reaction types (Section 2.2): elementary, third-body, falloff with
+ * Lindemann, Troe or SRI broadening (Section 2.2.3), pressure-dependent
+ * Arrhenius "PLOG" (Section 2.2.4; the pressure is the cell's own
+ * R T sum C) */
+enum { CG_RXN_ELEMENTARY = 0, CG_RXN_THREE_BODY = 1, CG_RXN_LINDEMANN = 2, CG_RXN_TROE = 3,
+       CG_RXN_SRI = 4, CG_RXN_PLOG = 5 };
 
 /* reactor forms: constant volume (Section 3, eq. temperature_source);
  * constant pressure with the dilution of the cell's volume (the reading of
@@ -107,7 +111,16 @@ enum { CG_PC_NONE = 0, CG_PC_JACOBI = 1, CG_PC_GAUSS_SEIDEL = 2 };
  *   arr0[nr*3]      ln A0, b0, Ea0 of the low-pressure limit (falloff only)
  *   troe[nr*4]      alpha, T3, T1, T2 of eq. f_and_fcent; T2 = NaN: absent
  *   eff_ptr[nr+1], eff_idx[], eff_val[]  CSR of third-body efficiencies
- *                   that differ from 1 (eq. TB_optimization)
+ *                   that differ from 1 (eq. TB_optimization); none for
+ *                   elementary and PLOG reactions
+ *   sri[nr*5]       a, b (K), c (K), d, e of SRI falloff (a >= 0, c > 0,
+ *                   d > 0); may be NULL when no reaction is CG_RXN_SRI
+ *   plog_ptr[nr+1], plog[K*4]  CSR of the PLOG rate expressions of each
+ *                   reaction: p (Pa), ln A, b, Ea, in non-decreasing p;
+ *                   expressions at the same p add (eq. plog_rate); only
+ *                   CG_RXN_PLOG reactions have entries (at least one); may
+ *                   be NULL when no reaction is CG_RXN_PLOG. arr is unused
+ *                   for PLOG reactions.
  */
 typedef struct {
     int n_species, n_reactions;
@@ -117,6 +130,9 @@ typedef struct {
     const double *arr, *arr0, *troe;
     const int *eff_ptr, *eff_idx;
     const double *eff_val;
+    const double *sri;
+    const int *plog_ptr;
+    const double *plog;
 } cg_mech_desc;
 
 /* Validate the description (index ranges, coefficients, sizes), build the

@@ -38,7 +38,7 @@ class cg_mech_desc(ctypes.Structure):
     _fields_ = [("n_species", ctypes.c_int), ("n_reactions", ctypes.c_int)] + [
         (name, ctypes.c_void_p) for name in (
             "W", "nasa7", "rxn_type", "reversible", "rf_idx", "rf_nu", "rr_idx", "rr_nu",
-            "arr", "arr0", "troe", "eff_ptr", "eff_idx", "eff_val")]
+            "arr", "arr0", "troe", "eff_ptr", "eff_idx", "eff_val", "sri", "plog_ptr", "plog")]
 
 
 class cg_integrate_opts(ctypes.Structure):
@@ -293,10 +293,12 @@ class MechHandle:
             rf_idx=i32(mech.rf_idx), rf_nu=i32(mech.rf_nu), rr_idx=i32(mech.rr_idx), rr_nu=i32(mech.rr_nu),
             arr=f64(mech.arr), arr0=f64(mech.arr0), troe=f64(mech.troe), eff_ptr=i32(mech.eff_ptr),
             eff_idx=i32(mech.eff_idx) if len(mech.eff_idx) else np.zeros(1, np.int32),
-            eff_val=f64(mech.eff_val) if len(mech.eff_val) else np.zeros(1))
+            eff_val=f64(mech.eff_val) if len(mech.eff_val) else np.zeros(1),
+            sri=f64(mech.sri), plog_ptr=i32(mech.plog_ptr),
+            plog=f64(mech.plog) if len(mech.plog) else np.zeros(4))
         d = cg_mech_desc(mech.ns, mech.nr, *[self._keep[k].ctypes.data for k in (
             "W", "nasa7", "rxn_type", "reversible", "rf_idx", "rf_nu", "rr_idx", "rr_nu", "arr", "arr0",
-            "troe", "eff_ptr", "eff_idx", "eff_val")])
+            "troe", "eff_ptr", "eff_idx", "eff_val", "sri", "plog_ptr", "plog")])
         h = ctypes.c_void_p()
         _check(lib.cg_mech_create(ctypes.byref(d), ctypes.byref(h)))
         self.ptr = h.value

@@ -385,8 +385,8 @@ template <class T> cg_status upload_sched(cg_mech* m, const std::vector<T>& h, c
 }
 
 // Reaction chunks of the rates loop for teams of `team` threads: runs of at
-// most 32 consecutive reactions (internal order, sorted by type) that all
-// have or all lack the falloff branch, so that no warp runs both branches;
+// most 32 consecutive reactions (internal order, sorted by type) of one kind
+// (plain, falloff, PLOG), so that no warp runs two branches;
 // chunks are dealt to the team's warps by estimated cost (a falloff chunk
 // about three plain ones), longest first onto the least-loaded warp.
 void make_rate_chunks(const std::vector<int>& itype, int team, std::vector<int>& ptr, std::vector<int>& first,
@@ -394,11 +394,13 @@ void make_rate_chunks(const std::vector<int>& itype, int team, std::vector<int>&
     const int nw = team / 32, nr = (int)itype.size();
     struct Chunk { int first, len; double cost; };
     std::vector<Chunk> all;
+    // kind 0: elementary and third-body, 1: falloff (Lindemann, Troe, SRI), 2: PLOG
+    auto kind = [](int t) { return t == CG_RXN_PLOG ? 2 : (t >= CG_RXN_LINDEMANN ? 1 : 0); };
     for (int j = 0; j < nr;) {
-        const bool fall = itype[j] == CG_RXN_LINDEMANN || itype[j] == CG_RXN_TROE;
+        const int kd = kind(itype[j]);
         int k = j;
-        while (k < nr && k - j < 32 && (itype[k] == CG_RXN_LINDEMANN || itype[k] == CG_RXN_TROE) == fall) ++k;
-        all.push_back({j, k - j, fall ? 3.0 : 1.0});
+        while (k < nr && k - j < 32 && kind(itype[k]) == kd) ++k;
+        all.push_back({j, k - j, kd == 0 ? 1.0 : 3.0});
         j = k;
     }
     std::vector<Chunk> order = all;
@@ -488,9 +490,13 @@ cg_status validate(const cg_mech_desc* d) {
         !d->arr || !d->arr0 || !d->troe || !d->eff_ptr)
         return fail(CG_EINVAL, "reaction arrays are required when n_reactions > 0");
     if (d->eff_ptr[0] != 0) return fail(CG_EINVAL, "eff_ptr[0] must be 0");
+    if (d->plog_ptr && d->plog_ptr[0] != 0) return fail(CG_EINVAL, "plog_ptr[0] must be 0");
+    if (d->plog_ptr)
+        for (int j = 0; j < nr; ++j)
+            if (d->plog_ptr[j + 1] < d->plog_ptr[j]) return fail(CG_EINVAL, "plog_ptr must be non-decreasing");
     for (int j = 0; j < nr; ++j) {
         const int t = d->rxn_type[j];
-        if (t < CG_RXN_ELEMENTARY || t > CG_RXN_TROE) return fail(CG_EINVAL, "reaction %d: bad type %d", j, t);
+        if (t < CG_RXN_ELEMENTARY || t > CG_RXN_PLOG) return fail(CG_EINVAL, "reaction %d: bad type %d", j, t);
         int nf = 0, nb = 0;
         for (int s = 0; s < 3; ++s) {
             const int a = d->rf_idx[3 * j + s], b = d->rr_idx[3 * j + s];
@@ -509,9 +515,31 @@ cg_status validate(const cg_mech_desc* d) {
         if (nf == 0 || nb == 0) return fail(CG_EINVAL, "reaction %d: needs reactants and products", j);
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(d->arr[3 * j + k])) return fail(CG_EINVAL, "reaction %d: arr not finite", j);
-        if (t == CG_RXN_LINDEMANN || t == CG_RXN_TROE)
+        if (t == CG_RXN_LINDEMANN || t == CG_RXN_TROE || t == CG_RXN_SRI)
             for (int k = 0; k < 3; ++k)
                 if (!std::isfinite(d->arr0[3 * j + k])) return fail(CG_EINVAL, "reaction %d: arr0 not finite", j);
+        if (t == CG_RXN_SRI) {
+            if (!d->sri) return fail(CG_EINVAL, "reaction %d is SRI but sri is NULL", j);
+            const double* q = d->sri + 5 * j;
+            for (int k = 0; k < 5; ++k)
+                if (!std::isfinite(q[k])) return fail(CG_EINVAL, "reaction %d: SRI parameters not finite", j);
+            if (!(q[0] >= 0.0) || !(q[2] > 0.0) || !(q[3] > 0.0))
+                return fail(CG_EINVAL, "reaction %d: SRI needs a >= 0, c > 0, d > 0", j);
+        }
+        const int p0 = d->plog_ptr ? d->plog_ptr[j] : 0, p1 = d->plog_ptr ? d->plog_ptr[j + 1] : 0;
+        if (t == CG_RXN_PLOG) {
+            if (!d->plog_ptr || !d->plog) return fail(CG_EINVAL, "reaction %d is PLOG but plog is NULL", j);
+            if (p1 <= p0) return fail(CG_EINVAL, "reaction %d: PLOG needs at least one rate expression", j);
+            for (int e = p0; e < p1; ++e) {
+                const double* q = d->plog + 4 * e;
+                if (!(q[0] > 0.0) || !std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) ||
+                    !std::isfinite(q[3]))
+                    return fail(CG_EINVAL, "reaction %d: PLOG entry %d invalid", j, e - p0);
+                if (e > p0 && q[0] < q[-4]) return fail(CG_EINVAL, "reaction %d: PLOG pressures must not decrease", j);
+            }
+        } else if (p1 != p0) {
+            return fail(CG_EINVAL, "reaction %d: only PLOG reactions take PLOG entries", j);
+        }
         if (t == CG_RXN_TROE) {
             const double* tr = d->troe + 4 * j;
             if (!std::isfinite(tr[0]) || !(tr[1] != 0.0) || !(tr[2] != 0.0) || !std::isfinite(tr[1]) ||
@@ -520,8 +548,8 @@ cg_status validate(const cg_mech_desc* d) {
         }
         const int e0 = d->eff_ptr[j], e1 = d->eff_ptr[j + 1];
         if (e1 < e0) return fail(CG_EINVAL, "eff_ptr must be non-decreasing (reaction %d)", j);
-        if (t == CG_RXN_ELEMENTARY && e1 != e0)
-            return fail(CG_EINVAL, "reaction %d: elementary reactions take no efficiencies", j);
+        if ((t == CG_RXN_ELEMENTARY || t == CG_RXN_PLOG) && e1 != e0)
+            return fail(CG_EINVAL, "reaction %d: elementary and PLOG reactions take no efficiencies", j);
         for (int e = e0; e < e1; ++e) {
             if (!d->eff_idx || !d->eff_val) return fail(CG_EINVAL, "eff_idx/eff_val required");
             if (d->eff_idx[e] < 0 || d->eff_idx[e] >= ns)
@@ -634,7 +662,8 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
         hasT2(nr, 0), eff_ptr(nr + 1, 0), eff_idx;
     std::vector<double> lnA(nr), beta(nr), Ta(nr), dlnA0(nr, 0.0), dbeta0(nr, 0.0), dTa0(nr, 0.0),
         talpha(nr, 0.0), tiT3(nr, 0.0), tiT1(nr, 0.0), tT2(nr, 0.0), eff_am1, snud(6 * (size_t)nr, 0.0),
-        sumnud(nr, 0.0);
+        sumnud(nr, 0.0), sri(5 * (size_t)nr, 0.0), pl_lnp, pl_lnA, pl_b, pl_Ta;
+    std::vector<int> pl_lev(nr + 1, 0), pl_rate;
     std::vector<Term> wterms, vterms, jterms;
     std::vector<double> nu(ns);
     for (int jj = 0; jj < nr; ++jj) {
@@ -658,7 +687,28 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
         lnA[jj] = d->arr[3 * j];
         beta[jj] = d->arr[3 * j + 1];
         Ta[jj] = d->arr[3 * j + 2] / kR;
-        const bool fall = rtype[jj] == CG_RXN_LINDEMANN || rtype[jj] == CG_RXN_TROE;
+        const bool fall = rtype[jj] == CG_RXN_LINDEMANN || rtype[jj] == CG_RXN_TROE || rtype[jj] == CG_RXN_SRI;
+        if (rtype[jj] == CG_RXN_SRI) {
+            const double* q = d->sri + 5 * j;
+            sri[0 * (size_t)nr + jj] = q[0];
+            sri[1 * (size_t)nr + jj] = q[1];
+            sri[2 * (size_t)nr + jj] = 1.0 / q[2];
+            sri[3 * (size_t)nr + jj] = std::log(q[3]);
+            sri[4 * (size_t)nr + jj] = q[4];
+        }
+        if (rtype[jj] == CG_RXN_PLOG) {   // levels of equal pressure, each with its rates
+            for (int e = d->plog_ptr[j]; e < d->plog_ptr[j + 1]; ++e) {
+                const double* q = d->plog + 4 * e;
+                if (e == d->plog_ptr[j] || q[0] != q[-4]) {
+                    pl_lnp.push_back(std::log(q[0]));
+                    pl_rate.push_back((int)pl_lnA.size());
+                }
+                pl_lnA.push_back(q[1]);
+                pl_b.push_back(q[2]);
+                pl_Ta.push_back(q[3] / kR);
+            }
+        }
+        pl_lev[jj + 1] = (int)pl_lnp.size();
         if (fall) {
             dlnA0[jj] = d->arr0[3 * j] - d->arr[3 * j];
             dbeta0[jj] = d->arr0[3 * j + 1] - d->arr[3 * j + 1];
@@ -725,6 +775,16 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     UP(sidx, sidx) UP(snu, snu) UP(snud, snud) UP(sumnud, sumnud) UP(lnA, lnA) UP(beta, beta) UP(Ta, Ta) UP(dlnA0, dlnA0)
     UP(dbeta0, dbeta0) UP(dTa0, dTa0) UP(talpha, talpha) UP(tiT3, tiT3) UP(tiT1, tiT1)
     UP(tT2, tT2) UP(hasT2, hasT2) UP(eff_ptr, eff_ptr) UP(eff_idx, eff_idx) UP(eff_am1, eff_am1)
+    UP(sri, sri)
+#undef UP
+    pl_rate.push_back((int)pl_lnA.size());
+    dm.has_plog = pl_lnp.empty() ? 0 : 1;
+#define UP(vec, field)                                           \
+    if ((st = upload(m->allocs, vec, &dm.field)) != CG_OK) {     \
+        cg_mech_destroy(m);                                      \
+        return st;                                               \
+    }
+    UP(pl_lev, pl_lev) UP(pl_rate, pl_rate) UP(pl_lnp, pl_lnp) UP(pl_lnA, pl_lnA) UP(pl_b, pl_b) UP(pl_Ta, pl_Ta)
 #undef UP
     if ((st = upload(m->allocs, perm, &m->dperm)) != CG_OK) {
         cg_mech_destroy(m);
@@ -1032,7 +1092,7 @@ cg_status cg_mech_set_arrhenius(cg_mech* m, const double* arr) {
         lnA[jj] = arr[3 * j];
         beta[jj] = arr[3 * j + 1];
         Ta[jj] = arr[3 * j + 2] / kR;
-        if (types[jj] == CG_RXN_LINDEMANN || types[jj] == CG_RXN_TROE) {   // k_0 is kept
+        if (types[jj] == CG_RXN_LINDEMANN || types[jj] == CG_RXN_TROE || types[jj] == CG_RXN_SRI) {   // k_0 kept
             dlnA0[jj] = m->arr0[3 * j] - arr[3 * j];
             dbeta0[jj] = m->arr0[3 * j + 1] - arr[3 * j + 1];
             dTa0[jj] = (m->arr0[3 * j + 2] - arr[3 * j + 2]) / kR;

@@ -32,7 +32,7 @@ constexpr double kLn10 = 2.302585092994045684;
 constexpr double kInvLn10 = 0.43429448190325182765;
 constexpr unsigned kFull = 0xffffffffu;
 
-enum { RXN_ELEM = 0, RXN_TB = 1, RXN_LIND = 2, RXN_TROE = 3 };
+enum { RXN_ELEM = 0, RXN_TB = 1, RXN_LIND = 2, RXN_TROE = 3, RXN_SRI = 4, RXN_PLOG = 5 };
 enum { R_CONV = 0, R_CONP = 1, R_CONP_LIT = 2 };
 enum { CELL_OK = 0, CELL_NEWTON_FAIL = 1, CELL_STEP_TOO_SMALL = 2, CELL_MAX_STEPS = 3,
        CELL_NONFINITE = 4, CELL_NO_RECORD = 5 };
@@ -72,6 +72,13 @@ struct DevMech {
     // rc_ptr[w] .. rc_ptr[w+1]-1, chunk c = reactions rc_first[c] + 0 .. rc_len[c]-1
     const int *rc_ptr, *rc_first, *rc_len;
     const double* exp2j;         // 2^(j/64), j = 0..63 (exp_tab)
+    // SRI falloff: [5][nr] = a, b, 1/c, ln d, e
+    const double* sri;
+    // PLOG: pressure levels of reaction j are pl_lev[j] .. pl_lev[j+1]-1,
+    // each with ln p and its Arrhenius rates pl_rate[l] .. pl_rate[l+1]-1
+    int has_plog;
+    const int *pl_lev, *pl_rate;
+    const double *pl_lnp, *pl_lnA, *pl_b, *pl_Ta;
 };
 
 // Working arrays of one cell. Each lives in the team's slice of shared
@@ -353,6 +360,7 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
     const double Mc = team_sum<TEAM>(csum, W.red);
     team_sync<TEAM>();   // SP visible to the whole team
     const double lnPRT = M.ln_pref_R - lnT;   // ln(p_ref / (R T))
+    const double lnP = M.has_plog ? log(8314.46261815324 * T * Mc) : 0.0;   // ln p = ln(R T sum C)
     double* q = W.RD;
     double* dqdT = q + nr;
     double* wv = dqdT + nr;
@@ -364,10 +372,46 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
         const int j = __ldg(M.rc_first + c) + l32;
         const int type = __ldg(M.rtype + j);
         const double bj = __ldg(M.beta + j), Taj = __ldg(M.Ta + j);
-        const double kA = exp_tab(__ldg(M.lnA + j) + bj * lnT - Taj * invT, M.exp2j);
+        const double kA = type == RXN_PLOG ? 0.0 : exp_tab(__ldg(M.lnA + j) + bj * lnT - Taj * invT, M.exp2j);
         const double dlnkA = (bj + Taj * invT) * invT;
         double kf, dkf_dT, dkf_dM = 0.0;
-        if (type == RXN_ELEM) {
+        if (type == RXN_PLOG) {
+            // Section 2.2.4: ln k linear in ln p between the bracketing levels
+            // (sum of a level's rates), the nearest level outside the range;
+            // p = R T sum C, so k depends on C through sum C (dkf_dM)
+            const int l0 = __ldg(M.pl_lev + j), l1 = __ldg(M.pl_lev + j + 1);
+            int lb = l0;
+            while (lb < l1 && __ldg(M.pl_lnp + lb) < lnP) ++lb;
+            auto level = [&](int l, double& dlnk) {
+                double k = 0.0, dk = 0.0;
+                const int r1 = __ldg(M.pl_rate + l + 1);
+                for (int r = __ldg(M.pl_rate + l); r < r1; ++r) {
+                    const double br = __ldg(M.pl_b + r), Tr = __ldg(M.pl_Ta + r);
+                    const double kr = exp_tab(__ldg(M.pl_lnA + r) + br * lnT - Tr * invT, M.exp2j);
+                    k += kr;
+                    dk = fma(kr, (br + Tr * invT) * invT, dk);
+                }
+                dlnk = dk / k;
+                return k;
+            };
+            if (lb == l0 || lb == l1) {
+                double d0;
+                kf = level(lb == l0 ? l0 : l1 - 1, d0);
+                dkf_dT = kf * d0;
+            } else {
+                double d0, d1;
+                const double k0 = level(lb - 1, d0), k1 = level(lb, d1);
+                const double p0 = __ldg(M.pl_lnp + lb - 1);
+                const double idl = 1.0 / (__ldg(M.pl_lnp + lb) - p0);
+                const double lk0 = log(k0), dlk = log(k1) - lk0;
+                const double w = (lnP - p0) * idl;
+                kf = exp(fma(dlk, w, lk0));
+                const double sl = dlk * idl;
+                dkf_dT = kf * (fma(w, d1 - d0, d0) + sl * invT);
+                dkf_dM = kf * sl / Mc;
+            }
+            if (xf) xf[j] = 0.0;   // not set by (ln A, b, Ea)
+        } else if (type == RXN_ELEM) {
             kf = kA;
             dkf_dT = kA * dlnkA;
             if (xf) xf[j] = 1.0;
@@ -416,6 +460,20 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                     const double t2 = 2.0 * Lc * f1 * ig * ig;
                     dlogF_dP = clamp ? 0.0 : -t2 * df1_dx;
                     dlogF_dT = (ig - t2 * (-0.67 * df1_dx - 1.27 * df1_dn)) * dL_dT;
+                } else if (type == RXN_SRI) {
+                    // Section 2.2.3: F = d [a e^(-b/T) + e^(-T/c)]^X T^e, X = 1/(1 + log10^2 Pr)
+                    const double a = __ldg(M.sri + j), bb = __ldg(M.sri + nr + j), ic = __ldg(M.sri + 2 * nr + j);
+                    const double lnd = __ldg(M.sri + 3 * nr + j), ee = __ldg(M.sri + 4 * nr + j);
+                    const bool clamp = !(Pr >= 1e-300);
+                    const double P = log(clamp ? 1e-300 : Pr) * kInvLn10;
+                    const double X = 1.0 / fma(P, P, 1.0);
+                    const double ea = exp_tab(-bb * invT, M.exp2j), ec = exp_tab(-T * ic, M.exp2j);
+                    const double G = fma(a, ea, ec);
+                    const double dG = fma(a * bb * invT * invT, ea, -ic * ec);
+                    const double lnG = log(G);
+                    F = exp_tab(fma(X, lnG, fma(ee, lnT, lnd)), M.exp2j);
+                    dlogF_dP = clamp ? 0.0 : lnG * kInvLn10 * (-2.0 * P * X * X);
+                    dlogF_dT = fma(X, dG / G, ee * invT) * kInvLn10;
                 }
                 const double ip = 1.0 / (1.0 + Pr);
                 kf = kA * (Pr * ip) * F;

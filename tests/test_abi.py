@@ -83,3 +83,24 @@ def test_null_arguments(lib):
     assert lib.cg_integrate(None, ctypes.byref(o), 4, None, None, None, None, None, None) == chemgb.CG_EINVAL
     assert "mech is NULL" in lib.cg_last_error().decode()
     assert lib.cg_mech_n_species(None) == -1
+
+
+def test_mech_create_checks_sri_and_plog(lib):
+    """SRI and PLOG reactions (Section 2.2.3, 2.2.4): their parameter
+    arrays are required and checked before anything reaches the GPU."""
+    base = inputs.with_sri_plog(inputs.gen_mechanism("h2"), n_sri=1, n_plog=2, seed=1)
+    j_sri = int(np.flatnonzero(base.rtype == inputs.RXN_SRI)[0])
+    j_plog = int(np.flatnonzero(base.rtype == inputs.RXN_PLOG)[0])
+    cases = []
+    m = base.copy(); m.sri[j_sri, 2] = 0.0; cases.append((m, "SRI needs"))
+    m = base.copy(); m.plog[m.plog_ptr[j_plog] + 1, 0] = m.plog[m.plog_ptr[j_plog], 0] / 2
+    cases.append((m, "must not decrease"))
+    m = base.copy(); m.plog[m.plog_ptr[j_plog], 0] = -1.0; cases.append((m, "PLOG entry"))
+    for mech, needle in cases:
+        with pytest.raises(chemgb.ChemgbError) as e:
+            chemgb.cg_mech_create(mech)
+        assert e.value.code == chemgb.CG_EINVAL and needle in str(e.value)
+    d, keep = _desc(base)   # no sri / plog arrays given
+    h = ctypes.c_void_p()
+    assert lib.cg_mech_create(ctypes.byref(d), ctypes.byref(h)) == chemgb.CG_EINVAL
+    assert b"SRI but sri is NULL" in lib.cg_last_error()

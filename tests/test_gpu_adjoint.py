@@ -257,3 +257,16 @@ def test_autograd_function(mechs, ref, handles):
     close(Y0.grad.cpu().numpy().T, dY0, 1e-6)
     for k in range(3):
         close(theta.grad.numpy()[:, k], grad.sum(axis=0)[:, k], 1e-6)
+
+
+def test_adjoint_parity_sri_plog():
+    """The adjoint with SRI falloff and PLOG reactions present (their rate
+    derivatives enter through the Jacobian and, for SRI, the parameter
+    factor Pr/(1+Pr) - dlog10F/dlog10Pr; PLOG rates take no (ln A, b, Ea))."""
+    m = inputs.with_sri_plog(inputs.gen_mechanism("ch4"), n_sri=8, n_plog=20, seed=3)
+    r, h = oracle.RefMech(m), chemgb.cg_mech_create(m)
+    T, Y, p = inputs.field_reactor(m, 29, (1250, 1450), (0.5, 40), (0.5, 2.0), "CH4", seed=17)
+    o, og = both_opts(dt=2e-6, rtol=1e-7, atol=1e-13)
+    g = compare(m, r, h, o, og, T, Y, p)
+    plog = np.flatnonzero(m.rtype == inputs.RXN_PLOG)
+    assert not g["dtheta"][plog].any()

@@ -530,3 +530,54 @@ def test_split_step_edge_cases(mechs, ref, handles):
     with pytest.raises(chemgb.ChemgbError) as e:
         run_split(h, chemgb.make_opts(**BE_OPTS), rho, u, rhoY, T)     # constant pressure: refused
     assert e.value.code == chemgb.CG_EINVAL
+
+
+# --- SRI falloff and PLOG reactions (Section 2.2.3, 2.2.4) ------------------
+
+@pytest.fixture(scope="module")
+def xset():
+    m = inputs.with_sri_plog(inputs.gen_mechanism("ch4"), n_sri=8, n_plog=20, seed=3)
+    return m, oracle.RefMech(m), chemgb.cg_mech_create(m)
+
+
+@pytest.mark.parametrize("reactor", [chemgb.CG_CONV, chemgb.CG_CONP])
+def test_sri_plog_rates_and_jacobian_parity(xset, reactor):
+    """Random states of Section 5.1 (pressures 0.1-10 atm, so PLOG cells
+    fall below, inside and between the 0.1-100 atm levels)."""
+    m, r, h = xset
+    N = 45
+    T, C, p = inputs.random_states(m, N, seed=303)
+    Sg = gpu_rates(h, T, C, reactor)
+    So = r.source(T, C, reactor)
+    nu = np.abs(nu_matrix(m))
+    for c in range(N):
+        scale = nu @ np.abs(r.rates(T[c], C[c])[2])
+        if reactor == chemgb.CG_CONP:
+            scale = scale + C[c] * (np.abs(So[c, 0]) / T[c] + scale.sum() / C[c].sum())
+        np.testing.assert_array_less(np.abs(Sg[c, 1:] - So[c, 1:]), 1e-12 * scale + 1e-300)
+        assert abs(Sg[c, 0] - So[c, 0]) <= 1e-11 * abs(So[c, 0]) + 1e-300 or abs(So[c, 0]) < 1e-300
+    J = torch.empty((N, h.n, h.n), dtype=torch.float64, device=DEV)
+    chemgb.cg_eval_jacobian(h, reactor, d(T), d(C.T), J)
+    torch.cuda.synchronize()
+    Jg, Jo = J.cpu().numpy(), r.jacobian(T, C, reactor)
+    rowmax = np.abs(Jo).max(axis=2, keepdims=True)
+    assert np.all(np.abs(Jg - Jo) <= 1e-10 * np.abs(Jo) + 1e-12 * rowmax)
+
+
+def test_sri_plog_integration_parity(xset):
+    m, r, h = xset
+    T, Y, p = inputs.field_reactor(m, 70, (1200, 1500), (0.5, 40), (0.5, 2.0), "CH4", seed=7)
+    o = dict(BE_OPTS, dt=1e-6, nsub=2)
+    To, Yo, so, sto = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, stg = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    assert np.all(so == 0)
+    same = np.all(stg[:, :3] == sto[:, :3], axis=1)
+    assert same.mean() > 0.98
+    assert_state_close(Tg[same], Yg[same], To[same], Yo[same], 1e-10, 1e-22)
+    o = dict(ADAPT, dt=2e-6)
+    To, Yo, so, _ = r.integrate(T, Y, p, o, nthreads=8)
+    Tg, Yg, sg, _ = run_gpu(h, chemgb.make_opts(**o), T, Y, p)
+    np.testing.assert_array_equal(sg, so)
+    np.testing.assert_allclose(Tg, To, rtol=1e-6)
+    assert np.max(np.abs(Yg - Yo)) < 1e-6

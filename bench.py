@@ -335,6 +335,10 @@ def run_gpu(args):
     cfg = CONFIGS[args.config]
     precision = cfg["precision"] if args.precision is None else args.precision
     parts = make_workload(args.config, args.cells or cfg["cells"], seed=rank)
+    if args.sri_plog:   # the same workload with SRI falloff and PLOG reactions in the mechanism
+        from paper_2510_10005_gb300 import inputs
+        parts = [(inputs.with_sri_plog(m, n_sri=max(1, m.nr // 40), n_plog=max(1, m.nr // 16), seed=3), T, Y, p)
+                 for m, T, Y, p in parts]
     opts_d = opts_dict(args.config, precision, args.method, args.linear, args.prec)
     split = args.surface == "split"
     if split:
@@ -499,7 +503,9 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args.config, args.method, args.linear, args.prec)
                    + ("; operator-split surface: (rho, u, rho Y) in, T recovered (5 Newton iterations), "
-                      "constant volume, T and R out" if split else ""),
+                      "constant volume, T and R out" if split else "")
+                   + ("; mechanism with nr/40 Troe reactions made SRI and nr/16 elementary reactions made "
+                      "PLOG (3-6 levels, 0.1-100 atm)" if args.sri_plog else ""),
                    "config": args.config,
                    "cells_per_gpu": N_total,
                    "newton_matrix": "fp32" if precision == 1 else "fp64", "state_bytes": state_bytes,
@@ -783,6 +789,8 @@ def main():
                     help="replace the workload's integrator (configs 1, 2, 3, 5)")
     ap.add_argument("--linear", choices=sorted(LINEAR), default=None, help="Newton systems: dense LU or GMRES")
     ap.add_argument("--prec", choices=sorted(PRECS), default=None, help="GMRES preconditioner (default gs)")
+    ap.add_argument("--sri-plog", action="store_true",
+                    help="give the workload's mechanisms SRI falloff and PLOG reactions")
     ap.add_argument("--surface", choices=["integrate", "split"], default="integrate",
                     help="split: the operator-split call of a compressible solver (rho, u, rho Y in; T, R out), "
                          "constant volume")

@@ -1,0 +1,40 @@
+"""The benchmark's input construction and bookkeeping (CPU): the conserved
+variables of the split surface match the oracle's thermodynamics, the
+workloads have the stated shapes and ranges, and the algorithmic flop count
+per Newton iteration is the stated formula's."""
+import numpy as np
+import pytest
+
+import bench
+import oracle
+from paper_2510_10005_gb300 import inputs
+
+
+def test_flow_state_energy_matches_oracle_thermo():
+    m = inputs.gen_mechanism("ch4")
+    r = oracle.RefMech(m)
+    T, Y, p = inputs.field_flames(m, 64, seed=2)
+    rho, u, rhoY = bench.flow_state(m, T, Y, p)
+    uo = np.array([Y[c] @ r.thermo(T[c])["u"] for c in range(len(T))])
+    np.testing.assert_allclose(u, uo, rtol=1e-12, atol=1e-9 * np.abs(uo).max())
+    np.testing.assert_allclose(rho, p / (inputs.R_UNIV * T * (Y / m.W).sum(axis=1)), rtol=1e-15)
+    np.testing.assert_allclose(rhoY.sum(axis=1), rho * Y.sum(axis=1), rtol=1e-14)
+
+
+@pytest.mark.parametrize("config,ns,lo,hi", [(1, 9, 1000, 1500), (4, 53, 1100, 1400), (5, 160, 700, 1600)])
+def test_workload_ranges(config, ns, lo, hi):
+    (m, T, Y, p), = bench.make_workload(config, 256)
+    assert m.ns == ns and len(T) == 256 and Y.shape == (256, ns)
+    assert T.min() >= lo and T.max() <= hi
+    np.testing.assert_allclose(Y.sum(axis=1), 1.0, rtol=1e-12)
+
+
+def test_flops_per_newton_formula():
+    m = inputs.gen_mechanism("ch4")
+    n = m.ns + 1
+    j = bench.j_term_count(m)
+    assert bench.algorithmic_flops_per_newton(m.ns, m.nr, j, False) == \
+        pytest.approx(2 * n**3 / 3 + 8 * n * n + 2 * j + 30 * m.nr + 40 * m.ns)
+    assert bench.algorithmic_flops_per_newton(m.ns, m.nr, j, True) == \
+        pytest.approx(8 * n * n + 2 * j + 30 * m.nr + 40 * m.ns)
+    assert 150_000 < bench.algorithmic_flops_per_newton(m.ns, m.nr, j, False) < 160_000

@@ -127,6 +127,9 @@ def j_term_count(mech) -> int:
     return total
 
 
+FP32_PEAK = 6.98e13   # FLOP/s, measured FP32 FMA rate on this GB300 (register-resident loop)
+
+
 def fp64_peak(sm_count: int, sm_max_mhz: float) -> float:
     """FP64 FMA pipe: one unit per SM sub-partition retiring half a lane per
     clock, 2 lanes (4 FLOP) per clock per SM (measured: 1.195e12 FLOP/s at
@@ -431,7 +434,7 @@ def run_gpu(args):
     value = multirank.job_throughput(N_total, ws, args.steps, ms * 1e-3)
     launch_ms = ms / args.steps
 
-    newton, flops, failed, stat_means = 0, 0.0, 0, []
+    newton, flops, flops32, failed, stat_means = 0, 0.0, 0.0, 0, []
     for (m, *_), b in zip(parts, bufs):
         sh = b["stats"].cpu().numpy()
         nwt = int(sh[2].astype(np.int64).sum())
@@ -442,6 +445,8 @@ def run_gpu(args):
         if opts_d["method"] == 3:   # Rosenbrock-2: plus a second rate evaluation and solve per step
             per += 30.0 * m.nr + 40.0 * m.ns + 2.0 * n1 ** 2
         flops += nwt * per
+        if precision == 1 and not gm:   # the FP32 factorisations (stats row 3), 2n^3/3 each
+            flops32 += float(sh[3].astype(np.int64).sum()) * 2.0 * n1 ** 3 / 3
         if gm:   # GMRES iterations (stats row 3): matvec 2n^2, preconditioner, Gram-Schmidt and norms ~10n
             pc = {0: 0.0, 1: n1, 2: n1 * n1}[opts_d.get("preconditioner", 2)]
             flops += float(sh[3].astype(np.int64).sum()) * (2.0 * n1 * n1 + pc + 10.0 * n1) - nwt * 2.0 * n1 * n1
@@ -516,6 +521,12 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": measured_traffic(args.config, N_total),
                      "peak_source": "derived: 4 FP64 FLOP/clk/SM (measured DFMA rate) x SMs x max SM clock",
                      "kernel": "integrate_kernel", "newton_per_launch": newton},
+        **({"roofline_fp32": {"bound": "alu", "achieved": flops32 / (launch_ms * 1e-3) / 1e12, "peak": FP32_PEAK / 1e12,
+                              "unit": "TFLOP/s", "frac": flops32 / (launch_ms * 1e-3) / FP32_PEAK,
+                              "what": "FP32 LU factorisations of the mixed-precision Newton (2n^3/3 each)",
+                              "peak_source": "measured FP32 FMA rate (register-resident loop)",
+                              "time_weighted_frac": (flops / peak + flops32 / FP32_PEAK) / (launch_ms * 1e-3)}}
+           if flops32 > 0 else {}),
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": args.steps,

@@ -122,3 +122,44 @@ def test_adjoint_equals_forward_sensitivity_with_sri_plog(xmech):
         e[:, k] = 1.0
         dyend, _ = r.tangent(y0, e, o)
         np.testing.assert_allclose(dy0[:, k], dyend[:, 0], rtol=1e-9)
+
+
+def _golden_plog():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "plog_section_2_2_4.txt")
+    rows = np.array([[float(v) for v in line.split()] for line in open(path)
+                     if line.strip() and not line.startswith("#")])
+    # SI-kmol: p in Pa, A of a bimolecular reaction in m^3/(kmol s), Ea in J/kmol
+    return np.stack([rows[:, 0] * inputs.P_ATM, np.log(rows[:, 1] * 1e-3), rows[:, 2], rows[:, 3] * 4184.0],
+                    axis=1)
+
+
+def test_plog_printed_example():
+    """The rate table printed in Section 2.2.4: seven pressure intervals (six
+    levels); the level's own rate at each printed pressure, log-linear in
+    between, the end levels' rates at and beyond 0.1 and 100 atm."""
+    table = _golden_plog()
+    c = np.array([3.5, 1e-4, -2e-8, 1e-12, -1e-16, -1000.0, 5.0])
+    m = inputs.Mechanism(
+        names=["A", "B", "C", "D"], elements=["X", "Y"], comp=np.array([[1, 0], [0, 1], [1, 0], [0, 1]]),
+        W=np.array([14.0, 18.0, 14.0, 18.0]), nasa7=np.stack([c] * 4),
+        rtype=np.array([inputs.RXN_PLOG], dtype=np.int32), reversible=np.array([1], dtype=np.int32),
+        rf_idx=np.array([[0, 1, -1]], dtype=np.int32), rf_nu=np.array([[1, 1, 0]], dtype=np.int32),
+        rr_idx=np.array([[2, 3, -1]], dtype=np.int32), rr_nu=np.array([[1, 1, 0]], dtype=np.int32),
+        arr=np.zeros((1, 3)), arr0=np.zeros((1, 3)), troe=np.zeros((1, 4)),
+        eff_ptr=np.zeros(2, dtype=np.int32), eff_idx=np.zeros(0, dtype=np.int32), eff_val=np.zeros(0),
+        plog_ptr=np.array([0, len(table)], dtype=np.int32), plog=table)
+    m.validate()
+    r = oracle.RefMech(m)
+    assert len(np.unique(table[:, 0])) + 1 == 7            # the seven interval tests the section counts
+    for T in (800.0, 1500.0, 2400.0):
+        ks = np.exp(table[:, 1] + table[:, 2] * np.log(T) - table[:, 3] / (R * T))
+        kf = lambda p: r.rates(T, _state_at(m, T, p))[0][0]
+        for p, k in zip(table[:, 0], ks):
+            assert kf(p) == pytest.approx(k, rel=1e-12)
+        for a in range(len(ks) - 1):
+            for w in (0.25, 0.5, 0.9):
+                p = np.exp((1 - w) * np.log(table[a, 0]) + w * np.log(table[a + 1, 0]))
+                assert kf(p) == pytest.approx(ks[a] ** (1 - w) * ks[a + 1] ** w, rel=1e-11)
+        assert kf(0.01 * inputs.P_ATM) == pytest.approx(ks[0], rel=1e-12)
+        assert kf(1000.0 * inputs.P_ATM) == pytest.approx(ks[-1], rel=1e-12)

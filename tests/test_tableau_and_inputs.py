@@ -1,5 +1,7 @@
 """Pins of the SDIRK tableaux (Appendix A) and invariants of the seeded
 input generator."""
+import os
+
 import numpy as np
 import pytest
 
@@ -7,11 +9,25 @@ from oracle import tableau
 from paper_2510_10005_gb300 import inputs
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
 def test_sdirk4_reproduces_printed_coefficients():
     """Full-precision coefficients agree with the seven printed digits of
-    Appendix A.2, and a_52 (missing from the print) equals b_2."""
+    Appendix A.2 (tests/golden/sdirk4_appendix_a2.txt), and a_52 (missing
+    from the print) equals b_2."""
     A = tableau.sdirk4_full_precision()
-    p = tableau.PRINTED_SDIRK4
+    p = read_golden("sdirk4_appendix_a2.txt")
+    assert np.all(np.diag(A) == p.pop("aii"))
     got = {"a21": A[1, 0], "a31": A[2, 0], "a32": A[2, 1], "a41": A[3, 0], "a42": A[3, 1],
            "a43": A[3, 2], "a51": A[4, 0], "a53": A[4, 2], "a54": A[4, 3], "b1": A[4, 0],
            "b2": A[4, 1], "b3": A[4, 2], "b4": A[4, 3], "b5": A[4, 4]}

@@ -289,6 +289,15 @@ def cpu_oracle_sample(parts, opts, n_sample: int, threads: int):
     return done / t, t, done
 
 
+def _take(x, idx, axis=0):
+    """Sampled entries of a host array or a device tensor (only the sample
+    leaves the device)."""
+    if hasattr(x, "index_select"):
+        import torch
+        return x.index_select(axis, torch.as_tensor(idx, device=x.device)).cpu().numpy()
+    return np.take(x, idx, axis=axis)
+
+
 def sampled_parity(parts, results, opts_d, n_sample):
     """Max errors of a launch's results (T [N], Y [ns, N], status [N] per
     mechanism) on an evenly spaced cell sample against the FP64 oracle;
@@ -300,10 +309,10 @@ def sampled_parity(parts, results, opts_d, n_sample):
             idx = np.linspace(0, len(T) - 1, min(n_sample, len(T))).astype(np.int64)
             To, Yo, so, _ = oracle.RefMech(m).integrate(T[idx], Y[idx], p[idx], oracle_opts(opts_d),
                                                         nthreads=os.cpu_count() or 1)
-            Tg, Yg = Tg_all[idx], Yg_all[:, idx].T
+            Tg, Yg = _take(Tg_all, idx), _take(Yg_all, idx, axis=1).T
             rel_T, abs_Y = float(np.max(np.abs(Tg - To) / To)), float(np.max(np.abs(Yg - Yo)))
             err[f"{m.ns}sp"] = {"cells": int(len(idx)), "max_rel_T": rel_T, "max_abs_Y": abs_Y,
-                                "status_match": float(np.mean(st_all[idx] == so)),
+                                "status_match": float(np.mean(_take(st_all, idx) == so)),
                                 "within_rtol": bool(rel_T <= opts_d["rtol"] and abs_Y <= opts_d["rtol"])}
         return err
     except Exception as e:   # the parity sample must not cost the bench line
@@ -503,8 +512,7 @@ def run_gpu(args):
     # sample of cells against the FP64 oracle, cell by cell
     err = None
     if args.err_sample > 0 and rank == 0 and not split:
-        err = sampled_parity(parts, [(b["T"].cpu().numpy(), b["Y"].cpu().numpy(), b["st"].cpu().numpy())
-                                     for b in bufs], opts_d, args.err_sample)
+        err = sampled_parity(parts, [(b["T"], b["Y"], b["st"]) for b in bufs], opts_d, args.err_sample)
 
     if rank != 0:
         return

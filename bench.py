@@ -14,19 +14,19 @@ Other workloads (reported beside the default line):
   --config 3  53 + 9 species in ONE persistent work-stealing launch,
               1,048,576 heavy-tailed cells each (90% frozen, 5% burnt,
               5% reacting, randomly interleaved), FP32 Newton matrix,
-              autotuned launch shape, replayed from a captured CUDA graph;
-              error against the FP64 oracle on a sample
+              autotuned launch shape, replayed from a captured CUDA graph
   --config 4  discrete adjoint: 53 species, 65,536 cells, T0 in U[1100, 1400] K,
               1 atm, phi in U[0.5, 2], adaptive SDIRK-4 over dt = 1e-4 s with
               checkpoints, then the backward sweep for
               L = sum (T_end - T_target)^2 (target from ln A + N(0, 0.1^2));
-              gradients w.r.t. (ln A, b, Ea) of all reactions and (T0, Y0);
-              sampled cells checked against the oracle's adjoint
+              gradients w.r.t. (ln A, b, Ea) of all reactions and (T0, Y0)
   --config 5  160 species / 900 reactions, T in U[700, 1600] K,
               p in U[20, 40] atm, adaptive SDIRK-4 (use --cells for a subset)
 
 Prints one JSON line. --impl reference times the FP64 CPU oracle on the
-host cores instead (a bounded sample of the same workload).
+host cores instead (a bounded sample of the same workload). The oracle runs
+only in that arm and in the cpu_baseline leg; parity at these sizes is
+checked by the GPU tests (tests/test_gpu_zfull_size.py).
 
 Multi-GPU (torchrun): every rank integrates its own cells (cells are
 independent; no collective on the data path); value = all cells /
@@ -289,36 +289,6 @@ def cpu_oracle_sample(parts, opts, n_sample: int, threads: int):
     return done / t, t, done
 
 
-def _take(x, idx, axis=0):
-    """Sampled entries of a host array or a device tensor (only the sample
-    leaves the device)."""
-    if hasattr(x, "index_select"):
-        import torch
-        return x.index_select(axis, torch.as_tensor(idx, device=x.device)).cpu().numpy()
-    return np.take(x, idx, axis=axis)
-
-
-def sampled_parity(parts, results, opts_d, n_sample):
-    """Max errors of a launch's results (T [N], Y [ns, N], status [N] per
-    mechanism) on an evenly spaced cell sample against the FP64 oracle;
-    recorded in the bench line, never fatal to it."""
-    try:
-        import oracle
-        err = {}
-        for (m, T, Y, p), (Tg_all, Yg_all, st_all) in zip(parts, results):
-            idx = np.linspace(0, len(T) - 1, min(n_sample, len(T))).astype(np.int64)
-            To, Yo, so, _ = oracle.RefMech(m).integrate(T[idx], Y[idx], p[idx], oracle_opts(opts_d),
-                                                        nthreads=os.cpu_count() or 1)
-            Tg, Yg = _take(Tg_all, idx), _take(Yg_all, idx, axis=1).T
-            rel_T, abs_Y = float(np.max(np.abs(Tg - To) / To)), float(np.max(np.abs(Yg - Yo)))
-            err[f"{m.ns}sp"] = {"cells": int(len(idx)), "max_rel_T": rel_T, "max_abs_Y": abs_Y,
-                                "status_match": float(np.mean(_take(st_all, idx) == so)),
-                                "within_rtol": bool(rel_T <= opts_d["rtol"] and abs_Y <= opts_d["rtol"])}
-        return err
-    except Exception as e:   # the parity sample must not cost the bench line
-        return {"error": f"{type(e).__name__}: {e}"}
-
-
 def dist_env():
     from paper_2510_10005_gb300 import multirank
     return multirank.env()
@@ -508,12 +478,6 @@ def run_gpu(args):
                "h2d_bytes_per_step": N * (m.ns + 2) * 8, "d2h_bytes_per_step": N * (m.ns + 1) * 8 + 20 * N,
                "steps": args.e2e_steps}
 
-    # parity at full size: the launch's own results on an evenly spaced
-    # sample of cells against the FP64 oracle, cell by cell
-    err = None
-    if args.err_sample > 0 and rank == 0 and not split:
-        err = sampled_parity(parts, [(b["T"], b["Y"], b["st"]) for b in bufs], opts_d, args.err_sample)
-
     if rank != 0:
         return
     cpu = None
@@ -558,8 +522,6 @@ def run_gpu(args):
         line["autotune"] = tuned
     if graph is not None:
         line["cuda_graph"] = True
-    if err is not None:
-        line["error_vs_fp64_oracle"] = err
     print(json.dumps(line), flush=True)
 
 
@@ -706,25 +668,6 @@ def run_adjoint(args):
                "d2h_bytes_per_step": N * (m.ns + 1) * 8 + m.nr * 3 * 8, "steps": args.e2e_steps,
                "api": "paper_2510_10005_gb300.autograd.integrate + loss.backward()"}
 
-    # parity at full size: sampled cells against the oracle's adjoint
-    parity = None
-    if args.adj_sample > 0 and rank == 0:
-        import oracle
-        idx = np.linspace(0, N - 1, args.adj_sample).astype(np.int64)
-        gT = 2.0 * (Tb - T_target).cpu().numpy()
-        r = oracle.RefMech(m)
-        t0 = time.perf_counter()
-        oT, oY, og, ost = r.adjoint_TY(T[idx], Y[idx], p[idx], gT[idx], np.zeros((len(idx), m.ns)),
-                                       oracle_opts(opts_d), nthreads=os.cpu_count() or 1)
-        el = time.perf_counter() - t0
-        gT0 = dT0.cpu().numpy()[idx]
-        gY0 = dY0.cpu().numpy()[:, idx].T
-        gc = np.moveaxis(dcells.cpu().numpy()[:, :, idx], 2, 0)
-        rel = lambda a, b: float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
-        parity = {"cells": int(len(idx)), "oracle_s": el, "status_ok": bool(np.all(ost == 0)),
-                  "max_rel_dT0": rel(gT0, oT), "max_rel_dY0": rel(gY0, oY),
-                  "max_rel_dtheta_cells": max(rel(gc[:, :, k], og[:, :, k]) for k in range(3))}
-
     if rank != 0:
         return
     cpu = None
@@ -761,7 +704,6 @@ def run_adjoint(args):
         "cells_failed": int((adj_status != 0).sum()),
         "stats_mean": {"steps": float(sh[0].mean()), "max_steps": int(sh[0].max()), "newton": float(sh[2].mean())},
         "loss": loss,
-        "adjoint_vs_oracle": parity,
     }
     print(json.dumps(line), flush=True)
 
@@ -810,13 +752,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=2048)
     ap.add_argument("--ref-sample", type=int, default=1024)
-    ap.add_argument("--err-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--team", type=int, default=0, help="threads per cell (default: the library's choice)")
     ap.add_argument("--tpb", type=int, default=1, help="cells per block with --team 32")
     ap.add_argument("--precision", type=int, default=None, help="0: FP64 Newton matrix, 1: FP32 LU")
-    ap.add_argument("--adj-sample", type=int, default=8, help="--config 4: cells checked against the oracle")
     ap.add_argument("--method", choices=sorted(METHODS), default=None,
                     help="replace the workload's integrator (configs 1, 2, 3, 5)")
     ap.add_argument("--linear", choices=sorted(LINEAR), default=None, help="Newton systems: dense LU or GMRES")

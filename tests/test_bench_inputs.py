@@ -39,14 +39,3 @@ def test_flops_per_newton_formula():
         pytest.approx(8 * n * n + 2 * j + 30 * m.nr + 40 * m.ns)
     assert 150_000 < bench.algorithmic_flops_per_newton(m.ns, m.nr, j, False) < 160_000
 
-
-def test_sampled_parity_record():
-    """The bench line's full-size parity record: zero for identical results,
-    an error entry (not an exception) when the results are unusable."""
-    parts = bench.make_workload(1, 48)
-    opts_d = bench.opts_dict(1, 0)
-    (m, T, Y, p), = parts
-    To, Yo, so, _ = oracle.RefMech(m).integrate(T, Y, p, bench.oracle_opts(opts_d))
-    rec = bench.sampled_parity(parts, [(To, Yo.T.copy(), so)], opts_d, 12)
-    assert rec["9sp"]["max_rel_T"] == 0.0 and rec["9sp"]["within_rtol"] and rec["9sp"]["cells"] == 12
-    assert "error" in bench.sampled_parity(parts, [(To, None, so)], opts_d, 12)

@@ -1,0 +1,120 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times, on sampled outputs the oracle computes cell by cell:
+
+* the 53-species flame field, 1,048,576 cells, adaptive SDIRK-4 in FP64
+  (the default bench line): T within rtol, Y within rtol (absolute),
+  statuses identical;
+* the heavy-tailed batch of 53 + 9 species, 2 x 1,048,576 cells, one
+  persistent launch with the FP32 Newton matrix: within rtol of the FP64
+  oracle;
+* the adjoint workload, 65,536 cells over 1e-4 s: sampled dL/dT0, dL/dY0 and
+  per-cell dL/dtheta within 1e-6 of the largest entry of each kind.
+
+Slow (about a minute and a half): collected after the other GPU tests."""
+import os
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+from paper_2510_10005_gb300 import chemgb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+THREADS = min(16, os.cpu_count() or 1)
+F64 = torch.float64
+
+
+def _dev(a, dtype=F64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def test_full_size_flame_field():
+    chemgb.load(build_if_missing=True)
+    (m, T, Y, p), = bench.make_workload(2, 1 << 20)
+    o = bench.opts_dict(2, 0)
+    h = chemgb.cg_mech_create(m)
+    Tt, Yt, pt = _dev(T), _dev(Y.T), _dev(p)
+    st = torch.empty(len(T), dtype=torch.int32, device=DEV)
+    chemgb.cg_integrate(h, chemgb.make_opts(**o), Tt, Yt, pt, st)
+    torch.cuda.synchronize()
+    idx = np.linspace(0, len(T) - 1, 96).astype(np.int64)
+    To, Yo, so, _ = oracle.RefMech(m).integrate(T[idx], Y[idx], p[idx], bench.oracle_opts(o), nthreads=THREADS)
+    sel = torch.as_tensor(idx, device=DEV)
+    Tg = Tt.index_select(0, sel).cpu().numpy()
+    Yg = Yt.index_select(1, sel).cpu().numpy().T
+    assert np.array_equal(st.index_select(0, sel).cpu().numpy(), so) and np.all(so == 0)
+    assert int((st != 0).sum()) == 0
+    np.testing.assert_allclose(Tg, To, rtol=o["rtol"])
+    assert np.max(np.abs(Yg - Yo)) <= o["rtol"]
+
+
+def test_full_size_mixed_batch_fp32():
+    chemgb.load(build_if_missing=True)
+    parts = bench.make_workload(3, 1 << 20)
+    o = bench.opts_dict(3, 1)
+    og = chemgb.make_opts(**o)
+    handles = [chemgb.cg_mech_create(m) for m, *_ in parts]
+    Ts, Ys, ps, sts = [], [], [], []
+    for m, T, Y, p in parts:
+        Ts.append(_dev(T))
+        Ys.append(_dev(Y.T))
+        ps.append(_dev(p))
+        sts.append(torch.empty(len(T), dtype=torch.int32, device=DEV))
+    # the benchmark's launch shape: autotuned on 16,384 cells of the dominant
+    # mechanism, the same team size for the other
+    sel = torch.linspace(0, len(Ts[0]) - 1, 16384, device=DEV).long()
+    chemgb.cg_autotune(handles[0], og, Ts[0][sel].contiguous(), Ys[0][:, sel].contiguous(), ps[0][sel].contiguous())
+    team, tpb = chemgb.cg_mech_get_launch(handles[0])
+    for h in handles[1:]:
+        chemgb.cg_mech_set_launch(h, team, tpb if team == 32 else 1)
+    chemgb.cg_integrate_batch(handles, og, Ts, Ys, ps, sts)
+    torch.cuda.synchronize()
+    for (m, T, Y, p), Tt, Yt, st in zip(parts, Ts, Ys, sts):
+        idx = np.linspace(0, len(T) - 1, 48).astype(np.int64)
+        To, Yo, so, _ = oracle.RefMech(m).integrate(T[idx], Y[idx], p[idx], bench.oracle_opts(o), nthreads=THREADS)
+        sel = torch.as_tensor(idx, device=DEV)
+        assert np.array_equal(st.index_select(0, sel).cpu().numpy(), so)
+        np.testing.assert_allclose(Tt.index_select(0, sel).cpu().numpy(), To, rtol=o["rtol"])
+        assert np.max(np.abs(Yt.index_select(1, sel).cpu().numpy().T - Yo)) <= o["rtol"]
+
+
+def test_full_size_adjoint():
+    chemgb.load(build_if_missing=True)
+    (m, T, Y, p), = bench.make_workload(4, 1 << 16)
+    o = bench.opts_dict(4, 0)
+    og = chemgb.make_opts(**o)
+    h = chemgb.cg_mech_create(m)
+    N = len(T)
+    Tt, Yt, pt = _dev(T), _dev(Y.T), _dev(p)
+    stats = torch.empty((4, N), dtype=torch.int32, device=DEV)
+    chemgb.cg_integrate(h, og, Tt.clone(), Yt.clone(), pt, None, stats)
+    torch.cuda.synchronize()
+    cap = int(stats[0].max().item()) * 2 + 8
+    ckpt = torch.empty((N, cap, m.ns + 2), dtype=F64, device=DEV)
+    ckpt_n = torch.empty(N, dtype=torch.int32, device=DEV)
+    st = torch.empty(N, dtype=torch.int32, device=DEV)
+    chemgb.cg_integrate_ckpt(h, og, Tt, Yt, pt, ckpt, ckpt_n, st)
+    rng = np.random.default_rng(4)
+    gT = rng.normal(size=N)
+    dT0, dY0 = torch.empty(N, dtype=F64, device=DEV), torch.empty((m.ns, N), dtype=F64, device=DEV)
+    dcell = torch.empty((m.nr, 3, N), dtype=F64, device=DEV)
+    ast = torch.empty(N, dtype=torch.int32, device=DEV)
+    chemgb.cg_integrate_adjoint(h, og, ckpt, ckpt_n, _dev(gT), torch.zeros((m.ns, N), dtype=F64, device=DEV),
+                                dT0, dY0, None, dcell, ast)
+    torch.cuda.synchronize()
+    assert int((st != 0).sum()) == 0 and int((ast != 0).sum()) == 0
+    idx = np.linspace(0, N - 1, 8).astype(np.int64)
+    oT, oY, og_, ost = oracle.RefMech(m).adjoint_TY(T[idx], Y[idx], p[idx], gT[idx], np.zeros((len(idx), m.ns)),
+                                                    bench.oracle_opts(o), nthreads=THREADS)
+    assert np.all(ost == 0)
+    sel = torch.as_tensor(idx, device=DEV)
+    rel = lambda a, b: np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+    assert rel(dT0.index_select(0, sel).cpu().numpy(), oT) < 1e-6
+    assert rel(dY0.index_select(1, sel).cpu().numpy().T, oY) < 1e-6
+    gc = np.moveaxis(dcell.index_select(2, sel).cpu().numpy(), 2, 0)
+    for k in range(3):
+        assert rel(gc[:, :, k], og_[:, :, k]) < 1e-6

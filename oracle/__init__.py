@@ -52,6 +52,8 @@ def _load():
         lib.cgref_mech_create.restype = P
         lib.cgref_mech_create.argtypes = [ctypes.c_int, ctypes.c_int] + [P] * 17
         lib.cgref_mech_destroy.argtypes = [P]
+        lib.cgref_mech_set_thermo.restype = ctypes.c_int
+        lib.cgref_mech_set_thermo.argtypes = [P, ctypes.c_int, P]
         lib.cgref_thermo.argtypes = [P, ctypes.c_double] + [P] * 6
         lib.cgref_rates.argtypes = [P, ctypes.c_double, P, P, P, P]
         lib.cgref_source.argtypes = [P, ctypes.c_int, ctypes.c_long, P, P]
@@ -131,6 +133,10 @@ class RefMech:
                       _f64(mech.sri), _i32(mech.plog_ptr),
                       _f64(mech.plog) if len(mech.plog) else np.zeros(4)]
         self.h = lib.cgref_mech_create(mech.ns, mech.nr, *[_p(a) for a in self._keep])
+        if getattr(mech, "thermo", None) is not None:   # a c_p polynomial of degree n_p != NASA-7's
+            coef = _f64(mech.thermo)
+            if lib.cgref_mech_set_thermo(self.h, coef.shape[1] - 3, _p(coef)) != 0:
+                raise ValueError("thermo degree n_p must lie in [0, 15]")
         self.ns, self.nr = mech.ns, mech.nr
         self.n = mech.ns + 1
 

@@ -59,13 +59,15 @@ struct Reaction {
     int sum_nu = 0;             // sum_i nu_ij = sum nu^r - sum nu^f
 };
 
-// Mechanism with the coefficient sets of Table 1 in mass-specific form,
-// n_p = 4 (a NASA-7 range is the n_p = 4 instance: a_k = R_i * a_{k+1}^{NASA},
-// h_ref = R_i * a6, s_ref = R_i * a7).
+// Mechanism with the coefficient sets of Table 1 in mass-specific form for a
+// c_p polynomial of degree n_p (eq. specific_heat_polynomial). A NASA-7 range
+// is the n_p = 4 instance: a_k = R_i * a_{k+1}^{NASA}, h_ref = R_i * a6,
+// s_ref = R_i * a7; Appendix C.1 refits to other degrees.
 struct Mech {
     int ns = 0, nr = 0;
+    int np = 4;                               // degree of the c_p polynomial
     std::vector<double> W, Ri;
-    std::vector<double> a, bc, cc, dc, fc;   // a: ns x 5; b, c, f: ns x 6; d: ns x 5
+    std::vector<double> a, bc, cc, dc, fc;   // a, d: ns x (n_p+1); b, c, f: ns x (n_p+2)
     std::vector<Reaction> rx;
 };
 
@@ -80,26 +82,64 @@ template <class S> S poly(const double* coef, int deg, const S& T) {
 }
 
 // c_p,i = sum_{k=0}^{n_p} a_ik T^k   (eq. specific_heat_polynomial)
-template <class S> S cp_i(const Mech& m, int i, const S& T) { return poly(&m.a[5 * i], 4, T); }
+template <class S> S cp_i(const Mech& m, int i, const S& T) {
+    return poly(&m.a[(m.np + 1) * i], m.np, T);
+}
 // h_i = sum_{k=0}^{n_p+1} b_ik T^k   (eq. enthalpy-polynomial)
-template <class S> S h_i(const Mech& m, int i, const S& T) { return poly(&m.bc[6 * i], 5, T); }
+template <class S> S h_i(const Mech& m, int i, const S& T) {
+    return poly(&m.bc[(m.np + 2) * i], m.np + 1, T);
+}
 // u_i = sum_{k=0}^{n_p+1} c_ik T^k   (eq. internal-energy-polynomial)
-template <class S> S u_i(const Mech& m, int i, const S& T) { return poly(&m.cc[6 * i], 5, T); }
+template <class S> S u_i(const Mech& m, int i, const S& T) {
+    return poly(&m.cc[(m.np + 2) * i], m.np + 1, T);
+}
 // s_i^o = a_i0 ln T + sum_{k=0}^{n_p} d_ik T^k   (eq. entropy_polynomial)
 template <class S> S s_i(const Mech& m, int i, const S& T, const S& lnT) {
-    return m.a[5 * i] * lnT + poly(&m.dc[5 * i], 4, T);
+    return m.a[(m.np + 1) * i] * lnT + poly(&m.dc[(m.np + 1) * i], m.np, T);
 }
 // g_i^o = -a_i0 T ln T + sum_{k=0}^{n_p+1} f_ik T^k   (eq. gibbs-polynomial)
 template <class S> S g_i(const Mech& m, int i, const S& T, const S& lnT) {
-    return -m.a[5 * i] * T * lnT + poly(&m.fc[6 * i], 5, T);
+    return -m.a[(m.np + 1) * i] * T * lnT + poly(&m.fc[(m.np + 2) * i], m.np + 1, T);
 }
 // c_v,i = c_p,i - R_i   (eq. cv_equation)
 template <class S> S cv_i(const Mech& m, int i, const S& T) { return cp_i(m, i, T) - m.Ri[i]; }
 // d c_p,i / dT
 double dcp_i(const Mech& m, int i, double T) {
+    const double* a = &m.a[(m.np + 1) * i];
     double out = 0.0, Tk = 1.0;
-    for (int k = 1; k <= 4; ++k) { out += k * m.a[5 * i + k] * Tk; Tk *= T; }
+    for (int k = 1; k <= m.np; ++k) { out += k * a[k] * Tk; Tk *= T; }
     return out;
+}
+
+// The coefficient sets of Table 1 from a c_p polynomial of degree n_p given
+// in molar form over R: coef[i*stride + k] = a_k of c_p/R (k = 0..n_p), then
+// the constants of h/R and s/R (the NASA-7 a6, a7 when n_p = 4).
+void set_thermo(Mech& m, int np, const double* coef, int stride) {
+    const int ns = m.ns;
+    m.np = np;
+    m.a.assign((np + 1) * ns, 0.0); m.dc.assign((np + 1) * ns, 0.0);
+    m.bc.assign((np + 2) * ns, 0.0); m.cc.assign((np + 2) * ns, 0.0); m.fc.assign((np + 2) * ns, 0.0);
+    for (int i = 0; i < ns; ++i) {
+        const double Ri = m.Ri[i];
+        const double* nc = coef + stride * i;
+        double* a = &m.a[(np + 1) * i];
+        for (int k = 0; k <= np; ++k) a[k] = Ri * nc[k];       // c_p fit coefficients
+        double href = Ri * nc[np + 1], sref = Ri * nc[np + 2];
+        double* b = &m.bc[(np + 2) * i];                         // Table 1, h_i
+        b[0] = href;
+        for (int k = 1; k <= np + 1; ++k) b[k] = a[k - 1] / k;
+        double* c = &m.cc[(np + 2) * i];                         // Table 1, u_i
+        c[0] = href;
+        c[1] = a[0] - Ri;
+        for (int k = 2; k <= np + 1; ++k) c[k] = a[k - 1] / k;
+        double* d = &m.dc[(np + 1) * i];                         // Table 1, s_i^o
+        d[0] = sref;
+        for (int k = 1; k <= np; ++k) d[k] = a[k] / k;
+        double* f = &m.fc[(np + 2) * i];                         // Table 1, g_i^o
+        f[0] = href;
+        f[1] = a[0] - sref;
+        for (int k = 2; k <= np + 1; ++k) f[k] = (1.0 / k - 1.0 / (k - 1)) * a[k - 1];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1160,30 +1200,8 @@ void* cgref_mech_create(int ns, int nr, const double* W, const double* nasa7,
     m->nr = nr;
     m->W.assign(W, W + ns);
     m->Ri.resize(ns);
-    m->a.resize(5 * ns); m->bc.resize(6 * ns); m->cc.resize(6 * ns);
-    m->dc.resize(5 * ns); m->fc.resize(6 * ns);
-    for (int i = 0; i < ns; ++i) {
-        double Ri = R_U / W[i];
-        m->Ri[i] = Ri;
-        const double* nc = nasa7 + 7 * i;
-        double* a = &m->a[5 * i];
-        for (int k = 0; k <= 4; ++k) a[k] = Ri * nc[k];        // c_p fit coefficients
-        double href = Ri * nc[5], sref = Ri * nc[6];
-        double* b = &m->bc[6 * i];                               // Table 1, h_i
-        b[0] = href;
-        for (int k = 1; k <= 5; ++k) b[k] = a[k - 1] / k;
-        double* c = &m->cc[6 * i];                               // Table 1, u_i
-        c[0] = href;
-        c[1] = a[0] - Ri;
-        for (int k = 2; k <= 5; ++k) c[k] = a[k - 1] / k;
-        double* d = &m->dc[5 * i];                               // Table 1, s_i^o
-        d[0] = sref;
-        for (int k = 1; k <= 4; ++k) d[k] = a[k] / k;
-        double* f = &m->fc[6 * i];                               // Table 1, g_i^o
-        f[0] = href;
-        f[1] = a[0] - sref;
-        for (int k = 2; k <= 5; ++k) f[k] = (1.0 / k - 1.0 / (k - 1)) * a[k - 1];
-    }
+    for (int i = 0; i < ns; ++i) m->Ri[i] = R_U / W[i];
+    set_thermo(*m, 4, nasa7, 7);
     m->rx.resize(nr);
     for (int j = 0; j < nr; ++j) {
         Reaction& r = m->rx[j];
@@ -1216,6 +1234,16 @@ void* cgref_mech_create(int ns, int nr, const double* W, const double* nasa7,
 }
 
 void cgref_mech_destroy(void* h) { delete static_cast<Mech*>(h); }
+
+// Replace the thermodynamics by a c_p polynomial of degree n_p (Section 2.1,
+// eq. specific_heat_polynomial; Appendix C.1): coef[ns][n_p + 3] holds a_0..a_np
+// of c_p/R (molar) and the h/R and s/R constants. 0, or -1 for n_p outside [0, 15].
+int cgref_mech_set_thermo(void* h, int np, const double* coef) {
+    if (np < 0 || np > 15) return -1;
+    Mech& m = *static_cast<Mech*>(h);
+    set_thermo(m, np, coef, np + 3);
+    return 0;
+}
 
 // Mass-specific thermo per species at one temperature: cp, h, u, s, g, cv.
 void cgref_thermo(const void* h, double T, double* cp, double* hh, double* u, double* s, double* g,

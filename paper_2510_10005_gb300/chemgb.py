@@ -285,11 +285,15 @@ class MechHandle:
     """Owns one cg_mech."""
 
     def __init__(self, mech):
+        thermo = getattr(mech, "thermo", None)
+        if thermo is not None and thermo.shape[1] != 7:
+            raise NotImplementedError(f"c_p polynomial of degree {thermo.shape[1] - 3}: the CUDA library "
+                                      "evaluates the n_p = 4 (NASA-7) form only")
         lib = load()
         f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
         i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
         self._keep = dict(
-            W=f64(mech.W), nasa7=f64(mech.nasa7), rxn_type=i32(mech.rtype), reversible=i32(mech.reversible),
+            W=f64(mech.W), nasa7=f64(mech.nasa7 if thermo is None else thermo), rxn_type=i32(mech.rtype), reversible=i32(mech.reversible),
             rf_idx=i32(mech.rf_idx), rf_nu=i32(mech.rf_nu), rr_idx=i32(mech.rr_idx), rr_nu=i32(mech.rr_nu),
             arr=f64(mech.arr), arr0=f64(mech.arr0), troe=f64(mech.troe), eff_ptr=i32(mech.eff_ptr),
             eff_idx=i32(mech.eff_idx) if len(mech.eff_idx) else np.zeros(1, np.int32),

@@ -2,8 +2,10 @@
 
 This module is shared by the CUDA path, the oracle and the tests. It holds
 no arithmetic of the integration method itself: it never evaluates
-thermodynamic properties, rates, source terms or Jacobians. It only draws
-mechanism parameters and cell states from seeded distributions shaped like
+thermodynamic properties of cells, rates, source terms or Jacobians. It
+draws mechanism parameters (and fits the c_p polynomials of a mechanism to
+its drawn curves, anchored at 298.15 K) and cell states from seeded
+distributions shaped like
 the workloads the paper studies (Table 2: mechanisms of 10-96 species and
 27-1054 reactions; Section 5.1 random-state recipe; Section 5.3 homogeneous
 reactor initial conditions).
@@ -17,6 +19,11 @@ Mechanism arrays (all numpy):
   names[ns], elements[ne], comp[ns, ne] (int atom counts), W[ns] kg/kmol,
   nasa7[ns, 7]  (a1..a5: cp/R polynomial; a6: h/R constant; a7: s/R constant,
                  one range used over the whole temperature domain),
+  thermo[ns, n_p + 3] or None  a c_p/R polynomial of another degree n_p in the
+                 same layout (a_0..a_np, h/R constant, s/R constant; Section 2.1,
+                 Appendix C.1); None means nasa7 (n_p = 4) is the thermodynamics,
+  cp_src[ns, 5] or None  the drawn curve the polynomials are fitted to:
+                 (c_lo, c_hi, theta, h_f(298.15 K) J/kmol, s(298.15 K) J/(kmol K)),
   rtype[nr]     (0 elementary, 1 third-body, 2 Lindemann, 3 Troe, 4 SRI falloff,
                  5 pressure-dependent Arrhenius "PLOG"),
   reversible[nr],
@@ -70,6 +77,8 @@ class Mechanism:
     sri: np.ndarray = None
     plog_ptr: np.ndarray = None
     plog: np.ndarray = None
+    thermo: np.ndarray = None
+    cp_src: np.ndarray = None
 
     def __post_init__(self):
         nr = int(self.rtype.shape[0])
@@ -79,6 +88,16 @@ class Mechanism:
             self.plog_ptr = np.zeros(nr + 1, dtype=np.int32)
         if self.plog is None:
             self.plog = np.zeros((0, 4))
+
+    @property
+    def thermo_np(self) -> int:
+        """Degree n_p of the c_p polynomial (4 for NASA-7)."""
+        return 4 if self.thermo is None else int(self.thermo.shape[1]) - 3
+
+    @property
+    def thermo_coef(self) -> np.ndarray:
+        """[ns, n_p + 3]: a_0..a_np of c_p/R, then the h/R and s/R constants."""
+        return self.nasa7 if self.thermo is None else self.thermo
 
     @property
     def ns(self) -> int:
@@ -92,16 +111,19 @@ class Mechanism:
         return self.names.index(name)
 
     def copy(self) -> "Mechanism":
-        return dataclasses.replace(
-            self, **{f.name: (np.array(getattr(self, f.name), copy=True)
-                              if isinstance(getattr(self, f.name), np.ndarray)
-                              else list(getattr(self, f.name)))
-                     for f in dataclasses.fields(self)})
+        def dup(v):
+            if isinstance(v, np.ndarray):
+                return np.array(v, copy=True)
+            return list(v) if isinstance(v, list) else v
+        return dataclasses.replace(self, **{f.name: dup(getattr(self, f.name)) for f in dataclasses.fields(self)})
 
     def validate(self) -> None:
         """Structural checks: index ranges, padding and element balance."""
         ns, nr = self.ns, self.nr
         assert self.nasa7.shape == (ns, 7) and self.W.shape == (ns,)
+        if self.thermo is not None:
+            assert self.thermo.ndim == 2 and self.thermo.shape[0] == ns and 3 <= self.thermo.shape[1] <= 18
+        assert self.cp_src is None or self.cp_src.shape == (ns, 5)
         for a in (self.rf_idx, self.rf_nu, self.rr_idx, self.rr_nu):
             assert a.shape == (nr, 3)
         assert self.arr.shape == (nr, 3) and self.arr0.shape == (nr, 3)
@@ -144,7 +166,7 @@ class Mechanism:
     def save(self, path: str) -> None:
         np.savez(path, names=np.array(self.names), elements=np.array(self.elements),
                  **{f.name: getattr(self, f.name) for f in dataclasses.fields(self)
-                    if f.name not in ("names", "elements")})
+                    if f.name not in ("names", "elements") and getattr(self, f.name) is not None})
 
     @staticmethod
     def load(path: str) -> "Mechanism":
@@ -215,6 +237,43 @@ def _species_set(kind: str, rng: np.random.Generator) -> list:
 # thermodynamic data (drawn, then fitted to the NASA-7 form)
 
 
+T_FIT = (300.0, 3000.0)   # K, range of the c_p fits
+T_ANCHOR = 298.15         # K, where h and s of a fit equal the drawn values
+
+
+def fit_thermo(src: np.ndarray, n_p: int) -> np.ndarray:
+    """Coefficients [n_p + 3] of one species fitted to its drawn curve
+    src = (c_lo, c_hi, theta, h_f, s_298): c_p/R = c_lo + (c_hi - c_lo)
+    (1 - exp(-T/theta)) fitted by least squares on 200 points over 300-3000 K
+    with a polynomial of degree n_p (Section 2.1, eq.
+    specific_heat_polynomial); the h/R and s/R constants make h and s equal
+    h_f and s_298 at 298.15 K (eq. enthalpy-adjustment and its entropy
+    analogue). n_p = 4 gives the NASA-7 row of the same species."""
+    c_lo, c_hi, theta, hf, s298 = (float(v) for v in src)
+    Tg = np.linspace(T_FIT[0], T_FIT[1], 200)
+    cp = c_lo + (c_hi - c_lo) * (1.0 - np.exp(-Tg / theta))
+    V = np.vander(Tg / 1000.0, n_p + 1, increasing=True)
+    coef = np.linalg.lstsq(V, cp, rcond=None)[0] / 1000.0 ** np.arange(n_p + 1)
+    T0 = T_ANCHOR
+    h_int = sum(coef[k] * T0 ** (k + 1) / (k + 1) for k in range(n_p + 1))
+    s_int = coef[0] * math.log(T0) + sum(coef[k] * T0 ** k / k for k in range(1, n_p + 1))
+    return np.concatenate([coef, [hf / R_UNIV - h_int, s298 / R_UNIV - s_int]])
+
+
+def with_thermo_degree(mech: Mechanism, n_p: int) -> Mechanism:
+    """A copy of `mech` whose thermodynamics is refitted with a c_p
+    polynomial of degree n_p (Appendix C.1 refits to n_p = 7 and 15) to the
+    same drawn curves; needs `cp_src` (generated mechanisms carry it)."""
+    if mech.cp_src is None:
+        raise ValueError("the mechanism carries no source curves (cp_src) to refit")
+    if not 0 <= n_p <= 15:
+        raise ValueError("n_p must lie in [0, 15]")
+    m = mech.copy()
+    m.thermo = np.array([fit_thermo(src, n_p) for src in m.cp_src])
+    m.validate()
+    return m
+
+
 def _nasa7_for(counts: dict, rng: np.random.Generator) -> np.ndarray:
     """Draw a smooth cp/R(T) curve, h_f(298) and s(298); fit NASA-7 to it.
 
@@ -222,6 +281,7 @@ def _nasa7_for(counts: dict, rng: np.random.Generator) -> np.ndarray:
     by least squares with a quartic (Section 2.1, eq. specific_heat_polynomial
     with n_p = 4); a6 and a7 anchor h and s at 298.15 K as the paper's
     enthalpy adjustment (eq. enthalpy-adjustment) does for h_ref.
+    Returns (NASA-7 row, h_f, s_298, radical, source curve).
     """
     nat = sum(counts.values())
     if nat == 1:
@@ -231,10 +291,6 @@ def _nasa7_for(counts: dict, rng: np.random.Generator) -> np.ndarray:
     else:
         c_lo, c_hi = 4.0, 3.0 * nat - 2.0
     theta = rng.uniform(500.0, 1500.0)
-    Tg = np.linspace(300.0, 3000.0, 200)
-    cp = c_lo + (c_hi - c_lo) * (1.0 - np.exp(-Tg / theta))
-    V = np.vander(Tg / 1000.0, 5, increasing=True)
-    coef = np.linalg.lstsq(V, cp, rcond=None)[0] / 1000.0 ** np.arange(5)
 
     # formation enthalpy: oxidised species are stable, open-shell ones are not
     h_, c_, o_, n_ = counts.get("H", 0), counts.get("C", 0), counts.get("O", 0), counts.get("N", 0)
@@ -248,12 +304,8 @@ def _nasa7_for(counts: dict, rng: np.random.Generator) -> np.ndarray:
         hf += rng.uniform(-30e6, 30e6) + 10e6 * (nat - 1) * rng.uniform(-1, 1)
     s298 = (rng.uniform(110e3, 150e3) + 25e3 * (nat - 1))        # J/(kmol K)
 
-    T0 = 298.15
-    h_int = sum(coef[k] * T0 ** (k + 1) / (k + 1) for k in range(5))
-    s_int = coef[0] * math.log(T0) + sum(coef[k] * T0 ** k / k for k in range(1, 5))
-    a6 = hf / R_UNIV - h_int
-    a7 = s298 / R_UNIV - s_int
-    return np.concatenate([coef, [a6, a7]]), hf, s298, radical
+    src = np.array([c_lo, c_hi, theta, hf, s298])
+    return fit_thermo(src, 4), hf, s298, radical, src
 
 
 # ----------------------------------------------------------------------------
@@ -289,6 +341,7 @@ def gen_mechanism(kind: str = "h2", seed: int | None = None) -> Mechanism:
     hf = np.array([t[1] for t in thermo])
     s298 = np.array([t[2] for t in thermo])
     radical = np.array([t[3] for t in thermo])
+    cp_src = np.array([t[4] for t in thermo])
     ns = len(names)
 
     # candidate reactions: 1<->2 (dissociation) and 2<->2 (exchange)
@@ -422,7 +475,7 @@ def gen_mechanism(kind: str = "h2", seed: int | None = None) -> Mechanism:
                      rf_idx=rf_idx, rf_nu=rf_nu, rr_idx=rr_idx, rr_nu=rr_nu,
                      arr=arr, arr0=arr0, troe=troe, eff_ptr=eff_ptr,
                      eff_idx=np.array(eff_idx, dtype=np.int32),
-                     eff_val=np.array(eff_val, dtype=np.float64))
+                     eff_val=np.array(eff_val, dtype=np.float64), cp_src=cp_src)
     mech.validate()
     return mech
 

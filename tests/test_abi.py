@@ -104,3 +104,11 @@ def test_mech_create_checks_sri_and_plog(lib):
     h = ctypes.c_void_p()
     assert lib.cg_mech_create(ctypes.byref(d), ctypes.byref(h)) == chemgb.CG_EINVAL
     assert b"SRI but sri is NULL" in lib.cg_last_error()
+
+
+def test_binding_refuses_other_thermo_degrees():
+    """The CUDA library evaluates the n_p = 4 (NASA-7) polynomial; a mechanism
+    refitted to another degree is refused before anything reaches it."""
+    m7 = inputs.with_thermo_degree(inputs.gen_mechanism("h2"), 7)
+    with pytest.raises(NotImplementedError):
+        chemgb.cg_mech_create(m7)

@@ -83,6 +83,22 @@ def test_generator_is_seeded():
     assert not np.array_equal(a.arr, c.arr)
 
 
+def test_mechanism_save_load_keeps_thermo_degree(tmp_path):
+    """A refitted mechanism (c_p polynomial of degree 7) and its source
+    curves survive save and load; a NASA-7 mechanism comes back without a
+    refit."""
+    m = inputs.gen_mechanism("h2")
+    m7 = inputs.with_thermo_degree(m, 7)
+    assert m7.thermo_np == 7 and m7.thermo.shape == (m.ns, 10) and m.thermo_np == 4
+    for mech, name in ((m, "a.npz"), (m7, "b.npz")):
+        mech.save(str(tmp_path / name))
+        back = inputs.Mechanism.load(str(tmp_path / name))
+        assert back.thermo_np == mech.thermo_np
+        np.testing.assert_array_equal(back.thermo_coef, mech.thermo_coef)
+        np.testing.assert_array_equal(back.cp_src, mech.cp_src)
+        np.testing.assert_array_equal(back.arr, mech.arr)
+
+
 def test_fields():
     m = inputs.gen_mechanism("ch4")
     T, Y, p = inputs.field_flames(m, 10000, seed=0)

@@ -5,10 +5,9 @@ no arithmetic of the integration method itself: it never evaluates
 thermodynamic properties of cells, rates, source terms or Jacobians. It
 draws mechanism parameters (and fits the c_p polynomials of a mechanism to
 its drawn curves, anchored at 298.15 K) and cell states from seeded
-distributions shaped like
-the workloads the paper studies (Table 2: mechanisms of 10-96 species and
-27-1054 reactions; Section 5.1 random-state recipe; Section 5.3 homogeneous
-reactor initial conditions).
+distributions shaped like the workloads the paper studies (Table 2:
+mechanisms of 10-96 species and 27-1054 reactions; Section 5.1 random-state
+recipe; Section 5.3 homogeneous reactor initial conditions).
 
 Units are SI-kmol throughout: concentrations in kmol/m^3, activation
 energies in J/kmol, pressures in Pa, molecular masses in kg/kmol, and the

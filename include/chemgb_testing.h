@@ -1,6 +1,8 @@
 /*
  * chemgb test hooks (C ABI). Not part of the method: entry points that let
- * the tests check device functions of the library against CUDA's own.
+ * the tests check device functions of the library against CUDA's own, and
+ * the host-side planners of the kernels (assembly schedules, reaction
+ * chunks, per-cell memory layout) without a GPU.
  */
 #ifndef CHEMGB_TESTING_H
 #define CHEMGB_TESTING_H
@@ -19,6 +21,48 @@ extern "C" {
  * `stream`. Errors: CG_EINVAL (NULL mechanism or arrays, n < 0), CG_ECUDA. */
 cg_status cgx_exp_check(const cg_mech *mech, int64_t n, const double *x, double *y_tab, double *y_lib,
                         void *stream);
+
+/* The thread-owned assembly schedule the kernels walk to form sparse sums
+ * out[dst] += fac * in[src] (the production rates omega_i = sum_j nu_ij q_j
+ * of Section 2.2 and the Jacobian entries of Section 3.2). Host only.
+ * Input: n_terms terms (dst, src, fac, order); terms of one destination are
+ * summed in increasing `order`. dst must lie in [0, 2^29 - 1].
+ * Output: *len = terms per lane. If the four arrays are non-NULL (all or
+ * none), slot t of lane l, at [t * lanes + l] for t < *len, receives the
+ * destination, flags (bit 0: the first term of the destination's run,
+ * bit 1: its last), source and factor; padding slots after a lane's last
+ * run hold 0, 0, 0, 0.0. capacity: the arrays' length, at least
+ * *len * lanes. Errors: CG_EINVAL (bad counts, NULL input arrays, a
+ * destination out of range), CG_ECAPACITY (capacity too small). */
+cg_status cgx_schedule(int64_t n_terms, const int *dst, const int *src, const double *fac, const int64_t *order,
+                       int lanes, int *len, int *sdst, int *sflags, int *ssrc, double *sfac, int64_t capacity);
+
+/* The reaction chunks of the rate loop for teams of `team` threads (32, 64,
+ * 128 or 256): runs of at most 32 consecutive reactions of one kind
+ * (elementary and third-body; falloff; PLOG; rxn_type[nr] holds the
+ * CG_RXN_* codes in the library's internal order) dealt to the team's warps.
+ * Host only. Writes *n_chunks and warp_ptr[team / 32 + 1] (warp w takes
+ * chunks warp_ptr[w] .. warp_ptr[w + 1] - 1); if first and len are non-NULL
+ * (both or neither, `capacity` entries), chunk c covers reactions first[c]
+ * .. first[c] + len[c] - 1. Errors: CG_EINVAL, CG_ECAPACITY. */
+cg_status cgx_rate_chunks(int nr, const int *rxn_type, int team, int *n_chunks, int *warp_ptr, int *first,
+                          int *len, int capacity);
+
+/* The per-cell memory layout for ns species and nr reactions: which arrays
+ * of a cell's working set go to shared memory (at most smem_limit bytes per
+ * cell, 1 KiB of it kept free) and which to the cell's global scratch slot.
+ * mat_bytes: 8 (FP64 Newton matrix) or 4 (FP32); adjoint: non-zero adds the
+ * backward sweep's arrays; gmres_m: the GMRES restart length, 0 for the LU.
+ * Host only. Writes *ld (row stride of the Newton matrix), *n_arrays (at
+ * most 32) and, per array a, offset[a] and size[a] in doubles within its
+ * space and in_global[a] (0 shared, 1 global); priority[k] is the array
+ * placed k-th (shared memory is filled in this order until one does not
+ * fit; it and all later ones go to global scratch, except the reduction
+ * scratch, which is always shared); *smem_doubles and *global_doubles are
+ * the totals. Arrays of 32 ints. Errors: CG_EINVAL. */
+cg_status cgx_layout(int ns, int nr, int mat_bytes, int64_t smem_limit, int adjoint, int gmres_m, int *ld,
+                     int *n_arrays, int *offset, int *size, int *in_global, int *priority, int *smem_doubles,
+                     int *global_doubles);
 
 #ifdef __cplusplus
 }

@@ -55,7 +55,8 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_eval_rates", "cg_eval_jacobian", "cg_temperature_from_energy",
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
-            "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split")
+            "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
+            "cgx_schedule", "cgx_rate_chunks", "cgx_layout")
 
 
 def library_path() -> str:
@@ -98,6 +99,9 @@ def load(build_if_missing: bool = False):
                                          P, P]
     lib.cg_mech_set_arrhenius.argtypes = [P, P]
     lib.cgx_exp_check.argtypes = [P, L, P, P, P, P]
+    lib.cgx_schedule.argtypes = [L, P, P, P, P, I, P, P, P, P, P, L]
+    lib.cgx_rate_chunks.argtypes = [I, P, I, P, P, P, P, I]
+    lib.cgx_layout.argtypes = [I, I, I, L, I, I] + [P] * 8
     lib.cg_react_split.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, I, P, P, P]
     lib.cg_last_error.restype = ctypes.c_char_p
     lib.cg_last_error.argtypes = []
@@ -279,6 +283,49 @@ def cg_react_split(h, opts, rho, e, rhoY, T, R, iters=5, status=None, stats=None
 def cgx_exp_check(h, x, y_tab, y_lib, stream=None):
     """Test hook: the library's table-driven exp and CUDA's exp of x."""
     _check(load().cgx_exp_check(h.ptr, x.shape[0], _dev(x), _dev(y_tab), _dev(y_lib), _stream(stream)))
+
+
+def cgx_schedule(dst, src, fac, order, lanes: int):
+    """Test hook (host only): the thread-owned assembly schedule of the terms
+    out[dst] += fac * in[src]; returns (len, dst, flags, src, fac), each of
+    the four arrays [len, lanes] (slot t of lane l at [t, l])."""
+    lib = load()
+    dst, src = np.ascontiguousarray(dst, np.int32), np.ascontiguousarray(src, np.int32)
+    fac, order = np.ascontiguousarray(fac, np.float64), np.ascontiguousarray(order, np.int64)
+    n = ctypes.c_int(0)
+    _check(lib.cgx_schedule(len(dst), _ptr(dst), _ptr(src), _ptr(fac), _ptr(order), lanes, ctypes.byref(n),
+                            None, None, None, None, 0))
+    slots = n.value * lanes
+    out = [np.zeros(slots, np.int32), np.zeros(slots, np.int32), np.zeros(slots, np.int32), np.zeros(slots)]
+    _check(lib.cgx_schedule(len(dst), _ptr(dst), _ptr(src), _ptr(fac), _ptr(order), lanes, ctypes.byref(n),
+                            *[_ptr(a) for a in out], slots))
+    return (n.value,) + tuple(a.reshape(n.value, lanes) for a in out)
+
+
+def cgx_rate_chunks(rxn_type, team: int):
+    """Test hook (host only): the rate loop's reaction chunks; returns
+    (warp_ptr, first, len)."""
+    lib = load()
+    t = np.ascontiguousarray(rxn_type, np.int32)
+    n = ctypes.c_int(0)
+    ptr = np.zeros(team // 32 + 1, np.int32)
+    _check(lib.cgx_rate_chunks(len(t), _ptr(t), team, ctypes.byref(n), _ptr(ptr), None, None, 0))
+    first, ln = np.zeros(n.value, np.int32), np.zeros(n.value, np.int32)
+    _check(lib.cgx_rate_chunks(len(t), _ptr(t), team, ctypes.byref(n), _ptr(ptr), _ptr(first), _ptr(ln), n.value))
+    return ptr, first, ln
+
+
+def cgx_layout(ns: int, nr: int, mat_bytes: int, smem_limit: int, adjoint: bool = False, gmres_m: int = 0) -> dict:
+    """Test hook (host only): one cell's memory layout; returns ld, and per
+    array offset, size, in_global, plus the priority order and the totals (in
+    doubles)."""
+    lib = load()
+    ints = [np.zeros(1, np.int32) for _ in range(2)] + [np.zeros(32, np.int32) for _ in range(4)] + \
+        [np.zeros(1, np.int32) for _ in range(2)]
+    _check(lib.cgx_layout(ns, nr, mat_bytes, int(smem_limit), int(adjoint), gmres_m, *[_ptr(a) for a in ints]))
+    k = int(ints[1][0])
+    return dict(ld=int(ints[0][0]), offset=ints[2][:k], size=ints[3][:k], in_global=ints[4][:k].astype(bool),
+                priority=ints[5][:k], smem=int(ints[6][0]), glob=int(ints[7][0]))
 
 
 class MechHandle:

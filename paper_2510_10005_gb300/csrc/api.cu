@@ -106,8 +106,11 @@ Schedule make_schedule(std::vector<Term> terms, int lanes_n) {
 // Place one cell's arrays: hottest first into shared memory (at most
 // smem_limit bytes per cell), the rest into the cell's global scratch slot.
 // mat_bytes: 8 for the FP64 Newton matrix, 4 for the FP32 one; adjoint:
-// add the arrays of the backward sweep (size 0 otherwise).
-Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoint = false, int gmres_m = 0) {
+// add the arrays of the backward sweep (size 0 otherwise). sizes_out and
+// order_out (A_COUNT entries each, may be NULL) receive the placed size of
+// every array and the priority order.
+Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoint = false, int gmres_m = 0,
+                   int* sizes_out = nullptr, int* order_out = nullptr) {
     using namespace cg;
     const int n = ns + 1;
     Layout L;
@@ -147,6 +150,8 @@ Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoin
             go += sz;
             L.gmask |= 1u << a;
         }
+        if (sizes_out) sizes_out[a] = sz;
+        if (order_out) order_out[k] = a;
     }
     L.stotal = so;
     L.gtotal = go;
@@ -571,6 +576,71 @@ cg_status cgx_exp_check(const cg_mech* m, int64_t n, const double* x, double* y_
     if (!m || n < 0 || (n > 0 && (!x || !y_tab || !y_lib))) return fail(CG_EINVAL, "bad arguments");
     cudaError_t e = cg::launch_exp_check(m->dm, n, x, y_tab, y_lib, (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "exp check launch");
+}
+
+// ---------------------------------------------------------------------------
+// Test hooks on the host-side planners (no device work).
+
+cg_status cgx_schedule(int64_t n_terms, const int* dst, const int* src, const double* fac, const int64_t* order,
+                       int lanes, int* len, int* sdst, int* sflags, int* ssrc, double* sfac, int64_t capacity) {
+    if (n_terms < 0 || lanes < 1 || lanes > 1024 || !len || (n_terms > 0 && (!dst || !src || !fac || !order)))
+        return fail(CG_EINVAL, "bad arguments");
+    std::vector<Term> terms((size_t)n_terms);
+    for (int64_t i = 0; i < n_terms; ++i) {
+        if (dst[i] < 0 || dst[i] > cg::kSchedIndex) return fail(CG_EINVAL, "destination %d out of range", dst[i]);
+        terms[(size_t)i] = {dst[i], src[i], fac[i], (long)order[i]};
+    }
+    const Schedule s = make_schedule(terms, lanes);
+    *len = s.len;
+    if (!sdst && !sflags && !ssrc && !sfac) return CG_OK;
+    const int64_t slots = (int64_t)s.len * lanes;
+    if (!sdst || !sflags || !ssrc || !sfac) return fail(CG_EINVAL, "output arrays: all or none");
+    if (capacity < slots) return fail(CG_ECAPACITY, "the schedule has %lld slots", (long long)slots);
+    for (int64_t k = 0; k < slots; ++k) {
+        const int d = s.dst[(size_t)k];
+        sdst[k] = d & cg::kSchedIndex;
+        sflags[k] = ((d & cg::kSchedFirst) ? 1 : 0) | ((d & cg::kSchedLast) ? 2 : 0);
+        ssrc[k] = s.src[(size_t)k];
+        sfac[k] = s.fac[(size_t)k];
+    }
+    return CG_OK;
+}
+
+cg_status cgx_rate_chunks(int nr, const int* rxn_type, int team, int* n_chunks, int* warp_ptr, int* first,
+                          int* len, int capacity) {
+    if (nr < 0 || (nr > 0 && !rxn_type) || !n_chunks || !warp_ptr ||
+        (team != 32 && team != 64 && team != 128 && team != 256))
+        return fail(CG_EINVAL, "bad arguments");
+    std::vector<int> itype(rxn_type, rxn_type + nr), ptr, f, l;
+    make_rate_chunks(itype, team, ptr, f, l);
+    *n_chunks = (int)f.size();
+    for (size_t w = 0; w < ptr.size(); ++w) warp_ptr[w] = ptr[w];
+    if (!first && !len) return CG_OK;
+    if (!first || !len) return fail(CG_EINVAL, "output arrays: both or none");
+    if (capacity < (int)f.size()) return fail(CG_ECAPACITY, "%zu chunks", f.size());
+    for (size_t c = 0; c < f.size(); ++c) {
+        first[c] = f[c];
+        len[c] = l[c];
+    }
+    return CG_OK;
+}
+
+cg_status cgx_layout(int ns, int nr, int mat_bytes, int64_t smem_limit, int adjoint, int gmres_m, int* ld,
+                     int* n_arrays, int* offset, int* size, int* in_global, int* priority, int* smem_doubles,
+                     int* global_doubles) {
+    if (ns < 1 || nr < 0 || (mat_bytes != 4 && mat_bytes != 8) || smem_limit < 0 || gmres_m < 0 || !ld ||
+        !n_arrays || !offset || !size || !in_global || !priority || !smem_doubles || !global_doubles)
+        return fail(CG_EINVAL, "bad arguments");
+    const Layout L = make_layout(ns, nr, mat_bytes, (size_t)smem_limit, adjoint != 0, gmres_m, size, priority);
+    *ld = L.ld;
+    *n_arrays = cg::A_COUNT;
+    for (int a = 0; a < cg::A_COUNT; ++a) {
+        offset[a] = L.off[a];
+        in_global[a] = (L.gmask >> a) & 1u;
+    }
+    *smem_doubles = L.stotal;
+    *global_doubles = L.gtotal;
+    return CG_OK;
 }
 
 void cg_mech_destroy(cg_mech* m) {

@@ -5,6 +5,7 @@ high pressure limits, Troe at f1 = 0, the extreme Troe parameters of
 Appendix C.1, the reverse reaction's equilibrium constant, and conservation
 of mass and of every element by omega."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -218,3 +219,45 @@ def test_conp_keeps_pressure_and_enthalpy_rates_zero(mechs, ref):
                                    atol=1e-13 * np.abs(w).max())
         dH = np.sum(m.W * th["h"] * w) + np.sum(m.W * C[c] * th["cp"]) * wT
         assert abs(dH) <= 1e-12 * np.abs(m.W * th["h"] * w).sum()
+
+
+def _golden_h_o2():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "h_o2_section_4_3.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    (name, A, b, Ea), = rows
+    return name, float(A), float(b), float(Ea)
+
+
+def test_golden_h_o2_example_of_section_4_3(mechs):
+    """The printed example of the generation process (Section 4.3): H + O2
+    <=> O + OH with A = 1.0399e11 m^3/kmol/s, b = 0, Ea = 6.405704e7 J/kmol
+    in SI-kmol units. The oracle's k_f is A exp(-Ea/(R T)) at every T, and
+    the rate of progress is the printed form [H][O2] k_f - [O][OH] k_f / K
+    with K = exp(-Delta G/RT) and no pressure factor (sum nu = 0)."""
+    name, A, b, Ea = _golden_h_o2()
+    assert name == "H+O2<=>O+OH"
+    m = mechs["h2"].copy()
+    sp = {s: m.index(s) for s in ("H", "O2", "O", "OH")}
+    m.rtype[0] = inputs.RXN_ELEMENTARY
+    m.rf_idx[0], m.rf_nu[0] = [sp["H"], sp["O2"], -1], [1, 1, 0]
+    m.rr_idx[0], m.rr_nu[0] = [sp["O"], sp["OH"], -1], [1, 1, 0]
+    m.arr[0] = (math.log(A), b, Ea)
+    m.eff_idx = m.eff_idx[m.eff_ptr[1] - m.eff_ptr[0]:]
+    m.eff_val = m.eff_val[m.eff_ptr[1] - m.eff_ptr[0]:]
+    m.eff_ptr = m.eff_ptr - m.eff_ptr[1]
+    m.eff_ptr[0] = 0
+    m.validate()
+    r = oracle.RefMech(m)
+    T, C, p = inputs.random_states(m, 4, seed=11)
+    for Tc in (800.0, 1500.0, 2500.0):
+        for c in range(4):
+            kf, kr, q = r.rates(Tc, C[c])
+            assert kf[0] == pytest.approx(A * math.exp(-Ea / (R * Tc)), rel=1e-13)
+            g = r.thermo(Tc)["g"]
+            dG = (m.W[sp["O"]] * g[sp["O"]] + m.W[sp["OH"]] * g[sp["OH"]]
+                  - m.W[sp["H"]] * g[sp["H"]] - m.W[sp["O2"]] * g[sp["O2"]])
+            K = math.exp(-dG / (R * Tc))
+            expect = C[c, sp["H"]] * C[c, sp["O2"]] * kf[0] - C[c, sp["O"]] * C[c, sp["OH"]] * kf[0] / K
+            assert q[0] == pytest.approx(expect, rel=1e-10, abs=1e-12 * abs(kf[0] * C[c, sp["H"]] * C[c, sp["O2"]]))
+    # about 4.7e7 m^3/kmol/s at 1000 K (1.0399e11 e^-7.70)
+    assert r.rates(1000.0, C[0])[0][0] == pytest.approx(4.7e7, rel=0.02)

@@ -6,11 +6,15 @@
  * the state of a cell is y = (T, C_1..C_ns) (Section 3, eq.
  * extracted_problem-1), its right-hand side S(y) = (omega_T, dC/dt) is built
  * from NASA-7 thermodynamics (Section 2.1, Table 1), Gibbs-based equilibrium
- * constants and Arrhenius / third-body / Troe rates (Section 2.2), and a cell
- * is advanced over dt with backward Euler + Newton (Section 3.2) or an SDIRK
- * scheme in stage-derivative form (Appendix A), each Newton step solving
- * (I - gamma h J) delta = -f with the analytical Jacobian J (Section 3.2) and
- * a dense LU with partial pivoting (Section 3.4).
+ * constants and Arrhenius, third-body, Lindemann / Troe / SRI falloff and
+ * PLOG rates (Section 2.2), and a cell is advanced over dt with backward
+ * Euler + Newton (Section 3.2), an SDIRK scheme in stage-derivative form
+ * (Appendix A.1, A.2), second-order Rosenbrock (Appendix A.3) or YASS
+ * (Appendix A.4), each linear system (I - gamma h J) delta = -f taking the
+ * analytical Jacobian J (Section 3.2) and a dense LU with partial pivoting
+ * or restarted, preconditioned GMRES (Section 3.4). cg_react_split is the
+ * operator-split call of a compressible flow solver (Section 5.5), and
+ * cg_integrate_ckpt / cg_integrate_adjoint differentiate the integration.
  *
  * Conventions shared by every entry point:
  *   - Units are SI-kmol: C in kmol/m^3, T in K, p in Pa, rho in kg/m^3,
@@ -102,7 +106,9 @@ enum { CG_PC_NONE = 0, CG_PC_JACOBI = 1, CG_PC_GAUSS_SEIDEL = 2 };
  * with at most three distinct species on each side.
  *   W[ns]           molecular masses
  *   nasa7[ns*7]     a1..a5 (c_p/R polynomial), a6 (h/R constant), a7 (s/R
- *                   constant); one range used at every temperature
+ *                   constant); one range used at every temperature. This
+ *                   is the n_p = 4 case of eq. specific_heat_polynomial;
+ *                   the library takes no other degree.
  *   rxn_type[nr]    CG_RXN_*
  *   reversible[nr]  0 or 1; reverse rate k_f / K_c (eq. reverse_rate)
  *   rf_idx/rf_nu[nr*3]  reactant species and integer coefficients (-1 / 0 pad)

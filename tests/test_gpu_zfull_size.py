@@ -101,10 +101,11 @@ def test_full_size_adjoint():
     rng = np.random.default_rng(4)
     gT = rng.normal(size=N)
     dT0, dY0 = torch.empty(N, dtype=F64, device=DEV), torch.empty((m.ns, N), dtype=F64, device=DEV)
+    dth = torch.empty((m.nr, 3), dtype=F64, device=DEV)
     dcell = torch.empty((m.nr, 3, N), dtype=F64, device=DEV)
     ast = torch.empty(N, dtype=torch.int32, device=DEV)
     chemgb.cg_integrate_adjoint(h, og, ckpt, ckpt_n, _dev(gT), torch.zeros((m.ns, N), dtype=F64, device=DEV),
-                                dT0, dY0, None, dcell, ast)
+                                dT0, dY0, dth, dcell, ast)
     torch.cuda.synchronize()
     assert int((st != 0).sum()) == 0 and int((ast != 0).sum()) == 0
     idx = np.linspace(0, N - 1, 8).astype(np.int64)

@@ -112,3 +112,11 @@ def test_binding_refuses_other_thermo_degrees():
     m7 = inputs.with_thermo_degree(inputs.gen_mechanism("h2"), 7)
     with pytest.raises(NotImplementedError):
         chemgb.cg_mech_create(m7)
+
+
+def test_rate_probe_checks_arguments(lib):
+    """The throughput probe refuses bad arguments before any device work."""
+    r = ctypes.c_double(0.0)
+    for kind, lanes, iters in ((5, 32, 10), (-1, 32, 10), (0, 0, 10), (0, 33, 10), (0, 32, 0), (0, 32, 1 << 40)):
+        assert lib.cgx_rate_probe(kind, lanes, iters, ctypes.byref(r), None) == chemgb.CG_EINVAL
+    assert lib.cgx_rate_probe(0, 32, 10, None, None) == chemgb.CG_EINVAL

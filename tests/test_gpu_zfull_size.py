@@ -10,7 +10,9 @@ benchmark times, on sampled outputs the oracle computes cell by cell:
 * the adjoint workload, 65,536 cells over 1e-4 s: sampled dL/dT0, dL/dY0 and
   per-cell dL/dtheta within 1e-6 of the largest entry of each kind.
 
-Slow (about a minute and a half): collected after the other GPU tests."""
+Slow: a 1,048,576-cell launch takes about 45 s, the batch about 30 s plus
+the autotuning, the adjoint about 15 s. Collected after the other GPU
+tests."""
 import os
 
 import numpy as np

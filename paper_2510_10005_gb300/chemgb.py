@@ -56,7 +56,7 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
             "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
-            "cgx_schedule", "cgx_rate_chunks", "cgx_layout")
+            "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo")
 
 
 def library_path() -> str:
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = False):
     lib.cg_integrate_adjoint.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, I, P, P, P, P, P, P,
                                          P, P]
     lib.cg_mech_set_arrhenius.argtypes = [P, P]
+    lib.cg_mech_set_thermo.argtypes = [P, I, P]
     lib.cgx_exp_check.argtypes = [P, L, P, P, P, P]
     lib.cgx_schedule.argtypes = [L, P, P, P, P, I, P, P, P, P, P, L]
     lib.cgx_rate_chunks.argtypes = [I, P, I, P, P, P, P, I]
@@ -265,6 +266,15 @@ def cg_integrate_adjoint(h, opts, ckpt, ckpt_n, dT_end, dY_end, dT0, dY0, dtheta
                                        None if status is None else _dev(status, "int32"), _stream(stream)))
 
 
+def cg_mech_set_thermo(h, coef):
+    """Thermodynamics of another degree: coef [ns, n_p + 3] (a_0..a_np of
+    c_p/R, then the h/R and s/R constants)."""
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    if c.ndim != 2 or c.shape[0] != h.ns or c.shape[1] < 3:
+        raise ValueError(f"coef must be [{h.ns}, n_p + 3]")
+    _check(load().cg_mech_set_thermo(h.ptr, c.shape[1] - 3, c.ctypes.data))
+
+
 def cg_mech_set_arrhenius(h, arr):
     """Replace (ln A, b, Ea) of every reaction (host array [nr, 3])."""
     a = np.ascontiguousarray(arr, dtype=np.float64).reshape(h.nr, 3)
@@ -333,14 +343,11 @@ class MechHandle:
 
     def __init__(self, mech):
         thermo = getattr(mech, "thermo", None)
-        if thermo is not None and thermo.shape[1] != 7:
-            raise NotImplementedError(f"c_p polynomial of degree {thermo.shape[1] - 3}: the CUDA library "
-                                      "evaluates the n_p = 4 (NASA-7) form only")
         lib = load()
         f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
         i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
         self._keep = dict(
-            W=f64(mech.W), nasa7=f64(mech.nasa7 if thermo is None else thermo), rxn_type=i32(mech.rtype), reversible=i32(mech.reversible),
+            W=f64(mech.W), nasa7=f64(mech.nasa7 if thermo is None or thermo.shape[1] != 7 else thermo), rxn_type=i32(mech.rtype), reversible=i32(mech.reversible),
             rf_idx=i32(mech.rf_idx), rf_nu=i32(mech.rf_nu), rr_idx=i32(mech.rr_idx), rr_nu=i32(mech.rr_nu),
             arr=f64(mech.arr), arr0=f64(mech.arr0), troe=f64(mech.troe), eff_ptr=i32(mech.eff_ptr),
             eff_idx=i32(mech.eff_idx) if len(mech.eff_idx) else np.zeros(1, np.int32),
@@ -356,6 +363,8 @@ class MechHandle:
         self.ns, self.nr, self.n = mech.ns, mech.nr, mech.ns + 1
         self.mech = mech
         self.arr = np.array(self._keep["arr"]).reshape(mech.nr, 3)   # current (ln A, b, Ea)
+        if thermo is not None and thermo.shape[1] != 7:   # a c_p polynomial of another degree
+            cg_mech_set_thermo(self, thermo)
 
     def close(self):
         if getattr(self, "ptr", None):

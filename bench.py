@@ -288,9 +288,11 @@ def oracle_opts(o: dict) -> dict:
     return {k: v for k, v in o.items() if k not in ("precision", "persistent")}
 
 
-def cpu_oracle_sample(parts, opts, n_sample: int, threads: int):
+def cpu_oracle_sample(parts, opts, n_sample: int, threads: int, split: bool = False):
     """Time the oracle on an evenly spaced sample of every mechanism's cells
-    (shares in proportion to the cells); returns (cells/s, seconds, cells)."""
+    (shares in proportion to the cells); returns (cells/s, seconds, cells).
+    split: the operator-split step (T from the conserved variables, then the
+    constant-volume integration) instead of the integration alone."""
     import oracle
     total = sum(len(T) for _, T, _, _ in parts)
     t, done = 0.0, 0
@@ -298,11 +300,27 @@ def cpu_oracle_sample(parts, opts, n_sample: int, threads: int):
         k = max(1, int(round(n_sample * len(T) / total)))
         idx = np.linspace(0, len(T) - 1, k).astype(np.int64)
         r = oracle.RefMech(m)
-        t0 = time.perf_counter()
-        r.integrate(T[idx], Y[idx], p[idx], oracle_opts(opts), nthreads=threads)
+        if split:
+            rho, u, rhoY = flow_state(m, T[idx], Y[idx], p[idx])
+            t0 = time.perf_counter()
+            r.react_split(rho, u, rhoY, T[idx], oracle_opts(opts), nthreads=threads)
+        else:
+            t0 = time.perf_counter()
+            r.integrate(T[idx], Y[idx], p[idx], oracle_opts(opts), nthreads=threads)
         t += time.perf_counter() - t0
         done += k
     return done / t, t, done
+
+
+def full_workload_name(args) -> str:
+    """The workload as both arms state it, with every option that changes it."""
+    return (workload_name(args.config, args.method, args.linear, args.prec)
+            + ("; operator-split surface: (rho, u, rho Y) in, T recovered (5 Newton iterations), "
+               "constant volume, T and R out" if args.surface == "split" else "")
+            + ("; mechanism with nr/40 Troe reactions made SRI and nr/16 elementary reactions made "
+               "PLOG (3-6 levels, 0.1-100 atm)" if args.sri_plog else "")
+            + (f"; thermodynamics refitted with a c_p polynomial of degree {args.thermo_degree}"
+               if getattr(args, "thermo_degree", None) is not None else ""))
 
 
 def dist_env():
@@ -317,12 +335,17 @@ def run_reference(args):
     cfg = CONFIGS[args.config]
     parts = workload_variant(make_workload(args.config, args.cells or cfg["cells"]), args)
     opts = opts_dict(args.config, 0, args.method, args.linear, args.prec)
+    split = args.surface == "split"
+    if split:
+        if len(parts) != 1:
+            raise SystemExit("--surface split takes one mechanism")
+        opts["reactor"] = 0   # the split step is at constant volume
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
-        cpu_oracle_sample(parts, opts, max(16, args.ref_sample // 8), threads)
+        cpu_oracle_sample(parts, opts, max(16, args.ref_sample // 8), threads, split)
     times, cells = [], 0
     for _ in range(args.steps):
-        v, el, k = cpu_oracle_sample(parts, opts, args.ref_sample, threads)
+        v, el, k = cpu_oracle_sample(parts, opts, args.ref_sample, threads, split)
         times.append(el)
         cells += k
     value = cells / sum(times)
@@ -330,8 +353,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(args.config, args.method, args.linear, args.prec),
-                                        "config": args.config},
+        "data": "synthetic", "config": {"workload": full_workload_name(args), "config": args.config},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.ref_sample} cells evenly spaced through the field, per step"},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -495,7 +517,7 @@ def run_gpu(args):
     cpu = None
     if ws == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
-        v, el, k = cpu_oracle_sample(parts, opts_d, args.cpu_sample, threads)
+        v, el, k = cpu_oracle_sample(parts, opts_d, args.cpu_sample, threads, split)
         cpu = {"value": v, "unit": "cells/s", "cores": threads, "kind": "oracle",
                "sample": f"{k} cells evenly spaced through the field ({el:.1f} s)"}
     state_bytes = sum(len(T) * (m.ns + 2) * 8 for m, T, _, _ in parts)
@@ -503,13 +525,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.config, args.method, args.linear, args.prec)
-                   + ("; operator-split surface: (rho, u, rho Y) in, T recovered (5 Newton iterations), "
-                      "constant volume, T and R out" if split else "")
-                   + ("; mechanism with nr/40 Troe reactions made SRI and nr/16 elementary reactions made "
-                      "PLOG (3-6 levels, 0.1-100 atm)" if args.sri_plog else "")
-                   + (f"; thermodynamics refitted with a c_p polynomial of degree {args.thermo_degree}"
-                      if args.thermo_degree is not None else ""),
+        "config": {"workload": full_workload_name(args),
                    "config": args.config,
                    "cells_per_gpu": N_total,
                    "newton_matrix": "fp32" if precision == 1 else "fp64", "state_bytes": state_bytes,

@@ -39,3 +39,20 @@ def test_flops_per_newton_formula():
         pytest.approx(8 * n * n + 2 * j + 30 * m.nr + 40 * m.ns)
     assert 150_000 < bench.algorithmic_flops_per_newton(m.ns, m.nr, j, False) < 160_000
 
+
+
+def test_reference_arm_takes_the_workload_options(capsys, monkeypatch):
+    """--surface split and --sri-plog change the reference arm's workload
+    (the oracle's split step on an SRI/PLOG mechanism) and its stated
+    workload, exactly as they change the GPU arm's."""
+    import argparse
+    import json
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+    args = argparse.Namespace(config=1, cells=64, method=None, linear=None, prec=None, surface="split",
+                              sri_plog=True, thermo_degree=None, ref_sample=8, steps=1, warmup=0, gpus=1)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["config"]["workload"] == bench.full_workload_name(args)
+    assert "operator-split" in line["config"]["workload"] and "PLOG" in line["config"]["workload"]
+    assert line["value"] > 0

@@ -56,7 +56,8 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
             "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
-            "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo")
+            "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo",
+            "cgx_thermo_table")
 
 
 def library_path() -> str:
@@ -99,6 +100,7 @@ def load(build_if_missing: bool = False):
                                          P, P]
     lib.cg_mech_set_arrhenius.argtypes = [P, P]
     lib.cg_mech_set_thermo.argtypes = [P, I, P]
+    lib.cgx_thermo_table.argtypes = [I, I, P, P, P, L]
     lib.cgx_exp_check.argtypes = [P, L, P, P, P, P]
     lib.cgx_schedule.argtypes = [L, P, P, P, P, I, P, P, P, P, P, L]
     lib.cgx_rate_chunks.argtypes = [I, P, I, P, P, P, P, I]
@@ -323,6 +325,19 @@ def cgx_rate_chunks(rxn_type, team: int):
     first, ln = np.zeros(n.value, np.int32), np.zeros(n.value, np.int32)
     _check(lib.cgx_rate_chunks(len(t), _ptr(t), team, ctypes.byref(n), _ptr(ptr), _ptr(first), _ptr(ln), n.value))
     return ptr, first, ln
+
+
+def cgx_thermo_table(coef):
+    """Test hook (host only): the device thermo table for coef [ns, n_p + 3];
+    returns (P, table [4 P + 1, ns])."""
+    lib = load()
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    ns, np_ = c.shape[0], c.shape[1] - 3
+    P = ctypes.c_int(0)
+    _check(lib.cgx_thermo_table(ns, np_, c.ctypes.data, ctypes.byref(P), None, 0))
+    t = np.zeros((4 * P.value + 1) * ns)
+    _check(lib.cgx_thermo_table(ns, np_, c.ctypes.data, ctypes.byref(P), t.ctypes.data, t.size))
+    return P.value, t.reshape(4 * P.value + 1, ns)
 
 
 def cgx_layout(ns: int, nr: int, mat_bytes: int, smem_limit: int, adjoint: bool = False, gmres_m: int = 0) -> dict:

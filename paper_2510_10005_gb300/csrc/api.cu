@@ -1185,16 +1185,18 @@ cg_status cg_mech_set_arrhenius(cg_mech* m, const double* arr) {
     return CG_OK;
 }
 
-cg_status cg_mech_set_thermo(cg_mech* m, int np, const double* coef) {
-    if (!m) return fail(CG_EINVAL, "mech is NULL");
+namespace {
+
+// The device thermo table of a c_p polynomial of degree np (layout of
+// cg::th_rows); returns the table's degree P = max(np, 4), since degrees
+// below 4 are the NASA-7 form with zero upper coefficients.
+cg_status thermo_table(int ns, int np, const double* coef, int* P_out, std::vector<double>& th) {
     if (np < 0 || np > kMaxThermoDegree) return fail(CG_EINVAL, "degree %d outside [0, %d]", np, kMaxThermoDegree);
-    const int ns = m->ns;
-    if (!coef) return fail(CG_EINVAL, "coef is NULL");
+    if (ns > 0 && !coef) return fail(CG_EINVAL, "coef is NULL");
     for (int k = 0; k < ns * (np + 3); ++k)
         if (!std::isfinite(coef[k])) return fail(CG_EINVAL, "coef[%d] not finite", k);
-    // degrees below 4 are the NASA-7 form with zero upper coefficients
     const int P = std::max(np, 4);
-    std::vector<double> th((size_t)cg::th_rows(P) * ns, 0.0);
+    th.assign((size_t)cg::th_rows(P) * ns, 0.0);
     for (int i = 0; i < ns; ++i) {
         const double* c = coef + (size_t)i * (np + 3);
         auto a = [&](int k) { return k <= np ? c[k] : 0.0; };
@@ -1206,6 +1208,28 @@ cg_status cg_mech_set_thermo(cg_mech* m, int np, const double* coef) {
         T(3 * P + 1) = c[np + 2];
         for (int k = 2; k <= P; ++k) T(3 * P + k) = k * a(k);
     }
+    *P_out = P;
+    return CG_OK;
+}
+
+}  // namespace
+
+cg_status cgx_thermo_table(int ns, int np, const double* coef, int* P, double* table, int64_t capacity) {
+    if (ns < 1 || !P) return fail(CG_EINVAL, "bad arguments");
+    std::vector<double> th;
+    cg_status st = thermo_table(ns, np, coef, P, th);
+    if (st != CG_OK || !table) return st;
+    if (capacity < (int64_t)th.size()) return fail(CG_ECAPACITY, "the table has %zu entries", th.size());
+    std::copy(th.begin(), th.end(), table);
+    return CG_OK;
+}
+
+cg_status cg_mech_set_thermo(cg_mech* m, int np, const double* coef) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    std::vector<double> th;
+    int P = 4;
+    cg_status st = thermo_table(m->ns, np, coef, &P, th);
+    if (st != CG_OK) return st;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
     if ((e = cudaMemcpy(const_cast<double*>(m->dm.th), th.data(), th.size() * sizeof(double),

@@ -409,17 +409,23 @@ def run_gpu(args):
     N_total = sum(len(b["T0"]) for b in bufs)
 
     tuned = None
-    if args.config == 3 and not args.team:
+    if (args.config == 3 or args.autotune) and not args.team:
         # autotune the launch shape on the dominant mechanism, then give the
         # other one the same team size (one launch needs one team size)
         k = min(16384, len(bufs[0]["T0"]))
         sel = torch.linspace(0, len(bufs[0]["T0"]) - 1, k, device=dev).long()
+        cache = os.path.join(tempfile.mkdtemp(prefix="chemgb_tune_"), "shape.json")   # new: always tunes
         ms = chemgb.cg_autotune(handles[0], opts, bufs[0]["T0"][sel].contiguous(),
-                                bufs[0]["Y0"][:, sel].contiguous(), bufs[0]["P"][sel].contiguous())
+                                bufs[0]["Y0"][:, sel].contiguous(), bufs[0]["P"][sel].contiguous(), cache)
         team, tpb = chemgb.cg_mech_get_launch(handles[0])
         for h in handles[1:]:
             chemgb.cg_mech_set_launch(h, team, tpb if team == 32 else 1)
         tuned = {"team": team, "teams_per_block": tpb, "sample_ms": ms}
+        try:   # the shared-memory limit per cell the tuner chose
+            with open(cache) as f:
+                tuned["smem_limit"] = json.load(f)["smem_limit"]
+        except (OSError, ValueError, KeyError):
+            pass
 
     def integrate():
         for b in bufs:
@@ -785,6 +791,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--team", type=int, default=0, help="threads per cell (default: the library's choice)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the launch shape and shared-memory limit with cg_autotune (always on for config 3)")
     ap.add_argument("--tpb", type=int, default=1, help="cells per block with --team 32")
     ap.add_argument("--precision", type=int, default=None, help="0: FP64 Newton matrix, 1: FP32 LU")
     ap.add_argument("--method", choices=sorted(METHODS), default=None,

@@ -56,3 +56,22 @@ def test_reference_arm_takes_the_workload_options(capsys, monkeypatch):
     assert line["config"]["workload"] == bench.full_workload_name(args)
     assert "operator-split" in line["config"]["workload"] and "PLOG" in line["config"]["workload"]
     assert line["value"] > 0
+
+
+def test_traffic_only_for_the_captured_kernel_sources(monkeypatch):
+    """The DRAM traffic of the bench line is the ncu capture's bytes per cell
+    scaled to the launch, and null for any workload or kernel source it was
+    not taken on."""
+    import hashlib
+    import os
+    h = hashlib.sha256()
+    for f in bench.TRAFFIC_SOURCES:
+        with open(os.path.join(bench.ROOT, "paper_2510_10005_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    per = bench.TRAFFIC[2]["bytes_per_cell"]
+    assert 400 < per < 500                      # about the 440 B of state read per cell
+    monkeypatch.setitem(bench.TRAFFIC, 2, dict(bench.TRAFFIC[2], sha256=h.hexdigest()))
+    assert bench.measured_traffic(2, 1 << 20) == pytest.approx(per * (1 << 20))
+    assert bench.measured_traffic(3, 1 << 20) is None
+    monkeypatch.setitem(bench.TRAFFIC, 2, dict(bench.TRAFFIC[2], sha256="0" * 64))
+    assert bench.measured_traffic(2, 1 << 20) is None

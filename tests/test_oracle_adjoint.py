@@ -45,10 +45,10 @@ def test_sdirk_decay_closed_form(method):
     s = t["s"]
     R = lambda z: 1.0 + z * t["b"][:s] @ np.linalg.solve(np.eye(s) - z * t["A"][:s, :s], np.ones(s))
     z = -k * dt / nsub
-    dR = (R(z + 1e-30j)).imag / 1e-30 if False else (R(z * (1 + 1e-7)) - R(z * (1 - 1e-7))) / (2e-7 * z)
-    expect = 0.03 * nsub * R(z) ** (nsub - 1) * dR * z
+    dR = R(z + 1e-30j).imag / 1e-30     # complex step: R'(z) to rounding
+    expect = 0.03 * nsub * R(z).real ** (nsub - 1) * dR * z
     assert st[0] == 0
-    assert g[0, 0, 0] == pytest.approx(expect, rel=1e-7)
+    assert g[0, 0, 0] == pytest.approx(expect, rel=1e-10)
     assert dy0[0, 1] == pytest.approx(R(z) ** nsub, rel=1e-12)
 
 

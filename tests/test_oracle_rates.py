@@ -261,3 +261,35 @@ def test_golden_h_o2_example_of_section_4_3(mechs):
             assert q[0] == pytest.approx(expect, rel=1e-10, abs=1e-12 * abs(kf[0] * C[c, sp["H"]] * C[c, sp["O2"]]))
     # about 4.7e7 m^3/kmol/s at 1000 K (1.0399e11 e^-7.70)
     assert r.rates(1000.0, C[0])[0][0] == pytest.approx(4.7e7, rel=0.02)
+
+
+@pytest.mark.parametrize("reverse", [False, True])
+def test_equilibrium_constant_sum_nu_two(mechs, reverse):
+    """The integer-power form of (p_ref/RT)^{sum nu} agrees with pow() at
+    sum nu = -2 (2 H + O <=> H2O) and +2 (the reaction reversed), which the
+    generated mechanisms never reach (Section 2.2, eq. equilibrium-constant-1)."""
+    m = mechs["h2"].copy()
+    H, O, H2O = m.index("H"), m.index("O"), m.index("H2O")
+    m.rtype[0] = inputs.RXN_ELEMENTARY
+    lhs, rhs = ([H, O, -1], [2, 1, 0]), ([H2O, -1, -1], [1, 0, 0])
+    if reverse:
+        lhs, rhs = rhs, lhs
+    m.rf_idx[0], m.rf_nu[0] = lhs
+    m.rr_idx[0], m.rr_nu[0] = rhs
+    n0 = m.eff_ptr[1] - m.eff_ptr[0]
+    m.eff_idx, m.eff_val = m.eff_idx[n0:], m.eff_val[n0:]
+    m.eff_ptr = np.concatenate([[0], m.eff_ptr[1:] - n0]).astype(np.int32)
+    m.validate()
+    r = oracle.RefMech(m)
+    nu = np.zeros(m.ns)
+    for idx, n, sgn in ((m.rf_idx[0], m.rf_nu[0], -1), (m.rr_idx[0], m.rr_nu[0], 1)):
+        for s in range(3):
+            if idx[s] >= 0:
+                nu[idx[s]] += sgn * n[s]
+    assert nu.sum() == (2 if reverse else -2)
+    T, C, _ = inputs.random_states(m, 3, seed=12)
+    for c in range(3):
+        kf, kr, _ = r.rates(T[c], C[c])
+        g = r.thermo(T[c])["g"]
+        K = np.exp(-(nu @ (m.W * g)) / (R * T[c])) * np.power(101325.0 / (R * T[c]), nu.sum())
+        assert kf[0] / kr[0] == pytest.approx(K, rel=1e-12)

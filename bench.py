@@ -312,6 +312,20 @@ def cpu_oracle_sample(parts, opts, n_sample: int, threads: int, split: bool = Fa
     return done / t, t, done
 
 
+def sized_sample(run, n_total: int, threads: int, cells: int, seconds: float):
+    """An oracle sample of `cells` cells, or, with cells = 0, of about
+    `seconds` of CPU work: a pilot of two cells per thread gives the rate,
+    then the sample that rate predicts (at most every cell). run(k) times
+    the oracle on about k evenly spaced cells and returns (seconds, cells
+    run); returns (cells run, seconds) of the sample."""
+    if cells > 0:
+        el, done = run(min(cells, n_total))
+        return done, el
+    el0, done0 = run(min(n_total, max(16, 2 * threads)))
+    el, done = run(int(min(n_total, max(done0, done0 / max(el0, 1e-9) * seconds))))
+    return done, el
+
+
 def full_workload_name(args) -> str:
     """The workload as both arms state it, with every option that changes it."""
     return (workload_name(args.config, args.method, args.linear, args.prec)
@@ -523,7 +537,10 @@ def run_gpu(args):
     cpu = None
     if ws == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
-        v, el, k = cpu_oracle_sample(parts, opts_d, args.cpu_sample, threads, split)
+        n_total = sum(len(T) for _, T, _, _ in parts)
+        k, el = sized_sample(lambda n: cpu_oracle_sample(parts, opts_d, n, threads, split)[1:], n_total, threads,
+                             args.cpu_sample, args.cpu_seconds)
+        v = k / el
         cpu = {"value": v, "unit": "cells/s", "cores": threads, "kind": "oracle",
                "sample": f"{k} cells evenly spaced through the field ({el:.1f} s)"}
     state_bytes = sum(len(T) * (m.ns + 2) * 8 for m, T, _, _ in parts)
@@ -710,13 +727,15 @@ def run_adjoint(args):
     if ws == 1 and not args.no_cpu:
         import oracle
         threads = os.cpu_count() or 1
-        k = max(1, min(args.cpu_sample // 16, N))
-        idx = np.linspace(0, N - 1, k).astype(np.int64)
         r = oracle.RefMech(m)
-        t0 = time.perf_counter()
-        r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(k), np.zeros((k, m.ns)), oracle_opts(opts_d),
-                     nthreads=threads)
-        el = time.perf_counter() - t0
+
+        def run(k):
+            idx = np.linspace(0, N - 1, k).astype(np.int64)
+            t0 = time.perf_counter()
+            r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(k), np.zeros((k, m.ns)), oracle_opts(opts_d),
+                         nthreads=threads)
+            return time.perf_counter() - t0, k
+        k, el = sized_sample(run, N, threads, args.cpu_sample, args.cpu_seconds)
         cpu = {"value": k / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
                "sample": f"{k} cells evenly spaced, forward + adjoint ({el:.1f} s)"}
     line = {
@@ -786,7 +805,10 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
     ap.add_argument("--cells", type=int, default=0, help="cells per mechanism (default: the workload's)")
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="cells of the oracle's cpu_baseline sample (0: sized for --cpu-seconds)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="CPU work of the cpu_baseline sample when --cpu-sample is 0")
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")

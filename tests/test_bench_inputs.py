@@ -75,3 +75,25 @@ def test_traffic_only_for_the_captured_kernel_sources(monkeypatch):
     assert bench.measured_traffic(3, 1 << 20) is None
     monkeypatch.setitem(bench.TRAFFIC, 2, dict(bench.TRAFFIC[2], sha256="0" * 64))
     assert bench.measured_traffic(2, 1 << 20) is None
+
+
+def test_cpu_baseline_sample_is_sized_by_time():
+    """cpu_baseline: a pilot gives the oracle's rate, and the sample is then
+    sized for the requested seconds of CPU work (capped at every cell);
+    an explicit cell count overrides the sizing."""
+    import time as _t
+    calls = []
+
+    def run(k):                       # a stand-in oracle at 1000 cells/s
+        calls.append(k)
+        return k / 1000.0, k
+    k, el = bench.sized_sample(run, 10 ** 6, 8, 0, 15.0)
+    assert calls[0] == 16 and k == 15000 and el == pytest.approx(15.0)
+    calls.clear()
+    assert bench.sized_sample(run, 5000, 8, 0, 15.0)[0] == 5000          # capped at every cell
+    assert bench.sized_sample(run, 10 ** 6, 8, 300, 15.0)[0] == 300       # explicit count
+    parts = bench.make_workload(1, 4096)
+    opts = bench.opts_dict(1, 0)
+    t0 = _t.perf_counter()
+    k, el = bench.sized_sample(lambda n: bench.cpu_oracle_sample(parts, opts, n, 4)[1:], 4096, 4, 0, 0.3)
+    assert 16 <= k <= 4096 and el > 0 and _t.perf_counter() - t0 < 10

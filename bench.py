@@ -543,6 +543,11 @@ def run_gpu(args):
         v = k / el
         cpu = {"value": v, "unit": "cells/s", "cores": threads, "kind": "oracle",
                "sample": f"{k} cells evenly spaced through the field ({el:.1f} s)"}
+        if args.cpu_1core_seconds > 0:   # the same oracle on one host core
+            k1, el1 = sized_sample(lambda n: cpu_oracle_sample(parts, opts_d, n, 1, split)[1:], n_total, 1, 0,
+                                   args.cpu_1core_seconds)
+            cpu["one_core"] = {"value": k1 / el1, "unit": "cells/s", "cores": 1,
+                               "sample": f"{k1} cells evenly spaced through the field ({el1:.1f} s)"}
     state_bytes = sum(len(T) * (m.ns + 2) * 8 for m, T, _, _ in parts)
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
@@ -729,15 +734,19 @@ def run_adjoint(args):
         threads = os.cpu_count() or 1
         r = oracle.RefMech(m)
 
-        def run(k):
+        def run(k, nthreads=threads):
             idx = np.linspace(0, N - 1, k).astype(np.int64)
             t0 = time.perf_counter()
             r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(k), np.zeros((k, m.ns)), oracle_opts(opts_d),
-                         nthreads=threads)
+                         nthreads=nthreads)
             return time.perf_counter() - t0, k
         k, el = sized_sample(run, N, threads, args.cpu_sample, args.cpu_seconds)
         cpu = {"value": k / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
                "sample": f"{k} cells evenly spaced, forward + adjoint ({el:.1f} s)"}
+        if args.cpu_1core_seconds > 0:   # the same oracle on one host core
+            k1, el1 = sized_sample(lambda n: run(n, 1), N, 1, 0, args.cpu_1core_seconds)
+            cpu["one_core"] = {"value": k1 / el1, "unit": "cells/s", "cores": 1,
+                               "sample": f"{k1} cells evenly spaced, forward + adjoint ({el1:.1f} s)"}
     line = {
         "metric": METRIC_ADJ, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -809,6 +818,8 @@ def main():
                     help="cells of the oracle's cpu_baseline sample (0: sized for --cpu-seconds)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU work of the cpu_baseline sample when --cpu-sample is 0")
+    ap.add_argument("--cpu-1core-seconds", type=float, default=5.0,
+                    help="work of the one-core oracle timing reported beside cpu_baseline (0: skip)")
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")

@@ -75,6 +75,18 @@ cg_status cgx_layout(int ns, int nr, int mat_bytes, int64_t smem_limit, int adjo
  * cg_mech_set_thermo, ns < 1), CG_ECAPACITY. */
 cg_status cgx_thermo_table(int ns, int np, const double *coef, int *P, double *table, int64_t capacity);
 
+/* Throughput probe of one arithmetic unit of the current device, the
+ * denominator of the integration kernels' ALU roofline (not part of the
+ * method). kind: 0 FP64 FMA on the first active_lanes lanes of every warp
+ * (1..32; the others idle), 1 FP32 FMA, 2 FP64 tensor-core MMA
+ * (mma.sync m8n8k4), 3 exp(double), 4 1/x (double). 8 blocks of 256
+ * threads per SM run independent register-resident chains for `iters`
+ * iterations (at most 2^32), once to warm up and once timed with CUDA
+ * events on `stream`. *ops_per_second receives FLOP/s for kinds 0-2
+ * (an FMA counts 2) and evaluations/s for kinds 3-4. Synchronises.
+ * Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
+cg_status cgx_rate_probe(int kind, int active_lanes, int64_t iters, double *ops_per_second, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,7 +57,7 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
             "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
             "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo",
-            "cgx_thermo_table")
+            "cgx_thermo_table", "cgx_rate_probe")
 
 
 def library_path() -> str:
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = False):
     lib.cgx_schedule.argtypes = [L, P, P, P, P, I, P, P, P, P, P, L]
     lib.cgx_rate_chunks.argtypes = [I, P, I, P, P, P, P, I]
     lib.cgx_layout.argtypes = [I, I, I, L, I, I] + [P] * 8
+    lib.cgx_rate_probe.argtypes = [I, I, L, ctypes.POINTER(ctypes.c_double), P]
     lib.cg_react_split.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, I, P, P, P]
     lib.cg_last_error.restype = ctypes.c_char_p
     lib.cg_last_error.argtypes = []
@@ -338,6 +339,14 @@ def cgx_thermo_table(coef):
     t = np.zeros((4 * P.value + 1) * ns)
     _check(lib.cgx_thermo_table(ns, np_, c.ctypes.data, ctypes.byref(P), t.ctypes.data, t.size))
     return P.value, t.reshape(4 * P.value + 1, ns)
+
+
+def cgx_rate_probe(kind: int, iters: int, active_lanes: int = 32, stream=None) -> float:
+    """Test hook: throughput of one arithmetic unit of cuda:0 (0 FP64 FMA,
+    1 FP32 FMA, 2 FP64 MMA, 3 exp, 4 reciprocal); FLOP/s or evaluations/s."""
+    r = ctypes.c_double(0.0)
+    _check(load().cgx_rate_probe(kind, active_lanes, int(iters), ctypes.byref(r), _stream(stream)))
+    return r.value
 
 
 def cgx_layout(ns: int, nr: int, mat_bytes: int, smem_limit: int, adjoint: bool = False, gmres_m: int = 0) -> dict:

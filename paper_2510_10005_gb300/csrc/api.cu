@@ -568,6 +568,11 @@ cg_status validate(const cg_mech_desc* d) {
 
 }  // namespace
 
+namespace cg {
+// csrc/probes.cu
+cudaError_t launch_rate_probe(int kind, int active, int64_t iters, int blocks, float* ms, cudaStream_t st);
+}  // namespace cg
+
 extern "C" {
 
 const char* cg_last_error(void) { return g_err.c_str(); }
@@ -641,6 +646,28 @@ cg_status cgx_layout(int ns, int nr, int mat_bytes, int64_t smem_limit, int adjo
     }
     *smem_doubles = L.stotal;
     *global_doubles = L.gtotal;
+    return CG_OK;
+}
+
+cg_status cgx_rate_probe(int kind, int active_lanes, int64_t iters, double* ops_per_second, void* stream) {
+    if (kind < 0 || kind > 4 || active_lanes < 1 || active_lanes > 32 || iters < 1 || iters > (int64_t)1 << 32 ||
+        !ops_per_second)
+        return fail(CG_EINVAL, "bad arguments");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    const int blocks = 8 * sms;   // 8 blocks of 256 threads per SM
+    float ms = 0.0f;
+    if ((e = cg::launch_rate_probe(kind, active_lanes, iters, blocks, &ms, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(e, "rate probe");
+    const double warps = 8.0 * blocks, lanes = 32.0 * warps, it = (double)iters;
+    const double ops[5] = {warps * active_lanes * it * 8 * 2,   // FP64 FMA: 8 chains, 2 FLOP each
+                           lanes * it * 8 * 2,                   // FP32 FMA
+                           warps * it * 4 * 2 * 8 * 8 * 4,       // 4 MMA of m8n8k4 per warp
+                           lanes * it * 8,                       // exp
+                           lanes * it * 8};                      // reciprocal
+    *ops_per_second = ops[kind] / (ms * 1e-3);
     return CG_OK;
 }
 

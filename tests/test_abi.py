@@ -111,3 +111,11 @@ def test_set_thermo_checks_arguments(lib):
     coef = np.zeros(10)
     assert lib.cg_mech_set_thermo(None, 7, coef.ctypes.data) == chemgb.CG_EINVAL
     assert b"mech is NULL" in lib.cg_last_error()
+
+
+def test_rate_probe_checks_arguments(lib):
+    """The throughput probe refuses bad arguments before any device work."""
+    r = ctypes.c_double(0.0)
+    for kind, lanes, iters in ((5, 32, 10), (-1, 32, 10), (0, 0, 10), (0, 33, 10), (0, 32, 0), (0, 32, 1 << 40)):
+        assert lib.cgx_rate_probe(kind, lanes, iters, ctypes.byref(r), None) == chemgb.CG_EINVAL
+    assert lib.cgx_rate_probe(0, 32, 10, None, None) == chemgb.CG_EINVAL

@@ -83,3 +83,44 @@ def test_integrators_with_gmres_match_lu(mechs, ref, prec, method):
     np.testing.assert_allclose(Tg, Tl, rtol=1e-10)
     np.testing.assert_allclose(Yg, Yl, rtol=1e-8, atol=1e-18)
     assert np.all(stg[:, 3] >= stg[:, 2])     # at least one GMRES iteration per Newton iteration
+
+
+def _krylov_minres(B, z0, kmax):
+    """Brute force: the smallest residual ||z0 - B x|| over x in the Krylov
+    space K_k(B, z0), k = 1..kmax (Arnoldi with two Gram-Schmidt passes in
+    numpy, then a dense least-squares solve); returns residuals and iterates."""
+    n = len(z0)
+    V = np.zeros((n, kmax + 1))
+    V[:, 0] = z0 / np.linalg.norm(z0)
+    res, xs = [], []
+    for k in range(1, kmax + 1):
+        w = B @ V[:, k - 1]
+        for _ in range(2):
+            w -= V[:, :k] @ (V[:, :k].T @ w)
+        V[:, k] = w / np.linalg.norm(w)
+        y = np.linalg.lstsq(B @ V[:, :k], z0, rcond=None)[0]
+        xs.append(V[:, :k] @ y)
+        res.append(np.linalg.norm(z0 - B @ xs[-1]))
+    return np.array(res), xs
+
+
+@pytest.mark.parametrize("prec", PCS)
+def test_stopping_rule_and_iterate_against_brute_force(prec):
+    """Section 3.4 (left preconditioning M^-1 A x = M^-1 b, M = I, diag A or
+    its lower triangle): full GMRES stops at the first iteration whose
+    preconditioned residual is within tol of that of x = 0, and its iterate
+    is the Krylov-space minimiser. The tolerance sits halfway (geometrically)
+    between two consecutive minimal residuals, so the expected count is
+    unambiguous."""
+    n = 30
+    A, b = _system(n, 40 + prec, dom=2.0)
+    M = {oracle.PC_NONE: np.eye(n), oracle.PC_JACOBI: np.diag(np.diag(A)),
+         oracle.PC_GAUSS_SEIDEL: np.tril(A)}[prec]
+    B, z0 = np.linalg.solve(M, A), np.linalg.solve(M, b)
+    res, xs = _krylov_minres(B, z0, 20)
+    k = int(np.argmax(res / np.linalg.norm(z0) < 1e-4))          # a mid-run iteration
+    assert 3 <= k + 1 <= 19 and res[k] < res[k - 1]
+    tol = np.sqrt(res[k - 1] * res[k]) / np.linalg.norm(z0)
+    x, ok, it = oracle.gmres(A, b, prec, m=n, maxit=n, tol=tol)
+    assert ok and it == k + 1
+    np.testing.assert_allclose(x, xs[k], rtol=1e-8, atol=1e-10 * np.abs(xs[k]).max())

@@ -255,15 +255,31 @@ def workload_name(config: int, method: str | None, linear: str | None = None, pr
     return w
 
 
+def workload_variant(parts, args):
+    """The workload's mechanisms with SRI falloff and PLOG reactions
+    (--sri-plog) and/or refitted thermodynamics (--thermo-degree)."""
+    from paper_2510_10005_gb300 import inputs
+    if args.sri_plog:
+        parts = [(inputs.with_sri_plog(m, n_sri=max(1, m.nr // 40), n_plog=max(1, m.nr // 16), seed=3), T, Y, p)
+                 for m, T, Y, p in parts]
+    if args.thermo_degree is not None:
+        parts = [(inputs.with_thermo_degree(m, args.thermo_degree), T, Y, p) for m, T, Y, p in parts]
+    return parts
+
+
 def flow_state(m, T, Y, p):
     """Conserved variables of a compressible flow solver for the split
     surface (input construction): rho from the ideal gas, u = sum Y_i u_i(T)
-    from the NASA-7 polynomials, rho Y."""
+    from the mechanism's c_p polynomials (NASA-7 or another degree), rho Y."""
     R = 8314.46261815324
     rho = p / (R * T * (Y / m.W).sum(axis=1))
-    a = m.nasa7
+    a = m.thermo_coef
+    P = a.shape[1] - 3
     Tc = T[:, None]
-    h_RT = a[:, 0] + Tc * (a[:, 1] / 2 + Tc * (a[:, 2] / 3 + Tc * (a[:, 3] / 4 + Tc * a[:, 4] / 5))) + a[:, 5] / Tc
+    h_RT = a[:, P] / (P + 1)
+    for k in range(P - 1, -1, -1):
+        h_RT = a[:, k] / (k + 1) + Tc * h_RT
+    h_RT = h_RT + a[:, P + 1] / Tc
     u = (Y * (R / m.W) * Tc * (h_RT - 1.0)).sum(axis=1)
     return rho, u, rho[:, None] * Y
 
@@ -310,23 +326,15 @@ def sized_sample(run, n_total: int, threads: int, cells: int, seconds: float):
     return done, el
 
 
-def workload_variant(parts, args):
-    """The workload's mechanisms with SRI falloff and PLOG reactions
-    (--sri-plog)."""
-    if not args.sri_plog:
-        return parts
-    from paper_2510_10005_gb300 import inputs
-    return [(inputs.with_sri_plog(m, n_sri=max(1, m.nr // 40), n_plog=max(1, m.nr // 16), seed=3), T, Y, p)
-            for m, T, Y, p in parts]
-
-
 def full_workload_name(args) -> str:
     """The workload as both arms state it, with every option that changes it."""
     return (workload_name(args.config, args.method, args.linear, args.prec)
             + ("; operator-split surface: (rho, u, rho Y) in, T recovered (5 Newton iterations), "
                "constant volume, T and R out" if args.surface == "split" else "")
             + ("; mechanism with nr/40 Troe reactions made SRI and nr/16 elementary reactions made "
-               "PLOG (3-6 levels, 0.1-100 atm)" if args.sri_plog else ""))
+               "PLOG (3-6 levels, 0.1-100 atm)" if args.sri_plog else "")
+            + (f"; thermodynamics refitted with a c_p polynomial of degree {args.thermo_degree}"
+               if getattr(args, "thermo_degree", None) is not None else ""))
 
 
 def dist_env():
@@ -826,6 +834,8 @@ def main():
     ap.add_argument("--prec", choices=sorted(PRECS), default=None, help="GMRES preconditioner (default gs)")
     ap.add_argument("--sri-plog", action="store_true",
                     help="give the workload's mechanisms SRI falloff and PLOG reactions")
+    ap.add_argument("--thermo-degree", type=int, default=None,
+                    help="refit the mechanisms' c_p polynomials to this degree (0-15; NASA-7 is 4)")
     ap.add_argument("--surface", choices=["integrate", "split"], default="integrate",
                     help="split: the operator-split call of a compressible solver (rho, u, rho Y in; T, R out), "
                          "constant volume")

@@ -108,7 +108,7 @@ enum { CG_PC_NONE = 0, CG_PC_JACOBI = 1, CG_PC_GAUSS_SEIDEL = 2 };
  *   nasa7[ns*7]     a1..a5 (c_p/R polynomial), a6 (h/R constant), a7 (s/R
  *                   constant); one range used at every temperature. This
  *                   is the n_p = 4 case of eq. specific_heat_polynomial;
- *                   the library takes no other degree.
+ *                   cg_mech_set_thermo takes other degrees.
  *   rxn_type[nr]    CG_RXN_*
  *   reversible[nr]  0 or 1; reverse rate k_f / K_c (eq. reverse_rate)
  *   rf_idx/rf_nu[nr*3]  reactant species and integer coefficients (-1 / 0 pad)
@@ -342,6 +342,18 @@ cg_status cg_integrate_adjoint(const cg_mech *mech, const cg_integrate_opts *opt
  * mechanism may be in flight. For parameter fitting with the adjoint.
  * Errors: CG_EINVAL (NULL or non-finite entries), CG_ECUDA. */
 cg_status cg_mech_set_arrhenius(cg_mech *mech, const double *arr);
+
+/* Replace the thermodynamics by a c_p polynomial of degree np in [0, 15]
+ * (Section 2.1, eq. specific_heat_polynomial; Appendix C.1 refits NASA data
+ * to np = 7 and 15). coef[ns * (np + 3)] (host) holds per species a_0..a_np
+ * of c_p/R = sum_k a_k T^k (molar) followed by the h/R and s/R constants, so
+ * that h/R = sum_k a_k T^(k+1)/(k+1) + a_(np+1) and s/R = a_0 ln T +
+ * sum_(k>=1) a_k T^k / k + a_(np+2); np = 4 is the nasa7 row. Synchronises
+ * the device; the table keeps its address, but the degree reaches kernels
+ * by value, so a CUDA graph captured earlier must be captured again.
+ * Errors: CG_EINVAL (NULL arguments, np out of range, non-finite entries),
+ * CG_ECUDA. */
+cg_status cg_mech_set_thermo(cg_mech *mech, int np, const double *coef);
 
 /* Same as cg_integrate with HOST arrays: copies the inputs to device memory
  * owned by the mechanism (grown on demand, freed with it), integrates,

@@ -64,6 +64,17 @@ cg_status cgx_layout(int ns, int nr, int mat_bytes, int64_t smem_limit, int adjo
                      int *n_arrays, int *offset, int *size, int *in_global, int *priority, int *smem_doubles,
                      int *global_doubles);
 
+/* The per-species thermo table that cg_mech_set_thermo(mech, np, coef)
+ * uploads for ns species (Section 2.1, eq. specific_heat_polynomial), in
+ * the kernels' layout: table[r * ns + i] for rows r < 4 P + 1, where
+ * P = max(np, 4) is written to *P; rows a_k (k = 0..P), a_k/(k+1) at
+ * P + k (k >= 1), the h/R constant at 2 P + 1, a_k/k at 2 P + k (k >= 2),
+ * the s/R constant at 3 P + 1, k a_k at 3 P + k (k >= 2), with a_k = 0
+ * above np. Host only. table may be NULL (only *P is written); otherwise
+ * `capacity` entries, at least (4 P + 1) ns. Errors: CG_EINVAL (as
+ * cg_mech_set_thermo, ns < 1), CG_ECAPACITY. */
+cg_status cgx_thermo_table(int ns, int np, const double *coef, int *P, double *table, int64_t capacity);
+
 /* Throughput probe of one arithmetic unit of the current device, the
  * denominator of the integration kernels' ALU roofline (not part of the
  * method). kind: 0 FP64 FMA on the first active_lanes lanes of every warp

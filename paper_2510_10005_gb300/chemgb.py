@@ -56,7 +56,8 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_integrate_opts_default", "cg_integrate", "cg_integrate_batch", "cg_integrate_host",
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
             "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
-            "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cgx_rate_probe")
+            "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo",
+            "cgx_thermo_table", "cgx_rate_probe")
 
 
 def library_path() -> str:
@@ -98,6 +99,8 @@ def load(build_if_missing: bool = False):
     lib.cg_integrate_adjoint.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, I, P, P, P, P, P, P,
                                          P, P]
     lib.cg_mech_set_arrhenius.argtypes = [P, P]
+    lib.cg_mech_set_thermo.argtypes = [P, I, P]
+    lib.cgx_thermo_table.argtypes = [I, I, P, P, P, L]
     lib.cgx_exp_check.argtypes = [P, L, P, P, P, P]
     lib.cgx_schedule.argtypes = [L, P, P, P, P, I, P, P, P, P, P, L]
     lib.cgx_rate_chunks.argtypes = [I, P, I, P, P, P, P, I]
@@ -266,6 +269,15 @@ def cg_integrate_adjoint(h, opts, ckpt, ckpt_n, dT_end, dY_end, dT0, dY0, dtheta
                                        None if status is None else _dev(status, "int32"), _stream(stream)))
 
 
+def cg_mech_set_thermo(h, coef):
+    """Thermodynamics of another degree: coef [ns, n_p + 3] (a_0..a_np of
+    c_p/R, then the h/R and s/R constants)."""
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    if c.ndim != 2 or c.shape[0] != h.ns or c.shape[1] < 3:
+        raise ValueError(f"coef must be [{h.ns}, n_p + 3]")
+    _check(load().cg_mech_set_thermo(h.ptr, c.shape[1] - 3, c.ctypes.data))
+
+
 def cg_mech_set_arrhenius(h, arr):
     """Replace (ln A, b, Ea) of every reaction (host array [nr, 3])."""
     a = np.ascontiguousarray(arr, dtype=np.float64).reshape(h.nr, 3)
@@ -316,6 +328,19 @@ def cgx_rate_chunks(rxn_type, team: int):
     return ptr, first, ln
 
 
+def cgx_thermo_table(coef):
+    """Test hook (host only): the device thermo table for coef [ns, n_p + 3];
+    returns (P, table [4 P + 1, ns])."""
+    lib = load()
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    ns, np_ = c.shape[0], c.shape[1] - 3
+    P = ctypes.c_int(0)
+    _check(lib.cgx_thermo_table(ns, np_, c.ctypes.data, ctypes.byref(P), None, 0))
+    t = np.zeros((4 * P.value + 1) * ns)
+    _check(lib.cgx_thermo_table(ns, np_, c.ctypes.data, ctypes.byref(P), t.ctypes.data, t.size))
+    return P.value, t.reshape(4 * P.value + 1, ns)
+
+
 def cgx_rate_probe(kind: int, iters: int, active_lanes: int = 32, stream=None) -> float:
     """Test hook: throughput of one arithmetic unit of cuda:0 (0 FP64 FMA,
     1 FP32 FMA, 2 FP64 MMA, 3 exp, 4 reciprocal); FLOP/s or evaluations/s."""
@@ -342,14 +367,11 @@ class MechHandle:
 
     def __init__(self, mech):
         thermo = getattr(mech, "thermo", None)
-        if thermo is not None and thermo.shape[1] != 7:
-            raise NotImplementedError(f"c_p polynomial of degree {thermo.shape[1] - 3}: the CUDA library "
-                                      "evaluates the n_p = 4 (NASA-7) form only")
         lib = load()
         f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
         i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
         self._keep = dict(
-            W=f64(mech.W), nasa7=f64(mech.nasa7 if thermo is None else thermo), rxn_type=i32(mech.rtype), reversible=i32(mech.reversible),
+            W=f64(mech.W), nasa7=f64(mech.nasa7 if thermo is None or thermo.shape[1] != 7 else thermo), rxn_type=i32(mech.rtype), reversible=i32(mech.reversible),
             rf_idx=i32(mech.rf_idx), rf_nu=i32(mech.rf_nu), rr_idx=i32(mech.rr_idx), rr_nu=i32(mech.rr_nu),
             arr=f64(mech.arr), arr0=f64(mech.arr0), troe=f64(mech.troe), eff_ptr=i32(mech.eff_ptr),
             eff_idx=i32(mech.eff_idx) if len(mech.eff_idx) else np.zeros(1, np.int32),
@@ -365,6 +387,8 @@ class MechHandle:
         self.ns, self.nr, self.n = mech.ns, mech.nr, mech.ns + 1
         self.mech = mech
         self.arr = np.array(self._keep["arr"]).reshape(mech.nr, 3)   # current (ln A, b, Ea)
+        if thermo is not None and thermo.shape[1] != 7:   # a c_p polynomial of another degree
+            cg_mech_set_thermo(self, thermo)
 
     def close(self):
         if getattr(self, "ptr", None):

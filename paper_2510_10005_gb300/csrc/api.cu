@@ -40,6 +40,7 @@ cg_status cuda_fail(cudaError_t e, const char* what) {
 const double kR = 8314.46261815324;
 const double kPref = 101325.0;
 const size_t kMaxSmemPerBlock = 227 * 1024;
+const int kMaxThermoDegree = 15;   // c_p polynomials of degree 0..15 (Appendix C.1 goes to 15)
 
 // One term of an assembly schedule: out[dst] += fac * in[src].
 struct Term {
@@ -741,7 +742,8 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     std::stable_sort(perm.begin(), perm.end(),
                      [&](int a, int b) { return d->rxn_type[a] < d->rxn_type[b]; });
 
-    std::vector<double> th((size_t)cg::TH_ROWS * ns), W(ns), invW(ns);
+    // room for the largest degree, so that cg_mech_set_thermo never moves the table
+    std::vector<double> th((size_t)cg::th_rows(kMaxThermoDegree) * ns, 0.0), W(ns), invW(ns);
     for (int i = 0; i < ns; ++i) {
         const double* a = d->nasa7 + 7 * i;
         auto T = [&](int r) -> double& { return th[(size_t)r * ns + i]; };
@@ -863,6 +865,7 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     dm.nr = nr;
     dm.n = n;
     dm.ln_pref_R = std::log(kPref / kR);
+    dm.th_np = 4;
 #define UP(vec, field)                                           \
     if ((st = upload(m->allocs, vec, &dm.field)) != CG_OK) {     \
         cg_mech_destroy(m);                                      \
@@ -1206,6 +1209,60 @@ cg_status cg_mech_set_arrhenius(cg_mech* m, const double* arr) {
         (e = cudaMemcpy(const_cast<double*>(m->dm.dTa0), dTa0.data(), b, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy (Arrhenius parameters)");
     m->arr.assign(arr, arr + 3 * (size_t)nr);
+    return CG_OK;
+}
+
+namespace {
+
+// The device thermo table of a c_p polynomial of degree np (layout of
+// cg::th_rows); returns the table's degree P = max(np, 4), since degrees
+// below 4 are the NASA-7 form with zero upper coefficients.
+cg_status thermo_table(int ns, int np, const double* coef, int* P_out, std::vector<double>& th) {
+    if (np < 0 || np > kMaxThermoDegree) return fail(CG_EINVAL, "degree %d outside [0, %d]", np, kMaxThermoDegree);
+    if (ns > 0 && !coef) return fail(CG_EINVAL, "coef is NULL");
+    for (int k = 0; k < ns * (np + 3); ++k)
+        if (!std::isfinite(coef[k])) return fail(CG_EINVAL, "coef[%d] not finite", k);
+    const int P = std::max(np, 4);
+    th.assign((size_t)cg::th_rows(P) * ns, 0.0);
+    for (int i = 0; i < ns; ++i) {
+        const double* c = coef + (size_t)i * (np + 3);
+        auto a = [&](int k) { return k <= np ? c[k] : 0.0; };
+        auto T = [&](int r) -> double& { return th[(size_t)r * ns + i]; };
+        for (int k = 0; k <= P; ++k) T(k) = a(k);
+        for (int k = 1; k <= P; ++k) T(P + k) = a(k) / (k + 1);
+        T(2 * P + 1) = c[np + 1];
+        for (int k = 2; k <= P; ++k) T(2 * P + k) = a(k) / k;
+        T(3 * P + 1) = c[np + 2];
+        for (int k = 2; k <= P; ++k) T(3 * P + k) = k * a(k);
+    }
+    *P_out = P;
+    return CG_OK;
+}
+
+}  // namespace
+
+cg_status cgx_thermo_table(int ns, int np, const double* coef, int* P, double* table, int64_t capacity) {
+    if (ns < 1 || !P) return fail(CG_EINVAL, "bad arguments");
+    std::vector<double> th;
+    cg_status st = thermo_table(ns, np, coef, P, th);
+    if (st != CG_OK || !table) return st;
+    if (capacity < (int64_t)th.size()) return fail(CG_ECAPACITY, "the table has %zu entries", th.size());
+    std::copy(th.begin(), th.end(), table);
+    return CG_OK;
+}
+
+cg_status cg_mech_set_thermo(cg_mech* m, int np, const double* coef) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    std::vector<double> th;
+    int P = 4;
+    cg_status st = thermo_table(m->ns, np, coef, &P, th);
+    if (st != CG_OK) return st;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    if ((e = cudaMemcpy(const_cast<double*>(m->dm.th), th.data(), th.size() * sizeof(double),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy (thermo table)");
+    m->dm.th_np = P;
     return CG_OK;
 }
 

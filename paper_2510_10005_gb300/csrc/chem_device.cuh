@@ -37,7 +37,8 @@ enum { R_CONV = 0, R_CONP = 1, R_CONP_LIT = 2 };
 enum { CELL_OK = 0, CELL_NEWTON_FAIL = 1, CELL_STEP_TOO_SMALL = 2, CELL_MAX_STEPS = 3,
        CELL_NONFINITE = 4, CELL_NO_RECORD = 5 };
 
-// rows of the per-species thermo table th[k * ns + i]
+// rows of the per-species thermo table th[k * ns + i] for the NASA-7 form
+// (c_p polynomial of degree P = 4)
 enum {
     TH_A1 = 0, TH_A2, TH_A3, TH_A4, TH_A5,       // c_p / R = a1 + a2 T + .. + a5 T^4
     TH_H2, TH_H3, TH_H4, TH_H5, TH_A6,           // h/(RT) = a1 + a2/2 T + .. + a6 / T
@@ -45,6 +46,12 @@ enum {
     TH_D3, TH_D4, TH_D5,                         // d(c_p/R)/dT = a2 + 2 a3 T + ..
     TH_ROWS
 };
+// The same table for a c_p polynomial of degree P >= 4 (Section 2.1, eq.
+// specific_heat_polynomial; Appendix C.1), c_p/R = sum_{k=0}^{P} a_k T^k:
+// 4 P + 1 rows, a_k at k, a_k/(k+1) at P + k (k >= 1), the h/R constant at
+// 2 P + 1, a_k/k at 2 P + k (k >= 2), the s/R constant at 3 P + 1, k a_k at
+// 3 P + k (k >= 2). P = 4 is the layout above.
+__host__ __device__ constexpr int th_rows(int P) { return 4 * P + 1; }
 
 // A mechanism as the kernels see it. All pointers are device memory.
 // Reactions are in the library's internal order (sorted by type).
@@ -52,7 +59,8 @@ struct DevMech {
     int ns, nr, n;               // species, reactions, n = ns + 1
     int team;                    // threads per cell the schedules were built for
     double ln_pref_R;            // ln(p_ref / R)
-    const double *th;            // [TH_ROWS][ns]
+    const double *th;            // [th_rows(th_np)][ns]
+    int th_np;                   // degree P of the c_p polynomial (4: NASA-7)
     const double *W, *invW;      // [ns]
     const int *rtype, *rev, *sumnu;
     const int *sidx, *snu;       // [6][nr]: slots 0..2 reactants, 3..5 products; -1 empty
@@ -326,6 +334,28 @@ static __device__ __forceinline__ double exp_tab(double x, const double* __restr
 // ---------------------------------------------------------------------------
 // thermodynamics and rates of progress (Sections 2.1, 2.2)
 
+// c_p/R and h/(RT) of species i from a table of degree P > 4, by Horner's rule
+__device__ __forceinline__ void thermo_cp_h_deg(const double* th, int ns, int P, double T, double invT,
+                                                double& cp, double& h) {
+    double c = __ldg(th + P * ns);
+    for (int k = P - 1; k >= 0; --k) c = fma(c, T, __ldg(th + k * ns));
+    double hp = __ldg(th + 2 * P * ns);
+    for (int k = P - 1; k >= 1; --k) hp = fma(hp, T, __ldg(th + (P + k) * ns));
+    cp = c;
+    h = fma(T, hp, __ldg(th)) + __ldg(th + (2 * P + 1) * ns) * invT;
+}
+
+// s/R and d(c_p/R)/dT of species i from a table of degree P > 4
+__device__ __forceinline__ void thermo_s_dcp_deg(const double* th, int ns, int P, double T, double lnT,
+                                                 double& s, double& dcp) {
+    double sp = __ldg(th + 3 * P * ns);
+    for (int k = P - 1; k >= 2; --k) sp = fma(sp, T, __ldg(th + (2 * P + k) * ns));
+    double dp = __ldg(th + 4 * P * ns);
+    for (int k = P - 1; k >= 2; --k) dp = fma(dp, T, __ldg(th + (3 * P + k) * ns));
+    s = __ldg(th) * lnT + T * fma(T, sp, __ldg(th + ns)) + __ldg(th + (3 * P + 1) * ns);
+    dcp = fma(T, dp, __ldg(th + ns));
+}
+
 // Fills SP (species thermo) and RD (q_j and, with deriv, dq_j/dT, the
 // third-body weight w_j and the mass-action partials). Returns sum C.
 template <int TEAM>
@@ -343,14 +373,20 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
     double csum = 0.0;
     for (int i = lane; i < ns; i += TEAM) {
         const double* th = M.th + i;
+        double cp, h, s, dcp;
+        if (M.th_np == 4) {
 #define TH(k) __ldg(th + (k) * ns)
-        const double cp = TH(TH_A1) + T * (TH(TH_A2) + T * (TH(TH_A3) + T * (TH(TH_A4) + T * TH(TH_A5))));
-        const double h = TH(TH_A1) + T * (TH(TH_H2) + T * (TH(TH_H3) + T * (TH(TH_H4) + T * TH(TH_H5))))
-                         + TH(TH_A6) * invT;
-        const double s = TH(TH_A1) * lnT
-                         + T * (TH(TH_A2) + T * (TH(TH_S3) + T * (TH(TH_S4) + T * TH(TH_S5)))) + TH(TH_A7);
-        const double dcp = TH(TH_A2) + T * (TH(TH_D3) + T * (TH(TH_D4) + T * TH(TH_D5)));
+            cp = TH(TH_A1) + T * (TH(TH_A2) + T * (TH(TH_A3) + T * (TH(TH_A4) + T * TH(TH_A5))));
+            h = TH(TH_A1) + T * (TH(TH_H2) + T * (TH(TH_H3) + T * (TH(TH_H4) + T * TH(TH_H5))))
+                + TH(TH_A6) * invT;
+            s = TH(TH_A1) * lnT
+                + T * (TH(TH_A2) + T * (TH(TH_S3) + T * (TH(TH_S4) + T * TH(TH_S5)))) + TH(TH_A7);
+            dcp = TH(TH_A2) + T * (TH(TH_D3) + T * (TH(TH_D4) + T * TH(TH_D5)));
 #undef TH
+        } else {
+            thermo_cp_h_deg(th, ns, M.th_np, T, invT, cp, h);
+            thermo_s_dcp_deg(th, ns, M.th_np, T, lnT, s, dcp);
+        }
         hRT[i] = h;
         gRT[i] = h - s;
         cpR[i] = cp;

@@ -77,11 +77,16 @@ __global__ void temperature_kernel(DevMech M, int reactor, int64_t N, const doub
         double ev = 0.0, cv = 0.0;
         for (int i = lane; i < ns; i += 32) {
             const double* th = M.th + i;
+            double cp, h;
+            if (M.th_np == 4) {
 #define TH(k) __ldg(th + (k) * ns)
-            const double cp = TH(TH_A1) + T * (TH(TH_A2) + T * (TH(TH_A3) + T * (TH(TH_A4) + T * TH(TH_A5))));
-            const double h = TH(TH_A1) + T * (TH(TH_H2) + T * (TH(TH_H3) + T * (TH(TH_H4) + T * TH(TH_H5))))
-                             + TH(TH_A6) * invT;
+                cp = TH(TH_A1) + T * (TH(TH_A2) + T * (TH(TH_A3) + T * (TH(TH_A4) + T * TH(TH_A5))));
+                h = TH(TH_A1) + T * (TH(TH_H2) + T * (TH(TH_H3) + T * (TH(TH_H4) + T * TH(TH_H5))))
+                    + TH(TH_A6) * invT;
 #undef TH
+            } else {
+                thermo_cp_h_deg(th, ns, M.th_np, T, invT, cp, h);
+            }
             const double yw = Y[(int64_t)i * N + cell] * __ldg(M.invW + i);
             ev = fma(yw, h - sub, ev);
             cv = fma(yw, cp - sub, cv);

@@ -38,11 +38,16 @@ __device__ void split_cell(const SplitTask& tk, const Ws& W, const IntParams& P,
         double ev = 0.0, cv = 0.0;
         for (int i = lane; i < ns; i += TEAM) {
             const double* th = M.th + i;
+            double cp, h;
+            if (M.th_np == 4) {
 #define TH(k) __ldg(th + (k) * ns)
-            const double cp = TH(TH_A1) + T * (TH(TH_A2) + T * (TH(TH_A3) + T * (TH(TH_A4) + T * TH(TH_A5))));
-            const double h = TH(TH_A1) + T * (TH(TH_H2) + T * (TH(TH_H3) + T * (TH(TH_H4) + T * TH(TH_H5))))
-                             + TH(TH_A6) * invT;
+                cp = TH(TH_A1) + T * (TH(TH_A2) + T * (TH(TH_A3) + T * (TH(TH_A4) + T * TH(TH_A5))));
+                h = TH(TH_A1) + T * (TH(TH_H2) + T * (TH(TH_H3) + T * (TH(TH_H4) + T * TH(TH_H5))))
+                    + TH(TH_A6) * invT;
 #undef TH
+            } else {
+                thermo_cp_h_deg(th, ns, M.th_np, T, invT, cp, h);
+            }
             const double yw = yn[1 + i] * __ldg(M.invW + i);
             ev = fma(yw, h - 1.0, ev);
             cv = fma(yw, cp - 1.0, cv);

@@ -106,12 +106,11 @@ def test_mech_create_checks_sri_and_plog(lib):
     assert b"SRI but sri is NULL" in lib.cg_last_error()
 
 
-def test_binding_refuses_other_thermo_degrees():
-    """The CUDA library evaluates the n_p = 4 (NASA-7) polynomial; a mechanism
-    refitted to another degree is refused before anything reaches it."""
-    m7 = inputs.with_thermo_degree(inputs.gen_mechanism("h2"), 7)
-    with pytest.raises(NotImplementedError):
-        chemgb.cg_mech_create(m7)
+def test_set_thermo_checks_arguments(lib):
+    """The degree entry point refuses a NULL mechanism before any device work."""
+    coef = np.zeros(10)
+    assert lib.cg_mech_set_thermo(None, 7, coef.ctypes.data) == chemgb.CG_EINVAL
+    assert b"mech is NULL" in lib.cg_last_error()
 
 
 def test_rate_probe_checks_arguments(lib):

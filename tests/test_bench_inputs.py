@@ -50,7 +50,7 @@ def test_reference_arm_takes_the_workload_options(capsys, monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "1")
     monkeypatch.setenv("RANK", "0")
     args = argparse.Namespace(config=1, cells=64, method=None, linear=None, prec=None, surface="split",
-                              sri_plog=True, ref_sample=8, steps=1, warmup=0, gpus=1)
+                              sri_plog=True, thermo_degree=None, ref_sample=8, steps=1, warmup=0, gpus=1)
     bench.run_reference(args)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["config"]["workload"] == bench.full_workload_name(args)

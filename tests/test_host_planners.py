@@ -241,3 +241,65 @@ def test_layout_arguments():
         chemgb.cgx_layout(0, 10, 8, 1024)
     with pytest.raises(chemgb.ChemgbError):
         chemgb.cgx_layout(9, 21, 2, 1024)
+
+
+def device_thermo(P, th, T):
+    """The kernels' evaluation of a thermo table at T (c_p/R, h/(RT), s/R,
+    d(c_p/R)/dT): the NASA-7 expressions when P = 4, Horner's rule above."""
+    lnT, invT = np.log(T), 1.0 / T
+    if P == 4:
+        cp = th[0] + T * (th[1] + T * (th[2] + T * (th[3] + T * th[4])))
+        h = th[0] + T * (th[5] + T * (th[6] + T * (th[7] + T * th[8]))) + th[9] * invT
+        s = th[0] * lnT + T * (th[1] + T * (th[10] + T * (th[11] + T * th[12]))) + th[13]
+        dcp = th[1] + T * (th[14] + T * (th[15] + T * th[16]))
+        return cp, h, s, dcp
+    cp = th[P].copy()
+    for k in range(P - 1, -1, -1):
+        cp = cp * T + th[k]
+    hp = th[2 * P].copy()
+    for k in range(P - 1, 0, -1):
+        hp = hp * T + th[P + k]
+    sp = th[3 * P].copy()
+    for k in range(P - 1, 1, -1):
+        sp = sp * T + th[2 * P + k]
+    dp = th[4 * P].copy()
+    for k in range(P - 1, 1, -1):
+        dp = dp * T + th[3 * P + k]
+    return cp, th[0] + T * hp + th[2 * P + 1] * invT, th[0] * lnT + T * (th[1] + T * sp) + th[3 * P + 1], \
+        th[1] + T * dp
+
+
+@pytest.mark.parametrize("n_p", [0, 2, 4, 7, 15])
+def test_thermo_table_evaluates_to_the_oracles_thermo(n_p):
+    """The table cg_mech_set_thermo uploads, evaluated as the kernels
+    evaluate it, gives the oracle's c_p, h and s (Horner against the
+    oracle's sum of powers: 1e-12 relative, 1e-10 at n_p = 15 where the
+    terms are ~5e3 times the value), and d c_p/dT agrees with the oracle's
+    c_p by finite differences; n_p = 4 reproduces the NASA-7 table."""
+    import oracle
+    m = inputs.with_thermo_degree(inputs.gen_mechanism("ch4"), n_p)
+    r = oracle.RefMech(m)
+    P, th = chemgb.cgx_thermo_table(m.thermo)
+    assert P == max(n_p, 4) and th.shape == (4 * P + 1, m.ns)
+    tol = 1e-10 if n_p == 15 else 1e-12
+    Ri = inputs.R_UNIV / m.W
+    for T in (300.0, 800.0, 1500.0, 2900.0):
+        cp, h, s, dcp = device_thermo(P, th, T)
+        o = r.thermo(T)
+        np.testing.assert_allclose(cp * Ri, o["cp"], rtol=tol)
+        np.testing.assert_allclose(h * Ri * T, o["h"], rtol=tol, atol=tol * np.abs(o["cp"] * T).max())
+        np.testing.assert_allclose(s * Ri, o["s"], rtol=tol)
+        fd = (r.thermo(T + 0.5)["cp"] - r.thermo(T - 0.5)["cp"]) / 1.0
+        np.testing.assert_allclose(dcp * Ri, fd, rtol=1e-5, atol=1e-9 * np.abs(o["cp"]).max())
+    if n_p == 4:
+        P0, th0 = chemgb.cgx_thermo_table(m.nasa7)
+        np.testing.assert_array_equal(th, th0)
+
+
+def test_thermo_table_arguments():
+    with pytest.raises(chemgb.ChemgbError):
+        chemgb.cgx_thermo_table(np.zeros((3, 19)))          # degree 16
+    bad = np.zeros((3, 10))
+    bad[1, 2] = np.nan
+    with pytest.raises(chemgb.ChemgbError):
+        chemgb.cgx_thermo_table(bad)

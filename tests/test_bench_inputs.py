@@ -10,8 +10,13 @@ import oracle
 from paper_2510_10005_gb300 import inputs
 
 
-def test_flow_state_energy_matches_oracle_thermo():
+@pytest.mark.parametrize("n_p", [4, 7, 15])
+def test_flow_state_energy_matches_oracle_thermo(n_p):
+    """u = sum Y_i u_i(T) of the split surface's input, for NASA-7 (n_p = 4)
+    and for refitted c_p polynomials of other degrees."""
     m = inputs.gen_mechanism("ch4")
+    if n_p != 4:
+        m = inputs.with_thermo_degree(m, n_p)
     r = oracle.RefMech(m)
     T, Y, p = inputs.field_flames(m, 64, seed=2)
     rho, u, rhoY = bench.flow_state(m, T, Y, p)

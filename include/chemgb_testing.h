@@ -87,6 +87,14 @@ cg_status cgx_thermo_table(int ns, int np, const double *coef, int *P, double *t
  * Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
 cg_status cgx_rate_probe(int kind, int active_lanes, int64_t iters, double *ops_per_second, void *stream);
 
+/* The Butcher tableau the kernels use for `method` (CG_BE, CG_SDIRK2,
+ * CG_SDIRK4; Appendix A.1, A.2, in stage-derivative form): *s stages,
+ * A[5*5] row-major, b[5], the embedded weights bh[5] and the embedded
+ * order *err_order (0: none). SDIRK-4's coefficients are the full-precision
+ * root of its order conditions near the printed values. Host only.
+ * Errors: CG_EINVAL (NULL arrays, a method without a tableau). */
+cg_status cgx_tableau(int method, int *s, double *A, double *b, double *bh, int *err_order);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,7 +57,7 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
             "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
             "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo",
-            "cgx_thermo_table", "cgx_rate_probe")
+            "cgx_thermo_table", "cgx_rate_probe", "cgx_tableau")
 
 
 def library_path() -> str:
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = False):
     lib.cgx_rate_chunks.argtypes = [I, P, I, P, P, P, P, I]
     lib.cgx_layout.argtypes = [I, I, I, L, I, I] + [P] * 8
     lib.cgx_rate_probe.argtypes = [I, I, L, ctypes.POINTER(ctypes.c_double), P]
+    lib.cgx_tableau.argtypes = [I, P, P, P, P, P]
     lib.cg_react_split.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, I, P, P, P]
     lib.cg_last_error.restype = ctypes.c_char_p
     lib.cg_last_error.argtypes = []
@@ -347,6 +348,14 @@ def cgx_rate_probe(kind: int, iters: int, active_lanes: int = 32, stream=None) -
     r = ctypes.c_double(0.0)
     _check(load().cgx_rate_probe(kind, active_lanes, int(iters), ctypes.byref(r), _stream(stream)))
     return r.value
+
+
+def cgx_tableau(method: int) -> dict:
+    """Test hook (host only): the kernels' Butcher tableau of `method`."""
+    s, e = np.zeros(1, np.int32), np.zeros(1, np.int32)
+    A, b, bh = np.zeros(25), np.zeros(5), np.zeros(5)
+    _check(load().cgx_tableau(method, _ptr(s), _ptr(A), _ptr(b), _ptr(bh), _ptr(e)))
+    return dict(s=int(s[0]), A=A.reshape(5, 5), b=b, bhat=bh, err_order=int(e[0]))
 
 
 def cgx_layout(ns: int, nr: int, mat_bytes: int, smem_limit: int, adjoint: bool = False, gmres_m: int = 0) -> dict:

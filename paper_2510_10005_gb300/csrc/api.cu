@@ -649,6 +649,20 @@ cg_status cgx_layout(int ns, int nr, int mat_bytes, int64_t smem_limit, int adjo
     return CG_OK;
 }
 
+cg_status cgx_tableau(int method, int* s, double* A, double* b, double* bh, int* err_order) {
+    if (!s || !A || !b || !bh || !err_order) return fail(CG_EINVAL, "bad arguments");
+    Tab t;
+    if (!make_tableau(method, t)) return fail(CG_EINVAL, "no tableau for method %d", method);
+    *s = t.s;
+    *err_order = t.err_order;
+    for (int i = 0; i < 5; ++i) {
+        b[i] = t.b[i];
+        bh[i] = t.bh[i];
+        for (int j = 0; j < 5; ++j) A[5 * i + j] = t.A[i][j];
+    }
+    return CG_OK;
+}
+
 cg_status cgx_rate_probe(int kind, int active_lanes, int64_t iters, double* ops_per_second, void* stream) {
     if (kind < 0 || kind > 4 || active_lanes < 1 || active_lanes > 32 || iters < 1 || iters > (int64_t)1 << 32 ||
         !ops_per_second)

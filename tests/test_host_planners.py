@@ -303,3 +303,36 @@ def test_thermo_table_arguments():
     bad[1, 2] = np.nan
     with pytest.raises(chemgb.ChemgbError):
         chemgb.cgx_thermo_table(bad)
+
+
+@pytest.mark.parametrize("method", [0, 1, 2])
+def test_library_tableaux_equal_the_oracles(method):
+    """The Butcher tableaux the kernels use (computed by the library on the
+    host, SDIRK-4 as the long-double root of its order conditions) equal the
+    oracle's independently computed ones to rounding, and SDIRK-4 keeps the
+    seven digits Appendix A.2 prints."""
+    from oracle import tableau
+    lib_t, ref = chemgb.cgx_tableau(method), tableau.tableau(method)
+    assert lib_t["s"] == ref["s"] and lib_t["err_order"] == ref["err_order"]
+    np.testing.assert_allclose(lib_t["A"], ref["A"], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(lib_t["b"], ref["b"], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(lib_t["bhat"], ref["bhat"], rtol=0, atol=1e-13)
+    if method == 2:
+        import os
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sdirk4_appendix_a2.txt")
+        printed = dict((k, float(v)) for k, v in (ln.split() for ln in open(path)
+                                                  if ln.strip() and not ln.startswith("#")))
+        A = lib_t["A"]
+        for k, v in printed.items():
+            if k[0] == "a" and k != "aii":
+                got = A[int(k[1]) - 1, int(k[2]) - 1]
+            elif k[0] == "b":
+                got = lib_t["b"][int(k[1]) - 1]
+            else:
+                got = A[0, 0]
+            assert got == pytest.approx(v, rel=5e-7, abs=5e-9), k
+
+
+def test_tableau_arguments():
+    with pytest.raises(chemgb.ChemgbError):
+        chemgb.cgx_tableau(99)

@@ -288,6 +288,16 @@ def oracle_opts(o: dict) -> dict:
     return {k: v for k, v in o.items() if k not in ("precision", "persistent")}
 
 
+# The oracle's timing sample of each workload: cells evenly spaced through
+# every mechanism's field (so in proportion from the regions of the
+# contiguous flame field, and a uniform sample of the interleaved ones)
+CPU_SAMPLE = {1: 4096, 2: 4096, 3: 4096, 4: 256, 5: 1024}
+
+
+def sample_indices(n_cells: int, k: int) -> np.ndarray:
+    return np.linspace(0, n_cells - 1, min(k, n_cells)).astype(np.int64)
+
+
 def cpu_oracle_sample(parts, opts, n_sample: int, threads: int, split: bool = False):
     """Time the oracle on an evenly spaced sample of every mechanism's cells
     (shares in proportion to the cells); returns (cells/s, seconds, cells).
@@ -298,7 +308,8 @@ def cpu_oracle_sample(parts, opts, n_sample: int, threads: int, split: bool = Fa
     t, done = 0.0, 0
     for m, T, Y, p in parts:
         k = max(1, int(round(n_sample * len(T) / total)))
-        idx = np.linspace(0, len(T) - 1, k).astype(np.int64)
+        idx = sample_indices(len(T), k)
+        k = len(idx)
         r = oracle.RefMech(m)
         if split:
             rho, u, rhoY = flow_state(m, T[idx], Y[idx], p[idx])
@@ -312,18 +323,15 @@ def cpu_oracle_sample(parts, opts, n_sample: int, threads: int, split: bool = Fa
     return done / t, t, done
 
 
-def sized_sample(run, n_total: int, threads: int, cells: int, seconds: float):
-    """An oracle sample of `cells` cells, or, with cells = 0, of about
-    `seconds` of CPU work: a pilot of two cells per thread gives the rate,
-    then the sample that rate predicts (at most every cell). run(k) times
-    the oracle on about k evenly spaced cells and returns (seconds, cells
-    run); returns (cells run, seconds) of the sample."""
-    if cells > 0:
-        el, done = run(min(cells, n_total))
-        return done, el
-    el0, done0 = run(min(n_total, max(16, 2 * threads)))
-    el, done = run(int(min(n_total, max(done0, done0 / max(el0, 1e-9) * seconds))))
-    return done, el
+def median_timing(run, cells: int, repeats: int):
+    """Times the oracle `repeats` times on the same sample of `cells` cells;
+    run(k) returns (seconds, cells run). Returns (cells run, median seconds,
+    all timings)."""
+    times, done = [], 0
+    for _ in range(max(1, repeats)):
+        el, done = run(cells)
+        times.append(el)
+    return done, statistics.median(times), times
 
 
 def full_workload_name(args) -> str:
@@ -355,21 +363,22 @@ def run_reference(args):
             raise SystemExit("--surface split takes one mechanism")
         opts["reactor"] = 0   # the split step is at constant volume
     threads = os.cpu_count() or 1
+    n_sample = args.cpu_sample or CPU_SAMPLE[args.config]
     for _ in range(args.warmup):
-        cpu_oracle_sample(parts, opts, max(16, args.ref_sample // 8), threads, split)
-    times, cells = [], 0
+        cpu_oracle_sample(parts, opts, n_sample, threads, split)
+    times, k = [], 0
     for _ in range(args.steps):
-        v, el, k = cpu_oracle_sample(parts, opts, args.ref_sample, threads, split)
+        _, el, k = cpu_oracle_sample(parts, opts, n_sample, threads, split)
         times.append(el)
-        cells += k
-    value = cells / sum(times)
+    value = k / statistics.median(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": full_workload_name(args), "config": args.config},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{args.ref_sample} cells evenly spaced through the field, per step"},
+                         "sample": f"the same {k} cells evenly spaced through the field every step; "
+                                   f"value = cells / median step time"},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -403,6 +412,8 @@ def run_gpu(args):
     handles, bufs = [], []
     for m, T, Y, p in parts:
         h = chemgb.cg_mech_create(m)
+        if args.smem_limit:
+            chemgb.cg_mech_set_smem_limit(h, args.smem_limit)
         if args.team:
             chemgb.cg_mech_set_launch(h, args.team, args.tpb)
         N = len(T)
@@ -519,33 +530,34 @@ def run_gpu(args):
         N = len(T)
         Th0, Yh0, ph = np.ascontiguousarray(T), np.ascontiguousarray(Y.T), np.ascontiguousarray(p)
         sh_, sth = np.zeros(N, np.int32), np.zeros((4, N), np.int32)
-        e2e_t = 0.0
-        for k in range(args.e2e_steps + 1):
+        calls = []
+        for k in range(args.e2e_steps):
             Th, Yh = Th0.copy(), Yh0.copy()
             barrier()
             t0 = time.perf_counter()
             chemgb.cg_integrate_host(handles[0], opts, Th, Yh, ph, sh_, sth)
-            if k > 0:   # the first call allocates the library's host-call workspace: untimed
-                e2e_t += time.perf_counter() - t0
-        e2e_t = multirank.max_over_ranks(e2e_t, dev)
-        e2e = {"value": multirank.job_throughput(N, ws, args.e2e_steps, e2e_t), "unit": "cells/s",
+            calls.append(multirank.max_over_ranks(time.perf_counter() - t0, dev))
+        e2e_t = statistics.median(calls)
+        e2e = {"value": multirank.job_throughput(N, ws, 1, e2e_t), "unit": "cells/s",
                "h2d_bytes_per_step": N * (m.ns + 2) * 8, "d2h_bytes_per_step": N * (m.ns + 1) * 8 + 20 * N,
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps, "call_s": calls,
+               "how": "median of the timed cg_integrate_host calls (host arrays in and out, copies inside; "
+                      "the first call also grows the library's device workspace once)"}
 
     if rank != 0:
         return
     cpu = None
     if ws == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
-        n_total = sum(len(T) for _, T, _, _ in parts)
-        k, el = sized_sample(lambda n: cpu_oracle_sample(parts, opts_d, n, threads, split)[1:], n_total, threads,
-                             args.cpu_sample, args.cpu_seconds)
-        v = k / el
-        cpu = {"value": v, "unit": "cells/s", "cores": threads, "kind": "oracle",
-               "sample": f"{k} cells evenly spaced through the field ({el:.1f} s)"}
-        if args.cpu_1core_seconds > 0:   # the same oracle on one host core
-            k1, el1 = sized_sample(lambda n: cpu_oracle_sample(parts, opts_d, n, 1, split)[1:], n_total, 1, 0,
-                                   args.cpu_1core_seconds)
+        n_sample = args.cpu_sample or CPU_SAMPLE[args.config]
+        k, el, times = median_timing(lambda n: cpu_oracle_sample(parts, opts_d, n, threads, split)[1:], n_sample,
+                                     args.cpu_repeats)
+        cpu = {"value": k / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
+               "sample": f"{k} cells evenly spaced through the field, median of {len(times)} timings "
+                         f"({', '.join(f'{t:.2f}' for t in times)} s)"}
+        if args.cpu_1core_cells > 0:   # the same oracle on one host core
+            k1, el1, t1 = median_timing(lambda n: cpu_oracle_sample(parts, opts_d, n, 1, split)[1:],
+                                        args.cpu_1core_cells, 1)
             cpu["one_core"] = {"value": k1 / el1, "unit": "cells/s", "cores": 1,
                                "sample": f"{k1} cells evenly spaced through the field ({el1:.1f} s)"}
     state_bytes = sum(len(T) * (m.ns + 2) * 8 for m, T, _, _ in parts)
@@ -735,16 +747,17 @@ def run_adjoint(args):
         r = oracle.RefMech(m)
 
         def run(k, nthreads=threads):
-            idx = np.linspace(0, N - 1, k).astype(np.int64)
+            idx = sample_indices(N, k)
             t0 = time.perf_counter()
-            r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(k), np.zeros((k, m.ns)), oracle_opts(opts_d),
+            r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(len(idx)), np.zeros((len(idx), m.ns)), oracle_opts(opts_d),
                          nthreads=nthreads)
-            return time.perf_counter() - t0, k
-        k, el = sized_sample(run, N, threads, args.cpu_sample, args.cpu_seconds)
+            return time.perf_counter() - t0, len(idx)
+        k, el, times = median_timing(run, args.cpu_sample or CPU_SAMPLE[4], args.cpu_repeats)
         cpu = {"value": k / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
-               "sample": f"{k} cells evenly spaced, forward + adjoint ({el:.1f} s)"}
-        if args.cpu_1core_seconds > 0:   # the same oracle on one host core
-            k1, el1 = sized_sample(lambda n: run(n, 1), N, 1, 0, args.cpu_1core_seconds)
+               "sample": f"{k} cells evenly spaced, forward + adjoint, median of {len(times)} timings "
+                         f"({', '.join(f'{t:.2f}' for t in times)} s)"}
+        if args.cpu_1core_cells > 0:   # the same oracle on one host core
+            k1, el1, _ = median_timing(lambda n: run(n, 1), max(1, args.cpu_1core_cells // 16), 1)
             cpu["one_core"] = {"value": k1 / el1, "unit": "cells/s", "cores": 1,
                                "sample": f"{k1} cells evenly spaced, forward + adjoint ({el1:.1f} s)"}
     line = {
@@ -782,25 +795,26 @@ def run_reference_adjoint(args):
     o = oracle_opts(opts_dict(4, 0))
     r = oracle.RefMech(m)
     threads = os.cpu_count() or 1
-    k = max(1, args.ref_sample // 16)
+    idx = sample_indices(len(T), args.cpu_sample or CPU_SAMPLE[4])
+    k = len(idx)
 
-    def sample(kk, off):
-        idx = (np.linspace(0, len(T) - 1, kk).astype(np.int64) + off) % len(T)
+    def sample():
         t0 = time.perf_counter()
-        r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(kk), np.zeros((kk, m.ns)), o, nthreads=threads)
+        r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(k), np.zeros((k, m.ns)), o, nthreads=threads)
         return time.perf_counter() - t0
 
-    for w in range(args.warmup):
-        sample(max(1, k // 8), w)
-    el = sum(sample(k, s) for s in range(args.steps))
-    value = k * args.steps / el
+    for _ in range(args.warmup):
+        sample()
+    times = [sample() for _ in range(args.steps)]
+    value = k / statistics.median(times)
     print(json.dumps({
         "impl": "reference", "metric": METRIC_ADJ, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": cfg["workload"], "config": 4},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{k} cells evenly spaced, forward + adjoint, per step"},
+                         "sample": f"the same {k} cells evenly spaced every step, forward + adjoint; "
+                                   f"value = cells / median step time"},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -813,14 +827,15 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", type=int, default=2, choices=sorted(CONFIGS))
     ap.add_argument("--cells", type=int, default=0, help="cells per mechanism (default: the workload's)")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3, help="timed host-array calls; e2e is their median")
     ap.add_argument("--cpu-sample", type=int, default=0,
-                    help="cells of the oracle's cpu_baseline sample (0: sized for --cpu-seconds)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0,
-                    help="CPU work of the cpu_baseline sample when --cpu-sample is 0")
-    ap.add_argument("--cpu-1core-seconds", type=float, default=5.0,
-                    help="work of the one-core oracle timing reported beside cpu_baseline (0: skip)")
-    ap.add_argument("--ref-sample", type=int, default=1024)
+                    help="cells of the oracle's timing sample, in the cpu_baseline leg and the reference arm "
+                         "(0: the workload's, " + ", ".join(f"config {c}: {k}" for c, k in CPU_SAMPLE.items()) + ")")
+    ap.add_argument("--cpu-repeats", type=int, default=5, help="timings of the cpu_baseline sample (median)")
+    ap.add_argument("--cpu-1core-cells", type=int, default=256,
+                    help="cells of the one-core oracle timing reported beside cpu_baseline (0: skip)")
+    ap.add_argument("--smem-limit", type=int, default=0,
+                    help="shared memory per cell in bytes before arrays go to global scratch (default: 227 KB)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--team", type=int, default=0, help="threads per cell (default: the library's choice)")

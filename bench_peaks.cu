@@ -1,4 +1,6 @@
-// Throughput probes of the arithmetic units the integration kernels use:
+// Throughput probes of the arithmetic units the integration kernels use
+// (a measurement program of bench.py's roofline, built apart from the
+// library by bench_peaks.py):
 // FP64 FMA (with all or some lanes of a warp active), FP32 FMA, FP64
 // tensor-core MMA (mma.sync m8n8k4), the double exponential and the double
 // reciprocal. They measure the denominators of the kernels' ALU roofline;
@@ -10,8 +12,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-
-namespace cg {
 
 namespace {
 
@@ -115,26 +115,40 @@ cudaError_t launch_one(int kind, int active, int64_t iters, int blocks, int thre
 
 }  // namespace
 
-// Runs probe `kind` (0 FP64 FMA, 1 FP32 FMA, 2 FP64 MMA, 3 exp, 4
-// reciprocal) on `blocks` blocks of 256 threads, once to warm up and once
-// timed with CUDA events on `st`; *ms receives the timed launch's duration.
-cudaError_t launch_rate_probe(int kind, int active, int64_t iters, int blocks, float* ms, cudaStream_t st) {
-    const int threads = 256;
+// Runs probe `kind` (0 FP64 FMA on the first `active` lanes of every warp,
+// 1 FP32 FMA, 2 FP64 MMA m8n8k4, 3 exp(double), 4 1/x (double)) on 8 blocks
+// of 256 threads per SM for `iters` iterations, once to warm up and once
+// timed with CUDA events; *rate receives FLOP/s for kinds 0-2 (an FMA
+// counts 2) and evaluations/s for kinds 3-4. Returns a cudaError_t code.
+extern "C" int peak_probe(int kind, int active, long long iters, double* rate) {
+    if (kind < 0 || kind > 4 || active < 1 || active > 32 || iters < 1 || !rate) return (int)cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+    const int threads = 256, blocks = 8 * sms;
     double* out = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * sizeof(double));
+    float ms = 0.0f;
+    e = cudaMalloc(&out, (size_t)blocks * threads * sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    if (e == cudaSuccess) e = launch_one(kind, active, iters, blocks, threads, out, st);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-    if (e == cudaSuccess) e = launch_one(kind, active, iters, blocks, threads, out, st);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = launch_one(kind, active, iters, blocks, threads, out, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) e = launch_one(kind, active, iters, blocks, threads, out, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(out);
-    return e;
+    if (e != cudaSuccess) return (int)e;
+    const double warps = 8.0 * blocks, lanes = 32.0 * warps, it = (double)iters;
+    const double ops[5] = {warps * active * it * kChains * 2,   // FP64 FMA
+                           lanes * it * kChains * 2,              // FP32 FMA
+                           warps * it * 4 * 2 * 8 * 8 * 4,        // 4 MMA of m8n8k4 per warp
+                           lanes * it * kChains,                  // exp
+                           lanes * it * kChains};                 // reciprocal
+    *rate = ops[kind] / (ms * 1e-3);
+    return 0;
 }
-
-}  // namespace cg

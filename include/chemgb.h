@@ -370,17 +370,24 @@ cg_status cg_integrate_host(const cg_mech *mech, const cg_integrate_opts *opts, 
  * same arguments and results. It always uses the persistent work-stealing
  * launch, and calls no cudaMalloc, cudaFree or other allocating routine:
  * the per-team scratch slots and the work counter live in one fixed 32 MiB
- * device array inside the library, which every GPU that loads the library
- * holds until the process exits.
- *   - The first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+ * device array inside the library.
+ *   - CUDA allocates that array on a device when it loads the library's
+ *     module there: at the first cg_integrate_noalloc call on the device
+ *     (under lazy module loading, the default), or when the library loads
+ *     (eager loading). Make one call per device during set-up, with the
+ *     device current, before taking over the device heap and before any
+ *     stream capture; a call with N = 0 is enough. The array is then held
+ *     until the process exits.
+ *   - Each call looks up the array's device address (cudaGetSymbolAddress)
+ *     on the current device, so a device reset between calls is harmless.
  *   - All calls share the array and it keeps the last call's contents; each
  *     call clears the work counter on its stream. Calls whose work overlaps
  *     on the GPU (other streams, other threads) race on the array: serialise
  *     them.
- *   - Errors: as cg_integrate, and CG_ECAPACITY when one cell's arrays need
- *     more scratch than the array holds (the message gives both sizes). */
+ *   - Errors: as cg_integrate, and CG_ECAPACITY when one block of cells
+ *     needs more scratch than the array holds (the message gives both
+ *     sizes; a lower cg_mech_set_smem_limit never helps, since it moves
+ *     arrays from shared memory into the scratch). */
 cg_status cg_integrate_noalloc(const cg_mech *mech, const cg_integrate_opts *opts, int64_t N, double *T,
                                double *Y, const double *p_or_rho, int32_t *cell_status,
                                int32_t *cell_stats, void *stream);

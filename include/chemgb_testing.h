@@ -22,6 +22,13 @@ extern "C" {
 cg_status cgx_exp_check(const cg_mech *mech, int64_t n, const double *x, double *y_tab, double *y_lib,
                         void *stream);
 
+/* For n arguments x (device array), writes the library's reciprocal (two
+ * Newton-Raphson steps from the hardware's single-precision approximation,
+ * used for the LU pivots of Section 3.4; division outside the
+ * single-precision exponent range) to y (device array of n doubles), on
+ * `stream`. Errors: CG_EINVAL (n < 0, NULL arrays), CG_ECUDA. */
+cg_status cgx_rcp_check(int64_t n, const double *x, double *y, void *stream);
+
 /* The thread-owned assembly schedule the kernels walk to form sparse sums
  * out[dst] += fac * in[src] (the production rates omega_i = sum_j nu_ij q_j
  * of Section 2.2 and the Jacobian entries of Section 3.2). Host only.
@@ -75,18 +82,6 @@ cg_status cgx_layout(int ns, int nr, int mat_bytes, int64_t smem_limit, int adjo
  * cg_mech_set_thermo, ns < 1), CG_ECAPACITY. */
 cg_status cgx_thermo_table(int ns, int np, const double *coef, int *P, double *table, int64_t capacity);
 
-/* Throughput probe of one arithmetic unit of the current device, the
- * denominator of the integration kernels' ALU roofline (not part of the
- * method). kind: 0 FP64 FMA on the first active_lanes lanes of every warp
- * (1..32; the others idle), 1 FP32 FMA, 2 FP64 tensor-core MMA
- * (mma.sync m8n8k4), 3 exp(double), 4 1/x (double). 8 blocks of 256
- * threads per SM run independent register-resident chains for `iters`
- * iterations (at most 2^32), once to warm up and once timed with CUDA
- * events on `stream`. *ops_per_second receives FLOP/s for kinds 0-2
- * (an FMA counts 2) and evaluations/s for kinds 3-4. Synchronises.
- * Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
-cg_status cgx_rate_probe(int kind, int active_lanes, int64_t iters, double *ops_per_second, void *stream);
-
 /* The Butcher tableau the kernels use for `method` (CG_BE, CG_SDIRK2,
  * CG_SDIRK4; Appendix A.1, A.2, in stage-derivative form): *s stages,
  * A[5*5] row-major, b[5], the embedded weights bh[5] and the embedded
@@ -94,6 +89,18 @@ cg_status cgx_rate_probe(int kind, int active_lanes, int64_t iters, double *ops_
  * root of its order conditions near the printed values. Host only.
  * Errors: CG_EINVAL (NULL arrays, a method without a tableau). */
 cg_status cgx_tableau(int method, int *s, double *A, double *b, double *bh, int *err_order);
+
+/* The scratch cg_integrate_noalloc would need for a mechanism of ns
+ * species and nr reactions: the per-cell layout for mat_bytes (8 FP64, 4
+ * FP32 Newton matrix), smem_limit bytes of shared memory per cell and
+ * gmres_m (0: LU), times the teams per block the launch would use (team
+ * threads per cell; teams_per_block lowered while the block's shared memory
+ * exceeds 227 KB; 1 for teams above a warp). Host only. *scratch_bytes
+ * receives that need. Returns CG_ECAPACITY, with the message
+ * cg_integrate_noalloc gives, when it exceeds the library's fixed array.
+ * Errors: CG_EINVAL. */
+cg_status cgx_noalloc_plan(int ns, int nr, int mat_bytes, int64_t smem_limit, int gmres_m, int team,
+                           int teams_per_block, int64_t *scratch_bytes);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@
 // State y = (T, C_1..C_ns) (eq. extracted_problem-1); S = (omega_T, omega_i).
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -1170,14 +1171,21 @@ double recover_T(const Mech& m, int reactor, double e, const double* Y, double T
     return T;
 }
 
+// Cells are independent and their cost varies by two orders of magnitude
+// (frozen vs igniting gas), so each thread takes the next unclaimed cell from
+// a shared counter; the result of a cell does not depend on which thread
+// computed it.
 template <class F> void parallel_for(long N, int nthreads, F fn) {
     if (nthreads <= 1 || N < 2) {
         for (long c = 0; c < N; ++c) fn(c);
         return;
     }
+    std::atomic<long> next(0);
     std::vector<std::thread> th;
     for (int t = 0; t < nthreads; ++t)
-        th.emplace_back([&, t]() { for (long c = t; c < N; c += nthreads) fn(c); });
+        th.emplace_back([&]() {
+            for (long c = next.fetch_add(1); c < N; c = next.fetch_add(1)) fn(c);
+        });
     for (auto& x : th) x.join();
 }
 

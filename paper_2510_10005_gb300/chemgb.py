@@ -57,7 +57,7 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
             "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
             "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo",
-            "cgx_thermo_table", "cgx_rate_probe", "cgx_tableau")
+            "cgx_thermo_table", "cgx_tableau", "cgx_rcp_check", "cgx_noalloc_plan")
 
 
 def library_path() -> str:
@@ -105,7 +105,8 @@ def load(build_if_missing: bool = False):
     lib.cgx_schedule.argtypes = [L, P, P, P, P, I, P, P, P, P, P, L]
     lib.cgx_rate_chunks.argtypes = [I, P, I, P, P, P, P, I]
     lib.cgx_layout.argtypes = [I, I, I, L, I, I] + [P] * 8
-    lib.cgx_rate_probe.argtypes = [I, I, L, ctypes.POINTER(ctypes.c_double), P]
+    lib.cgx_rcp_check.argtypes = [L, P, P, P]
+    lib.cgx_noalloc_plan.argtypes = [I, I, I, L, I, I, I, ctypes.POINTER(ctypes.c_int64)]
     lib.cgx_tableau.argtypes = [I, P, P, P, P, P]
     lib.cg_react_split.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, I, P, P, P]
     lib.cg_last_error.restype = ctypes.c_char_p
@@ -342,12 +343,20 @@ def cgx_thermo_table(coef):
     return P.value, t.reshape(4 * P.value + 1, ns)
 
 
-def cgx_rate_probe(kind: int, iters: int, active_lanes: int = 32, stream=None) -> float:
-    """Test hook: throughput of one arithmetic unit of cuda:0 (0 FP64 FMA,
-    1 FP32 FMA, 2 FP64 MMA, 3 exp, 4 reciprocal); FLOP/s or evaluations/s."""
-    r = ctypes.c_double(0.0)
-    _check(load().cgx_rate_probe(kind, active_lanes, int(iters), ctypes.byref(r), _stream(stream)))
-    return r.value
+def cgx_rcp_check(x, y, stream=None):
+    """Test hook: the library's pivot reciprocal of x (CUDA tensors)."""
+    _check(load().cgx_rcp_check(x.shape[0], _dev(x), _dev(y), _stream(stream)))
+
+
+def cgx_noalloc_plan(ns: int, nr: int, mat_bytes: int, smem_limit: int, team: int, teams_per_block: int,
+                     gmres_m: int = 0) -> int:
+    """Test hook (host only): the scratch bytes cg_integrate_noalloc needs
+    for such a mechanism and launch shape (raises ChemgbError with
+    CG_ECAPACITY when the library's fixed array is too small)."""
+    need = ctypes.c_int64(0)
+    _check(load().cgx_noalloc_plan(ns, nr, mat_bytes, int(smem_limit), gmres_m, team, teams_per_block,
+                                   ctypes.byref(need)))
+    return need.value
 
 
 def cgx_tableau(method: int) -> dict:

@@ -6,7 +6,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -568,11 +567,6 @@ cg_status validate(const cg_mech_desc* d) {
 
 }  // namespace
 
-namespace cg {
-// csrc/probes.cu
-cudaError_t launch_rate_probe(int kind, int active, int64_t iters, int blocks, float* ms, cudaStream_t st);
-}  // namespace cg
-
 extern "C" {
 
 const char* cg_last_error(void) { return g_err.c_str(); }
@@ -582,6 +576,12 @@ cg_status cgx_exp_check(const cg_mech* m, int64_t n, const double* x, double* y_
     if (!m || n < 0 || (n > 0 && (!x || !y_tab || !y_lib))) return fail(CG_EINVAL, "bad arguments");
     cudaError_t e = cg::launch_exp_check(m->dm, n, x, y_tab, y_lib, (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "exp check launch");
+}
+
+cg_status cgx_rcp_check(int64_t n, const double* x, double* y, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(CG_EINVAL, "bad arguments");
+    cudaError_t e = cg::launch_rcp_check(n, x, y, (cudaStream_t)stream);
+    return e == cudaSuccess ? CG_OK : cuda_fail(e, "reciprocal check launch");
 }
 
 // ---------------------------------------------------------------------------
@@ -660,28 +660,6 @@ cg_status cgx_tableau(int method, int* s, double* A, double* b, double* bh, int*
         bh[i] = t.bh[i];
         for (int j = 0; j < 5; ++j) A[5 * i + j] = t.A[i][j];
     }
-    return CG_OK;
-}
-
-cg_status cgx_rate_probe(int kind, int active_lanes, int64_t iters, double* ops_per_second, void* stream) {
-    if (kind < 0 || kind > 4 || active_lanes < 1 || active_lanes > 32 || iters < 1 || iters > (int64_t)1 << 32 ||
-        !ops_per_second)
-        return fail(CG_EINVAL, "bad arguments");
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "device query");
-    const int blocks = 8 * sms;   // 8 blocks of 256 threads per SM
-    float ms = 0.0f;
-    if ((e = cg::launch_rate_probe(kind, active_lanes, iters, blocks, &ms, (cudaStream_t)stream)) != cudaSuccess)
-        return cuda_fail(e, "rate probe");
-    const double warps = 8.0 * blocks, lanes = 32.0 * warps, it = (double)iters;
-    const double ops[5] = {warps * active_lanes * it * 8 * 2,   // FP64 FMA: 8 chains, 2 FLOP each
-                           lanes * it * 8 * 2,                   // FP32 FMA
-                           warps * it * 4 * 2 * 8 * 8 * 4,       // 4 MMA of m8n8k4 per warp
-                           lanes * it * 8,                       // exp
-                           lanes * it * 8};                      // reciprocal
-    *ops_per_second = ops[kind] / (ms * 1e-3);
     return CG_OK;
 }
 
@@ -1425,8 +1403,12 @@ cg_status cg_autotune(cg_mech* m, const cg_integrate_opts* o, int64_t N, const d
 // device memory while they run (for example a host code whose own memory
 // manager owns the device heap, or a solver that must not enter the
 // allocator inside its time step). The per-team scratch slots and the work
-// counter live in one fixed array that every GPU loading this library holds
-// until the process exits.
+// counter live in one fixed array of this file's device module. CUDA loads
+// a module (and so allocates the array, on that device) when it is first
+// used there, or when the library loads if module loading is eager: the
+// first cg_integrate_noalloc call on a device (an N = 0 call is enough)
+// does it, and that call belongs in the caller's set-up, before it takes
+// over the device heap and before any stream capture.
 
 namespace {
 
@@ -1436,28 +1418,48 @@ constexpr int64_t kNoAllocCounterDoubles = 32;                  // first 256 byt
 
 static __device__ __align__(256) double g_noalloc[kNoAllocDoubles];
 
-std::mutex g_noalloc_mutex;
-double* g_noalloc_addr[64] = {};   // device address of g_noalloc, per device ordinal
-
-// Device address of the array on the current device, looked up once per
-// device (a host-side reference to g_noalloc is not a device address).
+// Device address of the array on the current device. The host-side name
+// g_noalloc is not a device address; the lookup is repeated on every call
+// (cheap once the module is loaded), so a device reset or a new context
+// never leaves a stale pointer.
 cg_status noalloc_array(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return fail(CG_EUNSUPPORTED, "device ordinal %d above 63", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (no-alloc scratch)");
-        g_noalloc_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_noalloc_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (no-alloc scratch)");
+    *out = static_cast<double*>(p);
+    return CG_OK;
+}
+
+// Scratch an integration launch of these tasks needs from the fixed array:
+// one slot per team of every resident block, at least one block's worth.
+cg_status noalloc_plan(const cg::Tasks& tasks, int team, int tpb, int64_t* need_doubles) {
+    const int64_t per_block = cg::integrate_slot_doubles(tasks) * cg::integrate_tpb(tasks, team, tpb);
+    const int64_t avail = kNoAllocDoubles - kNoAllocCounterDoubles;
+    if (need_doubles) *need_doubles = per_block;
+    if (per_block > avail)
+        return fail(CG_ECAPACITY,
+                    "one block of this mechanism needs %lld bytes of scratch; cg_integrate_noalloc has %lld "
+                    "(raise cg_mech_set_smem_limit or use cg_integrate)",
+                    (long long)(per_block * (int64_t)sizeof(double)), (long long)(avail * (int64_t)sizeof(double)));
     return CG_OK;
 }
 
 }  // namespace
+
+extern "C" cg_status cgx_noalloc_plan(int ns, int nr, int mat_bytes, int64_t smem_limit, int gmres_m, int team,
+                                      int teams_per_block, int64_t* scratch_bytes) {
+    if (ns < 1 || nr < 0 || (mat_bytes != 4 && mat_bytes != 8) || smem_limit < 1024 || gmres_m < 0 ||
+        (team != 32 && team != 64 && team != 128 && team != 256) || teams_per_block < 1)
+        return fail(CG_EINVAL, "bad arguments");
+    cg::Tasks tasks;
+    tasks.count = 1;
+    tasks.total = 1;
+    tasks.t[0].L = make_layout(ns, nr, mat_bytes, (size_t)smem_limit, false, gmres_m);
+    int64_t need = 0;
+    const cg_status st = noalloc_plan(tasks, team, teams_per_block, &need);
+    if (scratch_bytes) *scratch_bytes = need * (int64_t)sizeof(double);
+    return st;
+}
 
 extern "C" cg_status cg_integrate_noalloc(const cg_mech* m, const cg_integrate_opts* o, int64_t N,
                                           double* T, double* Y, const double* p_or_rho,
@@ -1467,25 +1469,19 @@ extern "C" cg_status cg_integrate_noalloc(const cg_mech* m, const cg_integrate_o
     cg_status st = make_params(o, P);
     if (st != CG_OK) return st;
     if (N < 0) return fail(CG_EINVAL, "N < 0");
+    double* base = nullptr;   // also on N = 0: the set-up call that loads the array
+    if ((st = noalloc_array(&base)) != CG_OK) return st;
     if (N == 0) return CG_OK;
     if (!T || !Y || !p_or_rho) return fail(CG_EINVAL, "NULL array");
     cg::Tasks tasks;
     tasks.count = 1;
     tasks.total = N;
     tasks.t[0] = make_task(m, P, N, 0, T, Y, p_or_rho, cell_status, cell_stats);
-    const int64_t slot = cg::integrate_slot_doubles(tasks) * (m->dm.team > 32 ? 1 : m->tpb);
-    const int64_t avail = kNoAllocDoubles - kNoAllocCounterDoubles;
-    if (slot > avail)
-        return fail(CG_ECAPACITY,
-                    "one cell of this mechanism needs %lld bytes of scratch; cg_integrate_noalloc has %lld "
-                    "(raise cg_mech_set_smem_limit or use cg_integrate)",
-                    (long long)(slot * (int64_t)sizeof(double)), (long long)(avail * (int64_t)sizeof(double)));
-    double* base = nullptr;
-    if ((st = noalloc_array(&base)) != CG_OK) return st;
+    if ((st = noalloc_plan(tasks, m->dm.team, m->tpb, nullptr)) != CG_OK) return st;
     unsigned long long* counter = reinterpret_cast<unsigned long long*>(base);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (work counter)");
-    e = cg::launch_integrate_on(tasks, P, m->dm.team, m->tpb, base + kNoAllocCounterDoubles, avail, counter,
-                                (cudaStream_t)stream);
+    e = cg::launch_integrate_on(tasks, P, m->dm.team, m->tpb, base + kNoAllocCounterDoubles,
+                                kNoAllocDoubles - kNoAllocCounterDoubles, counter, (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch (no-alloc)");
 }

@@ -78,6 +78,7 @@ cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const d
                                const double* Y, double* T, int iters, cudaStream_t st);
 cudaError_t launch_exp_check(const DevMech& M, int64_t n, const double* x, double* y_tab, double* y_lib,
                              cudaStream_t st);
+cudaError_t launch_rcp_check(int64_t n, const double* x, double* y, cudaStream_t st);
 // All tasks share one team size; `persistent` selects the resident grid with
 // the work counter (always used when a cell needs global scratch).
 cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, int tpb, bool persistent,
@@ -87,7 +88,11 @@ cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, i
 // cudaErrorMemoryAllocation: not even one team's slot fits in the scratch.
 cudaError_t launch_integrate_on(const Tasks& tasks, const IntParams& P, int team, int tpb, double* scratch,
                                 int64_t scratch_doubles, unsigned long long* counter, cudaStream_t st);
+// Global scratch of one team's slot (doubles) and the teams per block an
+// integration launch of `team` threads per cell actually uses (the requested
+// count, lowered until the block's shared memory fits in 227 KB).
 int64_t integrate_slot_doubles(const Tasks& tasks);
+int integrate_tpb(const Tasks& tasks, int team, int tpb);
 // Operator-split reaction step (persistent launch, `team` threads per cell).
 cudaError_t launch_react_split(const SplitTask& t, const IntParams& P, int team, int tpb, cudaStream_t st);
 // Backward sweep of the discrete adjoint over the cells of t (persistent

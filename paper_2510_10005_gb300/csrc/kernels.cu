@@ -12,6 +12,7 @@
 //   temperature_kernel     T from (e, Y) by Newton (Section 2.1)
 //   integrate_kernel       backward Euler / SDIRK over dt (Section 3.2, App. A),
 //                          for up to kMaxTasks mechanisms in one launch
+//   exp_check_kernel, rcp_check_kernel   test hooks: exp_tab, rcp_nr
 #include "stepper.cuh"
 
 namespace cg {
@@ -105,6 +106,12 @@ __global__ void exp_check_kernel(int64_t n, const double* __restrict__ tab, cons
         y_tab[i] = exp_tab(x[i], tab);
         y_lib[i] = exp(x[i]);
     }
+}
+
+// rcp_nr on the same arguments (test hook).
+__global__ void rcp_check_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = rcp_nr(x[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,6 +248,13 @@ cudaError_t launch_exp_check(const DevMech& M, int64_t n, const double* x, doubl
     return cudaGetLastError();
 }
 
+cudaError_t launch_rcp_check(int64_t n, const double* x, double* y, cudaStream_t st) {
+    const int64_t blocks = n > 0 ? (n + 255) / 256 : 0;
+    if (blocks == 0) return cudaSuccess;
+    rcp_check_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(n, x, y);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const double* e,
                                const double* Y, double* T, int iters, cudaStream_t st) {
     const int wpb = 4;
@@ -250,18 +264,34 @@ cudaError_t launch_temperature(const DevMech& M, int reactor, int64_t N, const d
     return cudaGetLastError();
 }
 
+// Global scratch of one team's slot (doubles, a multiple of 32 so that slots
+// stay 256-byte aligned): the largest of the tasks.
+int64_t integrate_slot_doubles(const Tasks& tasks) {
+    int64_t g = 0;
+    for (int k = 0; k < tasks.count; ++k) g = g > tasks.t[k].L.gtotal ? g : tasks.t[k].L.gtotal;
+    return round_up(g, 32);
+}
+
+// Shared-memory stride (doubles) of one team's slice: the largest of the tasks.
+static int integrate_sstride(const Tasks& tasks) {
+    int sstride = 0;
+    for (int k = 0; k < tasks.count; ++k) sstride = sstride > tasks.t[k].L.stotal ? sstride : tasks.t[k].L.stotal;
+    return sstride;
+}
+
+int integrate_tpb(const Tasks& tasks, int team, int tpb) {
+    if (team > 32) return 1;
+    const int sstride = integrate_sstride(tasks);
+    while (tpb > 1 && (size_t)tpb * sstride * sizeof(double) > 227 * 1024) --tpb;   // larger layouts (GMRES)
+    return tpb;
+}
+
 template <int TEAM, class MT>
 static cudaError_t launch_integrate_t(const Tasks& tasks, const IntParams& P, int tpb, bool persistent,
                                       cudaStream_t st) {
-    if (TEAM > 32) tpb = 1;
-    int sstride = 0;
-    int64_t gstride = 0;
-    for (int k = 0; k < tasks.count; ++k) {
-        sstride = sstride > tasks.t[k].L.stotal ? sstride : tasks.t[k].L.stotal;
-        gstride = gstride > tasks.t[k].L.gtotal ? gstride : tasks.t[k].L.gtotal;
-    }
-    gstride = round_up(gstride, 32);   // 256-byte aligned slots
-    while (tpb > 1 && (size_t)tpb * sstride * sizeof(double) > 227 * 1024) --tpb;   // larger layouts (GMRES)
+    tpb = integrate_tpb(tasks, TEAM, tpb);
+    const int sstride = integrate_sstride(tasks);
+    const int64_t gstride = integrate_slot_doubles(tasks);   // 256-byte aligned slots
     const void* fn = (const void*)integrate_kernel<TEAM, MT>;
     const size_t smem = (size_t)tpb * sstride * sizeof(double);
     cudaError_t e = set_smem(fn, smem);
@@ -291,15 +321,9 @@ template <int TEAM, class MT>
 static cudaError_t launch_integrate_on_t(const Tasks& tasks, const IntParams& P, int tpb, double* scratch,
                                          int64_t scratch_doubles, unsigned long long* counter,
                                          cudaStream_t st) {
-    if (TEAM > 32) tpb = 1;
-    int sstride = 0;
-    int64_t gstride = 0;
-    for (int k = 0; k < tasks.count; ++k) {
-        sstride = sstride > tasks.t[k].L.stotal ? sstride : tasks.t[k].L.stotal;
-        gstride = gstride > tasks.t[k].L.gtotal ? gstride : tasks.t[k].L.gtotal;
-    }
-    gstride = round_up(gstride, 32);
-    while (tpb > 1 && (size_t)tpb * sstride * sizeof(double) > 227 * 1024) --tpb;
+    tpb = integrate_tpb(tasks, TEAM, tpb);
+    const int sstride = integrate_sstride(tasks);
+    const int64_t gstride = integrate_slot_doubles(tasks);
     const void* fn = (const void*)integrate_kernel<TEAM, MT>;
     const size_t smem = (size_t)tpb * sstride * sizeof(double);
     cudaError_t e = set_smem(fn, smem);
@@ -328,14 +352,6 @@ cudaError_t launch_integrate_on(const Tasks& tasks, const IntParams& P, int team
 #define CALL(TM) launch_integrate_on_t<TM, double>(tasks, P, tpb, scratch, scratch_doubles, counter, st)
     CG_DISPATCH_TEAM(team, CALL)
 #undef CALL
-}
-
-// Shared-memory and scratch need of one slot (doubles), for callers that
-// bring their own memory.
-int64_t integrate_slot_doubles(const Tasks& tasks) {
-    int64_t g = 0;
-    for (int k = 0; k < tasks.count; ++k) g = g > tasks.t[k].L.gtotal ? g : tasks.t[k].L.gtotal;
-    return round_up(g, 32);
 }
 
 cudaError_t launch_integrate(const Tasks& tasks, const IntParams& P, int team, int tpb, bool persistent,

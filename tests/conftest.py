@@ -23,3 +23,16 @@ def mechs():
 def ref(mechs):
     import oracle
     return {k: oracle.RefMech(m) for k, m in mechs.items()}
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """With CHEMGB_PARITY_REPORT set, write the largest errors the parity
+    checks measured (tests/parity.py) to that file as JSON."""
+    path = os.environ.get("CHEMGB_PARITY_REPORT")
+    if not path:
+        return
+    import json
+    import parity
+    if parity.REPORT:
+        with open(path, "w") as f:
+            json.dump(parity.REPORT, f, indent=1, sort_keys=True)

@@ -113,9 +113,34 @@ def test_set_thermo_checks_arguments(lib):
     assert b"mech is NULL" in lib.cg_last_error()
 
 
-def test_rate_probe_checks_arguments(lib):
-    """The throughput probe refuses bad arguments before any device work."""
-    r = ctypes.c_double(0.0)
-    for kind, lanes, iters in ((5, 32, 10), (-1, 32, 10), (0, 0, 10), (0, 33, 10), (0, 32, 0), (0, 32, 1 << 40)):
-        assert lib.cgx_rate_probe(kind, lanes, iters, ctypes.byref(r), None) == chemgb.CG_EINVAL
-    assert lib.cgx_rate_probe(0, 32, 10, None, None) == chemgb.CG_EINVAL
+def test_check_hooks_refuse_bad_arguments(lib):
+    """The reciprocal hook refuses bad arguments before any device work."""
+    assert lib.cgx_rcp_check(-1, None, None, None) == chemgb.CG_EINVAL
+    assert lib.cgx_rcp_check(4, None, None, None) == chemgb.CG_EINVAL
+    assert lib.cgx_rcp_check(0, None, None, None) == chemgb.CG_OK
+
+
+def test_noalloc_capacity_plan(lib):
+    """cg_integrate_noalloc's capacity check (host planner): the 53-species
+    mechanism needs no scratch with its arrays in shared memory, and one
+    slot per cell of a block when they spill; a layout too large for the
+    fixed 32 MiB array (1023 species, 400,000 reactions, everything spilled)
+    gets CG_ECAPACITY with both sizes in the message; teams per block that
+    the launcher lowers for shared memory are lowered here too."""
+    assert chemgb.cgx_noalloc_plan(53, 325, 8, 227 * 1024, 64, 1) == 0
+    one = chemgb.cgx_noalloc_plan(53, 325, 8, 16 * 1024, 64, 1)
+    assert one > 0 and one % 256 == 0
+    assert chemgb.cgx_noalloc_plan(53, 325, 8, 16 * 1024, 32, 4) == 4 * one
+    # GMRES(64) with a 100 KB limit: 97 KB of shared memory per cell, so of
+    # four cells per block requested two fit in 227 KB, each with its slot
+    lay = chemgb.cgx_layout(53, 325, 8, 100 * 1024, gmres_m=64)
+    assert lay["glob"] > 0 and 2 * lay["smem"] * 8 <= 227 * 1024 < 3 * lay["smem"] * 8
+    slot = chemgb.cgx_noalloc_plan(53, 325, 8, 100 * 1024, 32, 1, gmres_m=64)
+    assert slot > 0 and chemgb.cgx_noalloc_plan(53, 325, 8, 100 * 1024, 32, 4, gmres_m=64) == 2 * slot
+    with pytest.raises(chemgb.ChemgbError) as e:
+        chemgb.cgx_noalloc_plan(1023, 400000, 8, 1024, 64, 1)
+    assert e.value.code == chemgb.CG_ECAPACITY
+    assert "cg_integrate_noalloc has 33554176" in str(e.value)
+    with pytest.raises(chemgb.ChemgbError) as e:
+        chemgb.cgx_noalloc_plan(53, 325, 8, 16 * 1024, 48, 1)
+    assert e.value.code == chemgb.CG_EINVAL

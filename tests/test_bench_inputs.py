@@ -55,7 +55,7 @@ def test_reference_arm_takes_the_workload_options(capsys, monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "1")
     monkeypatch.setenv("RANK", "0")
     args = argparse.Namespace(config=1, cells=64, method=None, linear=None, prec=None, surface="split",
-                              sri_plog=True, thermo_degree=None, ref_sample=8, steps=1, warmup=0, gpus=1)
+                              sri_plog=True, thermo_degree=None, cpu_sample=8, steps=1, warmup=0, gpus=1)
     bench.run_reference(args)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["config"]["workload"] == bench.full_workload_name(args)
@@ -82,23 +82,21 @@ def test_traffic_only_for_the_captured_kernel_sources(monkeypatch):
     assert bench.measured_traffic(2, 1 << 20) is None
 
 
-def test_cpu_baseline_sample_is_sized_by_time():
-    """cpu_baseline: a pilot gives the oracle's rate, and the sample is then
-    sized for the requested seconds of CPU work (capped at every cell);
-    an explicit cell count overrides the sizing."""
-    import time as _t
-    calls = []
+def test_cpu_baseline_is_a_fixed_sample_and_a_median():
+    """cpu_baseline and the reference arm time the same fixed sample of each
+    workload (cells evenly spaced through the field) and report the median
+    of repeated timings."""
+    calls, seq = [], iter([3.0, 1.0, 2.0, 9.0, 2.5])
 
-    def run(k):                       # a stand-in oracle at 1000 cells/s
+    def run(k):                       # a stand-in oracle with varying timings
         calls.append(k)
-        return k / 1000.0, k
-    k, el = bench.sized_sample(run, 10 ** 6, 8, 0, 15.0)
-    assert calls[0] == 16 and k == 15000 and el == pytest.approx(15.0)
-    calls.clear()
-    assert bench.sized_sample(run, 5000, 8, 0, 15.0)[0] == 5000          # capped at every cell
-    assert bench.sized_sample(run, 10 ** 6, 8, 300, 15.0)[0] == 300       # explicit count
+        return next(seq), k
+    k, med, times = bench.median_timing(run, 4096, 5)
+    assert calls == [4096] * 5 and k == 4096 and med == 2.5 and len(times) == 5
+    assert bench.CPU_SAMPLE[2] == 4096 and bench.CPU_SAMPLE[5] == 1024 and bench.CPU_SAMPLE[4] == 256
+    idx = bench.sample_indices(1 << 20, 4096)
+    assert len(idx) == 4096 and idx[0] == 0 and idx[-1] == (1 << 20) - 1 and np.all(np.diff(idx) > 0)
+    assert len(bench.sample_indices(100, 4096)) == 100          # never more than every cell
     parts = bench.make_workload(1, 4096)
-    opts = bench.opts_dict(1, 0)
-    t0 = _t.perf_counter()
-    k, el = bench.sized_sample(lambda n: bench.cpu_oracle_sample(parts, opts, n, 4)[1:], 4096, 4, 0, 0.3)
-    assert 16 <= k <= 4096 and el > 0 and _t.perf_counter() - t0 < 10
+    v, el, k = bench.cpu_oracle_sample(parts, bench.opts_dict(1, 0), 256, 4)
+    assert k == 256 and el > 0 and v == pytest.approx(k / el)

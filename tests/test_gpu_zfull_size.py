@@ -2,13 +2,17 @@
 benchmark times, on sampled outputs the oracle computes cell by cell:
 
 * the 53-species flame field, 1,048,576 cells, adaptive SDIRK-4 in FP64
-  (the default bench line): T within rtol, Y within rtol (absolute),
+  (the default bench line): 1024 cells evenly spaced through the field (so
+  in proportion from its unburnt, front and burnt regions), T and every Y_k
+  within the integrator's own element-wise weight (tests/parity.py),
   statuses identical;
 * the heavy-tailed batch of 53 + 9 species, 2 x 1,048,576 cells, one
-  persistent launch with the FP32 Newton matrix: within rtol of the FP64
-  oracle;
-* the adjoint workload, 65,536 cells over 1e-4 s: sampled dL/dT0, dL/dY0 and
-  per-cell dL/dtheta within 1e-6 of the largest entry of each kind.
+  persistent launch with the FP32 Newton matrix: 1024 cells per mechanism,
+  the same element-wise bound against the FP64 oracle;
+* the adjoint workload, 65,536 cells over 1e-4 s: 64 sampled cells,
+  dL/dT0, dL/dY0 and the per-cell dL/dtheta element-wise within 1e-6 plus
+  1e-9 of the largest entry of each kind, on the cells whose accepted step
+  count equals the oracle's.
 
 Slow: a 1,048,576-cell launch takes about 45 s, the batch about 30 s plus
 the autotuning, the adjoint about 15 s. Collected after the other GPU
@@ -21,6 +25,7 @@ import pytest
 import bench
 import oracle
 from paper_2510_10005_gb300 import chemgb
+from parity import check_adaptive, check_elementwise
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -43,15 +48,14 @@ def test_full_size_flame_field():
     st = torch.empty(len(T), dtype=torch.int32, device=DEV)
     chemgb.cg_integrate(h, chemgb.make_opts(**o), Tt, Yt, pt, st)
     torch.cuda.synchronize()
-    idx = np.linspace(0, len(T) - 1, 96).astype(np.int64)
+    idx = np.linspace(0, len(T) - 1, 1024).astype(np.int64)
     To, Yo, so, _ = oracle.RefMech(m).integrate(T[idx], Y[idx], p[idx], bench.oracle_opts(o), nthreads=THREADS)
     sel = torch.as_tensor(idx, device=DEV)
     Tg = Tt.index_select(0, sel).cpu().numpy()
     Yg = Yt.index_select(1, sel).cpu().numpy().T
     assert np.array_equal(st.index_select(0, sel).cpu().numpy(), so) and np.all(so == 0)
     assert int((st != 0).sum()) == 0
-    np.testing.assert_allclose(Tg, To, rtol=o["rtol"])
-    assert np.max(np.abs(Yg - Yo)) <= o["rtol"]
+    check_adaptive("full_size_flame_field_1M", m, Tg, Yg, To, Yo, p[idx], o["reactor"], o["rtol"], o["atol"])
 
 
 def test_full_size_mixed_batch_fp32():
@@ -76,12 +80,12 @@ def test_full_size_mixed_batch_fp32():
     chemgb.cg_integrate_batch(handles, og, Ts, Ys, ps, sts)
     torch.cuda.synchronize()
     for (m, T, Y, p), Tt, Yt, st in zip(parts, Ts, Ys, sts):
-        idx = np.linspace(0, len(T) - 1, 48).astype(np.int64)
+        idx = np.linspace(0, len(T) - 1, 1024).astype(np.int64)
         To, Yo, so, _ = oracle.RefMech(m).integrate(T[idx], Y[idx], p[idx], bench.oracle_opts(o), nthreads=THREADS)
         sel = torch.as_tensor(idx, device=DEV)
         assert np.array_equal(st.index_select(0, sel).cpu().numpy(), so)
-        np.testing.assert_allclose(Tt.index_select(0, sel).cpu().numpy(), To, rtol=o["rtol"])
-        assert np.max(np.abs(Yt.index_select(1, sel).cpu().numpy().T - Yo)) <= o["rtol"]
+        check_adaptive(f"full_size_fp32_batch_{m.ns}sp", m, Tt.index_select(0, sel).cpu().numpy(),
+                       Yt.index_select(1, sel).cpu().numpy().T, To, Yo, p[idx], o["reactor"], o["rtol"], o["atol"])
 
 
 def test_full_size_adjoint():
@@ -110,14 +114,22 @@ def test_full_size_adjoint():
                                 dT0, dY0, dth, dcell, ast)
     torch.cuda.synchronize()
     assert int((st != 0).sum()) == 0 and int((ast != 0).sum()) == 0
-    idx = np.linspace(0, N - 1, 8).astype(np.int64)
-    oT, oY, og_, ost = oracle.RefMech(m).adjoint_TY(T[idx], Y[idx], p[idx], gT[idx], np.zeros((len(idx), m.ns)),
-                                                    bench.oracle_opts(o), nthreads=THREADS)
+    idx = np.linspace(0, N - 1, 64).astype(np.int64)
+    r = oracle.RefMech(m)
+    oo = bench.oracle_opts(o)
+    oT, oY, og_, ost = r.adjoint_TY(T[idx], Y[idx], p[idx], gT[idx], np.zeros((len(idx), m.ns)), oo,
+                                    nthreads=THREADS)
     assert np.all(ost == 0)
+    # both sides differentiate their own accepted steps: compare the cells
+    # whose step counts agree (an accept/reject flip at the threshold gives
+    # another, equally valid, step sequence)
+    C0 = r.concentrations(T[idx], Y[idx], p[idx], o["reactor"])
+    _, _, _, hn = r.integrate_hist(np.concatenate([T[idx, None], C0], axis=1), oo, cap=cap, nthreads=THREADS)
     sel = torch.as_tensor(idx, device=DEV)
-    rel = lambda a, b: np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
-    assert rel(dT0.index_select(0, sel).cpu().numpy(), oT) < 1e-6
-    assert rel(dY0.index_select(1, sel).cpu().numpy().T, oY) < 1e-6
+    same = ckpt_n.index_select(0, sel).cpu().numpy() == hn
+    assert same.mean() >= 0.9, (same.mean(), ckpt_n.index_select(0, sel).cpu().numpy(), hn)
+    check_elementwise("full_size_adjoint_dT0", dT0.index_select(0, sel).cpu().numpy()[same], oT[same], 1e-6, 1e-9)
+    check_elementwise("full_size_adjoint_dY0", dY0.index_select(1, sel).cpu().numpy().T[same], oY[same], 1e-6, 1e-9)
     gc = np.moveaxis(dcell.index_select(2, sel).cpu().numpy(), 2, 0)
-    for k in range(3):
-        assert rel(gc[:, :, k], og_[:, :, k]) < 1e-6
+    for k, name in enumerate(("lnA", "b", "Ea")):
+        check_elementwise(f"full_size_adjoint_dtheta_{name}", gc[same][:, :, k], og_[same][:, :, k], 1e-6, 1e-9)

@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from paper_2510_10005_gb300 import chemgb, inputs
+from parity import check_adaptive, check_fixed
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -109,8 +110,7 @@ def test_backward_euler_any_degree(refits):
     To, Yo, so, _ = r.integrate(T, Y, p, o, nthreads=8)
     Tg, Yg, sg = run(h, o, T, Y, p)
     np.testing.assert_array_equal(sg, so)
-    np.testing.assert_allclose(Tg, To, rtol=1e-9)
-    assert np.max(np.abs(Yg - Yo)) < 1e-9
+    check_fixed("be_thermo_degree_15", Tg, Yg, To, Yo, 1e-9, 1e-20)
 
 
 def test_adaptive_flame_any_degree(refits):
@@ -122,8 +122,7 @@ def test_adaptive_flame_any_degree(refits):
     To, Yo, so, _ = r.integrate(T[idx], Y[idx], p[idx], o, nthreads=8)
     Tg, Yg, sg = run(h, o, T[idx], Y[idx], p[idx])
     np.testing.assert_array_equal(sg, so)
-    np.testing.assert_allclose(Tg, To, rtol=1e-6)
-    assert np.max(np.abs(Yg - Yo)) < 1e-6
+    check_adaptive("adaptive_flame_thermo_degree_7", m, Tg, Yg, To, Yo, p[idx], o["reactor"], o["rtol"], o["atol"])
 
 
 def test_split_step_any_degree(refits):

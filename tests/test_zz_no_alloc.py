@@ -39,6 +39,20 @@ def call(fn, h, o, T, Y, p):
     return Tt.cpu().numpy(), Yt.cpu().numpy().T, st.cpu().numpy(), stats.cpu().numpy().T
 
 
+def test_noalloc_setup_call_with_no_cells():
+    """A call with N = 0 is the set-up call: it loads the fixed array on the
+    device (and so does the allocation a caller's memory manager must see
+    before it takes over the heap), and integrates nothing."""
+    mech = inputs.gen_mechanism("h2")
+    h = chemgb.cg_mech_create(mech)
+    lib = chemgb.load(build_if_missing=True)
+    o = chemgb.make_opts(**ADAPT)
+    code = lib.cg_integrate_noalloc(h.ptr, ctypes.byref(o), 0, None, None, None, None, None,
+                                    torch.cuda.current_stream().cuda_stream)
+    assert code == chemgb.CG_OK, lib.cg_last_error().decode()
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("smem_limit", [None, 16 * 1024])
 @pytest.mark.parametrize("precision", [chemgb.CG_FP64, chemgb.CG_FP32LU])
 def test_noalloc_matches_integrate_twice(smem_limit, precision):

@@ -416,6 +416,8 @@ def run_gpu(args):
             chemgb.cg_mech_set_smem_limit(h, args.smem_limit)
         if args.team:
             chemgb.cg_mech_set_launch(h, args.team, args.tpb)
+        if args.lu_panel is not None:
+            chemgb.cg_mech_set_lu_panel(h, args.lu_panel)
         N = len(T)
         b = dict(T0=torch.tensor(T, dtype=torch.float64, device=dev),
                  Y0=torch.tensor(np.ascontiguousarray(Y.T), dtype=torch.float64, device=dev),
@@ -446,9 +448,10 @@ def run_gpu(args):
         for h in handles[1:]:
             chemgb.cg_mech_set_launch(h, team, tpb if team == 32 else 1)
         tuned = {"team": team, "teams_per_block": tpb, "sample_ms": ms}
-        try:   # the shared-memory limit per cell the tuner chose
+        try:   # the shared-memory limit per cell and the LU panel width the tuner chose
             with open(cache) as f:
-                tuned["smem_limit"] = json.load(f)["smem_limit"]
+                c = json.load(f)
+            tuned["smem_limit"], tuned["lu_panel"] = c["smem_limit"], c["lu_panel"]
         except (OSError, ValueError, KeyError):
             pass
 
@@ -588,6 +591,8 @@ def run_gpu(args):
         "cells_failed": failed,
         "stats_mean": stat_means,
     }
+    line["launch"] = [dict(zip(("team", "teams_per_block"), chemgb.cg_mech_get_launch(h)),
+                           lu_panel=chemgb.cg_mech_get_lu_panel(h)) for h in handles]
     if tuned:
         line["autotune"] = tuned
     if graph is not None:
@@ -834,6 +839,8 @@ def main():
     ap.add_argument("--cpu-repeats", type=int, default=5, help="timings of the cpu_baseline sample (median)")
     ap.add_argument("--cpu-1core-cells", type=int, default=256,
                     help="cells of the one-core oracle timing reported beside cpu_baseline (0: skip)")
+    ap.add_argument("--lu-panel", type=int, default=None,
+                    help="panel width of the blocked LU (0: unblocked; default: the library's choice)")
     ap.add_argument("--smem-limit", type=int, default=0,
                     help="shared memory per cell in bytes before arrays go to global scratch (default: 227 KB)")
     ap.add_argument("--no-cpu", action="store_true")

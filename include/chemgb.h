@@ -155,25 +155,44 @@ int cg_mech_n_reactions(const cg_mech *mech);
 /* Launch shape of every kernel that uses this mechanism: `team` threads
  * (32, 64, 128 or 256) cooperate on one cell and `teams_per_block` cells
  * share a block (must be 1 when team > 32). The default is one warp per cell
- * up to 24 unknowns and two warps per cell above. Changing the team size
+ * up to 24 unknowns, two warps per cell up to 96 and eight above. Changing
+ * the team size
  * rebuilds the assembly schedules (synchronises the device); no call using
  * the mechanism may run concurrently. Results do not depend on the shape
  * beyond the summation order of team-wide reductions. Errors: CG_EINVAL
  * (bad shape), CG_ECAPACITY (shared memory), CG_ENOMEM, CG_ECUDA. This is
  * a launch-tuning hook, not part of the method of the paper. */
 cg_status cg_mech_set_launch(cg_mech *mech, int team, int teams_per_block);
-/* Shared memory a cell may use (bytes, 1 KiB .. 227 KiB; default 227 KiB).
- * A cell's arrays are placed hottest first (Newton matrix, state vectors,
- * thermo, stage derivatives, per-reaction data); those beyond the limit go
- * to a per-team slot of global scratch that the library allocates
- * stream-ordered for each launch (mechanisms whose Newton matrix alone
- * nears the limit, such as 160 species in FP64, always spill). A lower
- * limit trades L2 traffic for more cells per SM. Same concurrency rule as
- * cg_mech_set_launch. Launch tuning, not part of the paper's method. */
+/* Shared memory a cell may use (bytes, 1 KiB .. 227 KiB). A cell's arrays
+ * are placed hottest first (Newton matrix, state vectors, thermo, stage
+ * derivatives, per-reaction data); those beyond the limit go to a per-team
+ * slot of global scratch that the library allocates stream-ordered for each
+ * launch (mechanisms whose Newton matrix alone nears the limit, such as 160
+ * species in FP64, always spill). A lower limit trades L2 traffic for more
+ * cells per SM. Default: 227 KiB, except when the per-reaction block (9 nr
+ * doubles) is at least 8 KiB of a per-cell total of 40 KiB or more; then
+ * the limit keeps everything but that block in shared memory (53 species /
+ * 325 reactions: 33 KiB per cell, 6 cells per SM instead of 4). Same
+ * concurrency rule as cg_mech_set_launch. Launch tuning, not part of the
+ * paper's method. */
 cg_status cg_mech_set_smem_limit(cg_mech *mech, int64_t bytes);
 
 /* Current launch shape; returns 0, or -1 for a NULL mechanism. */
 int cg_mech_get_launch(const cg_mech *mech, int *team, int *teams_per_block);
+
+/* Panel width of the dense LU with partial pivoting of the Newton matrix
+ * (Section 3.4; the direct solver whose O(n^3) cost the paper names):
+ * 0 factors column by column with a rank-one update of the whole trailing
+ * block after each; nb = 1..64 factors panels of nb columns and then
+ * updates the trailing block once per panel from register tiles (a
+ * right-looking blocked LU). Both apply the same fused multiply-adds to
+ * every element in the same order, so the factors, the pivots and every
+ * result are identical to the last bit; only the memory traffic and the
+ * number of synchronisations differ. Default: 0 below 96 unknowns, 16
+ * above. Same concurrency rule as cg_mech_set_launch. Errors: CG_EINVAL.
+ * cg_mech_get_lu_panel returns the width, or -1 for a NULL mechanism. */
+cg_status cg_mech_set_lu_panel(cg_mech *mech, int nb);
+int cg_mech_get_lu_panel(const cg_mech *mech);
 
 /* Source term S(y) = (omega_T, dC_1/dt .. dC_ns/dt) for N cells
  * (Section 2.2, eqs. chemical-reaction-rate-of-progress, temperature_source;
@@ -232,8 +251,10 @@ void cg_integrate_opts_default(cg_integrate_opts *opts);
 /* Autotuner: integrates a caller-given sample of cells (device arrays as in
  * cg_integrate; not modified: each timing runs on a copy) once per launch
  * shape -- threads per cell {32, 64, 128, 256}, cells per block {1, 2, 4}
- * for one-warp teams, shared-memory limit {227, 113, 48} KiB -- and applies
- * the fastest to the mechanism (cg_mech_set_launch, cg_mech_set_smem_limit).
+ * for one-warp teams, shared-memory limit {227, 113, 48} KiB and the
+ * mechanism's default, LU panel width {0, 16} from 48 unknowns on (LU
+ * only) -- and applies the fastest to the mechanism (cg_mech_set_launch,
+ * cg_mech_set_smem_limit, cg_mech_set_lu_panel).
  * Synchronises `stream`; allocates two sample-sized work arrays for its
  * duration. With cache_json != NULL, a file written by an earlier call for
  * a mechanism of the same size and the same method and precision is applied

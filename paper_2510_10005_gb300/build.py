@@ -2,7 +2,8 @@
 
 The library is compiled from paper_2510_10005_gb300/csrc into
 paper_2510_10005_gb300/_build/ (git-ignored). Translation units compile in
-parallel; nothing is installed outside the tree.
+parallel (instances.cu once per team size and Newton-matrix type, as many
+at a time as there are cores); nothing is installed outside the tree.
 """
 from __future__ import annotations
 
@@ -29,12 +30,30 @@ def _nvcc() -> str:
     return "nvcc"
 
 
+# instances.cu is compiled once per team size and Newton-matrix type
+INSTANCES = [(team, mt) for team in (32, 64, 128, 256) for mt in ("double", "float")]
+
+
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(p for p in glob.glob(os.path.join(CSRC, "*.cu")) if os.path.basename(p) != "instances.cu")
+
+
+def _jobs():
+    """(command, object) of every translation unit, slowest first."""
+    jobs = []
+    inst = os.path.join(CSRC, "instances.cu")
+    for team, mt in INSTANCES:
+        obj = os.path.join(BUILD, f"instances_t{team}_{'f64' if mt == 'double' else 'f32'}.o")
+        defs = [f"-DCG_TEAM={team}", f"-DCG_MT={mt}", f"-DCG_MT_F64={1 if mt == 'double' else 0}"]
+        jobs.append((NVCC_FLAGS + defs + ["-c", inst, "-o", obj], obj))
+    for src in _sources():
+        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        jobs.append((NVCC_FLAGS + ["-c", src, "-o", obj], obj))
+    return jobs
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) \
+    return glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) \
         + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
@@ -50,17 +69,29 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    procs, objs = [], []
-    for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-    for cmd, p in procs:
+    jobs = _jobs()
+    objs = [obj for _, obj in jobs]
+    # an object is rebuilt when it is older than its source or any header
+    headers = [p for p in _deps() if not p.endswith(".cu")]
+    newest_header = max([os.path.getmtime(p) for p in headers] + [0.0])
+    def fresh(flags, obj):
+        src = flags[flags.index("-c") + 1]
+        return (not force and os.path.exists(obj)
+                and os.path.getmtime(obj) > max(newest_header, os.path.getmtime(src)))
+    width = max(1, os.cpu_count() or 1)
+    running, pending = [], [j for j in jobs if not fresh(*j)]
+    while pending or running:
+        while pending and len(running) < width:
+            flags, _ = pending.pop(0)
+            cmd = [nvcc] + flags
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            running.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        cmd, p = running.pop(0)
         out, _ = p.communicate()
         if p.returncode != 0:
+            for _, q in running:
+                q.kill()
             raise RuntimeError("nvcc failed: " + " ".join(cmd) + "\n" + out.decode(errors="replace"))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs

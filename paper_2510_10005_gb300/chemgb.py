@@ -57,7 +57,8 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_integrate_noalloc", "cg_autotune", "cg_last_error", "cg_integrate_ckpt",
             "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
             "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo",
-            "cgx_thermo_table", "cgx_tableau", "cgx_rcp_check", "cgx_noalloc_plan")
+            "cgx_thermo_table", "cgx_tableau", "cgx_rcp_check", "cgx_noalloc_plan", "cg_mech_set_lu_panel",
+            "cg_mech_get_lu_panel")
 
 
 def library_path() -> str:
@@ -84,6 +85,8 @@ def load(build_if_missing: bool = False):
     lib.cg_mech_set_launch.argtypes = [P, I, I]
     lib.cg_mech_get_launch.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.cg_mech_set_smem_limit.argtypes = [P, L]
+    lib.cg_mech_set_lu_panel.argtypes = [P, I]
+    lib.cg_mech_get_lu_panel.argtypes = [P]
     lib.cg_integrate_batch.argtypes = [I, P, P, P, P, P, P, P, ctypes.POINTER(cg_integrate_opts), P]
     lib.cg_integrate_noalloc.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, P]
     lib.cg_autotune.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, ctypes.c_char_p, P,
@@ -224,6 +227,15 @@ def cg_autotune(h, opts, T, Y, p_or_rho, cache_json=None, stream=None) -> float:
 
 def cg_mech_set_smem_limit(h, nbytes: int):
     _check(load().cg_mech_set_smem_limit(h.ptr, int(nbytes)))
+
+
+def cg_mech_set_lu_panel(h, nb: int):
+    """Panel width of the blocked LU (0: unblocked; identical results)."""
+    _check(load().cg_mech_set_lu_panel(h.ptr, int(nb)))
+
+
+def cg_mech_get_lu_panel(h) -> int:
+    return int(load().cg_mech_get_lu_panel(h.ptr))
 
 
 def cg_integrate_batch(handles, opts, Ts, Ys, ps, statuses=None, stats=None, stream=None):

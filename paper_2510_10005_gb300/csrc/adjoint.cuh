@@ -16,6 +16,11 @@
 //                    checkpoints, transposed solves on the FP64 LU of G_p,
 //                    per-cell gradients
 //   sum_rows_kernel  fixed-order sum of the per-cell parameter gradients
+//                    (kernels.cu)
+// (included only by instances.cu, which compiles it once per team size and
+// Newton-matrix type)
+#pragma once
+
 #include "stepper.cuh"
 
 namespace cg {
@@ -55,7 +60,7 @@ __device__ bool adjoint_step(const DevMech& M, const Ws& W, const IntParams& P, 
             rhs[i] = v;
         }
         team_sync<TEAM>();
-        if (!lu_factor<TEAM, double>(W.G, n, W.ld, W.piv, W.rinv, W.red, lane)) return false;
+        if (!lu_factor_nb<TEAM, double>(W.G, n, W.ld, M.lu_nb, W.piv, W.rinv, W.red, lane)) return false;
         lu_solve_t<TEAM, double>(W.G, n, W.ld, W.piv, W.rinv, nu, lane);
         const double igh = 1.0 / gh;
         for (int i = lane; i < n; i += TEAM) {
@@ -191,25 +196,8 @@ __global__ void adjoint_kernel(AdjTask tk, IntParams P, int sstride, double* gsc
         adjoint_cell<TEAM, MT>(tk, W, P, c, tp.lane);
 }
 
-// out[r] = sum_c g[r * N + c]: one block per row, a fixed order of
-// additions for a given N (strided partial sums, then a fixed tree).
-__global__ void sum_rows_kernel(int64_t N, const double* __restrict__ g, double* __restrict__ out) {
-    const double* row = g + (int64_t)blockIdx.x * N;
-    double s = 0.0;
-    for (int64_t c = threadIdx.x; c < N; c += blockDim.x) s += row[c];
-    __shared__ double red[32];
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        out[blockIdx.x] = t;
-    }
-}
-
 template <int TEAM, class MT>
-static cudaError_t launch_adjoint_t(const AdjTask& t, const IntParams& P, int tpb, cudaStream_t st) {
+cudaError_t launch_adjoint_team(const AdjTask& t, const IntParams& P, int tpb, cudaStream_t st) {
     if (TEAM > 32) tpb = 1;
     const int sstride = t.L.stotal;
     const int64_t gstride = round_up(t.L.gtotal, 32);
@@ -227,26 +215,6 @@ static cudaError_t launch_adjoint_t(const AdjTask& t, const IntParams& P, int tp
     e = cudaGetLastError();
     cudaError_t e2 = put_mem(mem, st);
     return e != cudaSuccess ? e : e2;
-}
-
-static cudaError_t launch_adjoint_sweep(const AdjTask& t, const IntParams& P, int team, int tpb,
-                                        cudaStream_t st) {
-    if (P.precision == 1) {
-#define CALL(TM) launch_adjoint_t<TM, float>(t, P, tpb, st)
-        CG_DISPATCH_TEAM(team, CALL)
-#undef CALL
-    }
-#define CALL(TM) launch_adjoint_t<TM, double>(t, P, tpb, st)
-    CG_DISPATCH_TEAM(team, CALL)
-#undef CALL
-}
-
-cudaError_t launch_adjoint(const AdjTask& t, const IntParams& P, int team, int tpb, double* dtheta,
-                           cudaStream_t st) {
-    cudaError_t e = launch_adjoint_sweep(t, P, team, tpb, st);
-    if (e != cudaSuccess || !dtheta || t.M.nr == 0) return e;
-    sum_rows_kernel<<<3 * t.M.nr, 256, 0, st>>>(t.N, t.grad_cells, dtheta);
-    return cudaGetLastError();
 }
 
 }  // namespace cg

@@ -373,8 +373,30 @@ namespace {
 
 // Default launch shape: one warp per cell for small mechanisms (several
 // cells per block), two warps per cell from 24 unknowns on, so that every SM
-// sub-partition holds two instruction streams.
-int default_team(int n) { return n <= 24 ? 32 : 64; }
+// sub-partition holds two instruction streams, and eight warps from 96 on,
+// where the Newton matrix alone fills an SM's shared memory and one cell's
+// team must keep all four sub-partitions busy (measured at 161 unknowns:
+// 2.2 times the rate of two warps).
+int default_team(int n) { return n <= 24 ? 32 : (n <= 96 ? 64 : 256); }
+
+// Default shared memory per cell: everything, unless the per-reaction block
+// (rates of progress and their partial derivatives, 9 nr doubles, read by
+// the assembly schedules) is what keeps the cells per SM low; then it goes
+// to the L2-resident scratch slot and the rest stays in shared memory
+// (measured at 53 species / 325 reactions: 6 cells per SM instead of 4,
+// 1.29 times the rate).
+size_t default_smem_limit(int ns, int nr) {
+    const Layout full = make_layout(ns, nr, 8, kMaxSmemPerBlock);
+    const size_t rd = 9 * (size_t)nr * sizeof(double);
+    const size_t per_cell = (size_t)full.stotal * sizeof(double);
+    if ((full.gmask >> cg::A_RD) & 1u || rd < 8 * 1024 || per_cell < 40 * 1024) return kMaxSmemPerBlock;
+    return per_cell - rd + 1024;   // the layout keeps 1 KiB of the limit free
+}
+
+// Default panel width of the LU: unblocked for small matrices (the
+// rank-one loop packs the trailing block into whole warps, the tiles leave
+// lanes idle at the ragged edges), panels of 16 above.
+int default_lu_nb(int n) { return n >= 96 ? 16 : 0; }
 
 int default_tpb(int team, const Layout& L) {
     if (team > 32) return 1;
@@ -712,6 +734,15 @@ cg_status cg_mech_set_smem_limit(cg_mech* m, int64_t bytes) {
     return CG_OK;
 }
 
+cg_status cg_mech_set_lu_panel(cg_mech* m, int nb) {
+    if (!m) return fail(CG_EINVAL, "mech is NULL");
+    if (nb < 0 || nb > 64) return fail(CG_EINVAL, "panel width must be 0 (unblocked) .. 64");
+    m->dm.lu_nb = nb;
+    return CG_OK;
+}
+
+int cg_mech_get_lu_panel(const cg_mech* m) { return m ? m->dm.lu_nb : -1; }
+
 int cg_mech_get_launch(const cg_mech* m, int* team, int* teams_per_block) {
     if (!m) return -1;
     if (team) *team = m->dm.team;
@@ -726,7 +757,8 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     if (st != CG_OK) return st;
     const int ns = d->n_species, nr = d->n_reactions, n = ns + 1;
     if (n > 1024) return fail(CG_ECAPACITY, "at most 1023 species are supported (got %d)", ns);
-    const Layout L = make_layout(ns, nr, 8, kMaxSmemPerBlock);
+    const size_t smem_limit = default_smem_limit(ns, nr);
+    const Layout L = make_layout(ns, nr, 8, smem_limit);
 
     // internal reaction order: by type, stable
     std::vector<int> perm(nr);
@@ -845,9 +877,9 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     m->ns = ns;
     m->nr = nr;
     m->L = L;
-    m->L32 = make_layout(ns, nr, 4, kMaxSmemPerBlock);
-    m->LA = make_layout(ns, nr, 8, kMaxSmemPerBlock, true);
-    m->smem_limit = kMaxSmemPerBlock;
+    m->L32 = make_layout(ns, nr, 4, smem_limit);
+    m->LA = make_layout(ns, nr, 8, smem_limit, true);
+    m->smem_limit = smem_limit;
     m->perm = perm;
     m->itype = rtype;
     m->arr.assign(d->arr, d->arr + 3 * (size_t)nr);
@@ -858,6 +890,7 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     dm.n = n;
     dm.ln_pref_R = std::log(kPref / kR);
     dm.th_np = 4;
+    dm.lu_nb = default_lu_nb(n);
 #define UP(vec, field)                                           \
     if ((st = upload(m->allocs, vec, &dm.field)) != CG_OK) {     \
         cg_mech_destroy(m);                                      \
@@ -1323,16 +1356,17 @@ cg_status cg_autotune(cg_mech* m, const cg_integrate_opts* o, int64_t N, const d
     if (cache_json) {   // reuse a previous result for the same mechanism size and options
         FILE* f = fopen(cache_json, "r");
         if (f) {
-            int ns = -1, nr = -1, prec = -1, method = -1, team = 0, tpb = 0;
+            int ns = -1, nr = -1, prec = -1, method = -1, team = 0, tpb = 0, nb = -1;
             long long lim = 0;
             double ms = 0;
             const int got = fscanf(f, "{\"ns\": %d, \"nr\": %d, \"precision\": %d, \"method\": %d, \"team\": %d, "
-                                      "\"teams_per_block\": %d, \"smem_limit\": %lld, \"ms\": %lf}",
-                                   &ns, &nr, &prec, &method, &team, &tpb, &lim, &ms);
+                                      "\"teams_per_block\": %d, \"smem_limit\": %lld, \"lu_panel\": %d, \"ms\": %lf}",
+                                   &ns, &nr, &prec, &method, &team, &tpb, &lim, &nb, &ms);
             fclose(f);
-            if (got == 8 && ns == m->ns && nr == m->nr && prec == o->precision && method == o->method) {
+            if (got == 9 && ns == m->ns && nr == m->nr && prec == o->precision && method == o->method) {
                 if ((st = cg_mech_set_smem_limit(m, lim)) != CG_OK) return st;
                 if ((st = cg_mech_set_launch(m, team, tpb)) != CG_OK) return st;
+                if ((st = cg_mech_set_lu_panel(m, nb)) != CG_OK) return st;
                 if (best_ms) *best_ms = ms;
                 return CG_OK;
             }
@@ -1349,18 +1383,28 @@ cg_status cg_autotune(cg_mech* m, const cg_integrate_opts* o, int64_t N, const d
         cudaFree(wY);
         return cuda_fail(e, "autotune workspace");
     }
-    const int old_team = m->dm.team, old_tpb = m->tpb;
+    const int old_team = m->dm.team, old_tpb = m->tpb, old_nb = m->dm.lu_nb;
     const int64_t old_lim = (int64_t)m->smem_limit;
-    struct Shape { int team, tpb; int64_t lim; };
+    struct Shape { int team, tpb; int64_t lim; int nb; };
     std::vector<Shape> shapes;
-    for (int64_t lim : {(int64_t)kMaxSmemPerBlock, (int64_t)kMaxSmemPerBlock / 2, (int64_t)48 * 1024})
+    std::vector<int64_t> lims = {(int64_t)kMaxSmemPerBlock, (int64_t)kMaxSmemPerBlock / 2, (int64_t)48 * 1024};
+    const int64_t def_lim = (int64_t)default_smem_limit(m->ns, m->nr);
+    if (std::find(lims.begin(), lims.end(), def_lim) == lims.end()) lims.push_back(def_lim);
+    // panel widths of the LU (identical results): only where the matrix is
+    // large enough for panels to matter
+    std::vector<int> panels = {0};
+    if (m->ns + 1 >= 48 && P.linear_solver == 0) panels.push_back(16);
+    for (int64_t lim : lims)
         for (int team : {32, 64, 128, 256})
             for (int tpb : {1, 2, 4})
-                if (team == 32 || tpb == 1) shapes.push_back({team, tpb, lim});
-    Shape best = {old_team, old_tpb, old_lim};
+                for (int nb : panels)
+                    if (team == 32 || tpb == 1) shapes.push_back({team, tpb, lim, nb});
+    Shape best = {old_team, old_tpb, old_lim, old_nb};
     float best_t = -1.0f;
     for (const Shape& sh : shapes) {
-        if (cg_mech_set_smem_limit(m, sh.lim) != CG_OK || cg_mech_set_launch(m, sh.team, sh.tpb) != CG_OK) continue;
+        if (cg_mech_set_smem_limit(m, sh.lim) != CG_OK || cg_mech_set_launch(m, sh.team, sh.tpb) != CG_OK ||
+            cg_mech_set_lu_panel(m, sh.nb) != CG_OK)
+            continue;
         float t_ms = 0.0f;
         bool ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) {   // first run warms up, second is timed
@@ -1382,14 +1426,15 @@ cg_status cg_autotune(cg_mech* m, const cg_integrate_opts* o, int64_t N, const d
     cudaEventDestroy(e1);
     if ((st = cg_mech_set_smem_limit(m, best.lim)) != CG_OK) return st;
     if ((st = cg_mech_set_launch(m, best.team, best.tpb)) != CG_OK) return st;
+    if ((st = cg_mech_set_lu_panel(m, best.nb)) != CG_OK) return st;
     if (best_t < 0.0f) return fail(CG_ECUDA, "no launch shape ran: %s", g_err.c_str());
     if (best_ms) *best_ms = best_t;
     if (cache_json) {
         FILE* f = fopen(cache_json, "w");
         if (f) {
             fprintf(f, "{\"ns\": %d, \"nr\": %d, \"precision\": %d, \"method\": %d, \"team\": %d, "
-                       "\"teams_per_block\": %d, \"smem_limit\": %lld, \"ms\": %.6f}\n",
-                    m->ns, m->nr, o->precision, o->method, best.team, best.tpb, (long long)best.lim, best_t);
+                       "\"teams_per_block\": %d, \"smem_limit\": %lld, \"lu_panel\": %d, \"ms\": %.6f}\n",
+                    m->ns, m->nr, o->precision, o->method, best.team, best.tpb, (long long)best.lim, best.nb, best_t);
             fclose(f);
         }
     }

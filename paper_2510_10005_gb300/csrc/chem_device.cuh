@@ -58,6 +58,7 @@ __host__ __device__ constexpr int th_rows(int P) { return 4 * P + 1; }
 struct DevMech {
     int ns, nr, n;               // species, reactions, n = ns + 1
     int team;                    // threads per cell the schedules were built for
+    int lu_nb;                   // panel width of the blocked LU (0: unblocked)
     double ln_pref_R;            // ln(p_ref / R)
     const double *th;            // [th_rows(th_np)][ns]
     int th_np;                   // degree P of the c_p polynomial (4: NASA-7)
@@ -716,61 +717,72 @@ static __device__ __forceinline__ unsigned long long abs_key(float x) {
     return (unsigned long long)((unsigned)__float_as_int(x) & 0x7fffffffu);
 }
 
+// Column k of the factorisation: pivot = the largest |G_ik|, i >= k (ties to
+// the lowest row; non-negative IEEE values order like their bit patterns),
+// whole rows k and pivot swapped, inverse pivot into rinv[k], column scaled
+// below the pivot. False on an exact zero pivot. Ends synchronised.
+template <int TEAM, class MT>
+__device__ __forceinline__ bool lu_pivot_column(MT* G, int n, int ld, int k, int* piv, double* rinv, double* red,
+                                                int lane) {
+    unsigned long long best = 0ull;
+    int bi = n;
+    for (int i = k + lane; i < n; i += TEAM) {
+        const unsigned long long b = abs_key(G[i * ld + k]);
+        if (bi == n || b > best) { best = b; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(kFull, best, o);
+        const int oi = __shfl_xor_sync(kFull, bi, o);
+        if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+    }
+    if constexpr (TEAM > 32) {
+        unsigned long long* rb = reinterpret_cast<unsigned long long*>(red + 8);
+        int* ri = reinterpret_cast<int*>(red + 16);
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) { rb[w] = best; ri[w] = bi; }
+        __syncthreads();
+        best = rb[0];
+        bi = ri[0];
+#pragma unroll
+        for (int v = 1; v < TEAM / 32; ++v) {
+            const unsigned long long ob = rb[v];
+            const int oi = ri[v];
+            if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+        }
+    }
+    if (lane == 0) piv[k] = bi;
+    if (bi != k) {
+        for (int j = lane; j < n; j += TEAM) {
+            const MT t = G[k * ld + j];
+            G[k * ld + j] = G[bi * ld + j];
+            G[bi * ld + j] = t;
+        }
+    }
+    team_sync<TEAM>();
+    const MT pv = G[k * ld + k];
+    if (abs_key(pv) == 0ull) return false;   // exact zero pivot (integer test)
+    // The first warp forms the reciprocal and scales the column; an FP64
+    // instruction costs the same for one lane as for 32, so the other
+    // warps of the team would only repeat it.
+    if (lane < 32) {
+        const double r = rcp_nr(static_cast<double>(pv));
+        if (lane == 0) rinv[k] = r;
+        const MT rm = static_cast<MT>(r);
+        for (int i = k + 1 + lane; i < n; i += 32) G[i * ld + k] *= rm;
+    }
+    team_sync<TEAM>();
+    return true;
+}
+
 // MT = double: the FP64 factorisation; MT = float: the FP32 factorisation
 // of the mixed-precision Newton (inverse pivots kept in FP64 for the solves).
+// Unblocked: after each column, the rank-one update of the whole trailing
+// block.
 template <int TEAM, class MT>
 __device__ bool lu_factor(MT* G, int n, int ld, int* piv, double* rinv, double* red, int lane) {
     for (int k = 0; k < n; ++k) {
-        // pivot: largest |G_ik|, i >= k; ties to the lowest row (non-negative
-        // doubles order like their bit patterns)
-        unsigned long long best = 0ull;
-        int bi = n;
-        for (int i = k + lane; i < n; i += TEAM) {
-            const unsigned long long b = abs_key(G[i * ld + k]);
-            if (bi == n || b > best) { best = b; bi = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ob = __shfl_xor_sync(kFull, best, o);
-            const int oi = __shfl_xor_sync(kFull, bi, o);
-            if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
-        }
-        if constexpr (TEAM > 32) {
-            unsigned long long* rb = reinterpret_cast<unsigned long long*>(red + 8);
-            int* ri = reinterpret_cast<int*>(red + 16);
-            const int w = threadIdx.x >> 5;
-            if ((threadIdx.x & 31) == 0) { rb[w] = best; ri[w] = bi; }
-            __syncthreads();
-            best = rb[0];
-            bi = ri[0];
-#pragma unroll
-            for (int v = 1; v < TEAM / 32; ++v) {
-                const unsigned long long ob = rb[v];
-                const int oi = ri[v];
-                if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
-            }
-        }
-        if (lane == 0) piv[k] = bi;
-        if (bi != k) {
-            for (int j = lane; j < n; j += TEAM) {
-                const MT t = G[k * ld + j];
-                G[k * ld + j] = G[bi * ld + j];
-                G[bi * ld + j] = t;
-            }
-        }
-        team_sync<TEAM>();
-        const MT pv = G[k * ld + k];
-        if (abs_key(pv) == 0ull) return false;   // exact zero pivot (integer test)
-        // The first warp forms the reciprocal and scales the column; an FP64
-        // instruction costs the same for one lane as for 32, so the other
-        // warps of the team would only repeat it.
-        if (lane < 32) {
-            const double r = rcp_nr(static_cast<double>(pv));
-            if (lane == 0) rinv[k] = r;
-            const MT rm = static_cast<MT>(r);
-            for (int i = k + 1 + lane; i < n; i += 32) G[i * ld + k] *= rm;
-        }
-        team_sync<TEAM>();
+        if (!lu_pivot_column<TEAM, MT>(G, n, ld, k, piv, rinv, red, lane)) return false;
         const int m = n - k - 1;
         if (m > 0) {
             const int k1 = k + 1;
@@ -806,6 +818,102 @@ __device__ bool lu_factor(MT* G, int n, int ld, int* piv, double* rinv, double* 
         team_sync<TEAM>();
     }
     return true;
+}
+
+// Right-looking blocked LU with partial pivoting (Section 3.4), in place,
+// team-cooperative, panels of nb columns. Within a panel each column is
+// pivoted (whole rows swapped) and scaled, and its rank-one update goes to
+// the panel's own columns and to the panel rows' columns right of the panel
+// (U12 of the panel). The trailing block A22 then takes the panel's nb
+// rank-one updates at once: A22 -= L21 U12, each thread accumulating an
+// RA x CB tile in registers (rows tr + a TRn, columns tc + b TCn of the
+// tile grid, so that neighbouring threads touch neighbouring columns).
+// Every element receives the same fused multiply-adds, in the same order
+// and rounded to MT after each, as in lu_factor: the factors and pivots are
+// identical to the last bit. The tile keeps the panel's rows and columns in
+// registers, so the trailing update reads (RA + CB) / (RA CB) operands from
+// shared memory per multiply-add instead of three reads and one write.
+template <int TEAM, class MT, int RA, int CB>
+__device__ bool lu_factor_blocked(MT* G, int n, int ld, int nb, int* piv, double* rinv, double* red, int lane) {
+    for (int k0 = 0; k0 < n; k0 += nb) {
+        const int kend = k0 + nb < n ? k0 + nb : n;
+        for (int k = k0; k < kend; ++k) {
+            if (!lu_pivot_column<TEAM, MT>(G, n, ld, k, piv, rinv, red, lane)) return false;
+            const int w = kend - k - 1;   // panel columns right of k
+            if (w > 0) {
+                const int h = n - k - 1, wr = n - kend;
+                for (Flat2D it(lane, w, TEAM); it.r < h; it.next()) {        // L part: rows below k
+                    MT* row = G + (k + 1 + it.r) * ld;
+                    const int c = k + 1 + it.c;
+                    row[c] = fma(-row[k], G[k * ld + c], row[c]);
+                }
+                if (wr > 0)
+                    for (Flat2D it(lane, wr, TEAM); it.r < w; it.next()) {   // U12: panel rows, right of it
+                        MT* row = G + (k + 1 + it.r) * ld;
+                        const int c = kend + it.c;
+                        row[c] = fma(-row[k], G[k * ld + c], row[c]);
+                    }
+            }
+            team_sync<TEAM>();
+        }
+        const int m = n - kend;
+        if (m <= 0) break;
+        const int kb = kend - k0;
+        const int TRn = (m + RA - 1) / RA, TCn = (m + CB - 1) / CB;
+        const MT* L21 = G + kend * ld + k0;   // L21[i * ld + j]: row kend + i, column k0 + j
+        const MT* U12 = G + k0 * ld + kend;   // U12[j * ld + c]: row k0 + j, column kend + c
+        MT* A22 = G + kend * ld + kend;
+        for (int t = lane; t < TRn * TCn; t += TEAM) {
+            const int tr = t / TCn, tc = t - tr * TCn;
+            int ro[RA], co[CB];
+            bool rv[RA], cv[CB];
+#pragma unroll
+            for (int a = 0; a < RA; ++a) {
+                const int r = tr + a * TRn;
+                rv[a] = r < m;
+                ro[a] = (rv[a] ? r : m - 1) * ld;   // rows past the end read the last row, store nothing
+            }
+#pragma unroll
+            for (int b = 0; b < CB; ++b) {
+                const int c = tc + b * TCn;
+                cv[b] = c < m;
+                co[b] = cv[b] ? c : m - 1;
+            }
+            MT acc[RA][CB];
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < CB; ++b) acc[a][b] = A22[ro[a] + co[b]];
+            for (int j = 0; j < kb; ++j) {
+                MT l[RA], u[CB];
+#pragma unroll
+                for (int a = 0; a < RA; ++a) l[a] = L21[ro[a] + j];
+#pragma unroll
+                for (int b = 0; b < CB; ++b) u[b] = U12[j * ld + co[b]];
+#pragma unroll
+                for (int a = 0; a < RA; ++a)
+#pragma unroll
+                    for (int b = 0; b < CB; ++b)
+                        acc[a][b] = fma(-l[a], u[b], acc[a][b]);
+            }
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < CB; ++b)
+                    if (rv[a] && cv[b]) A22[ro[a] + co[b]] = acc[a][b];
+        }
+        team_sync<TEAM>();
+    }
+    return true;
+}
+
+// The factorisation of the Newton matrix: blocked with panels of nb columns
+// (register tiles of 4 x 4), or unblocked for nb = 0; identical factors.
+template <int TEAM, class MT>
+__device__ __forceinline__ bool lu_factor_nb(MT* G, int n, int ld, int nb, int* piv, double* rinv, double* red,
+                                             int lane) {
+    if (nb > 0) return lu_factor_blocked<TEAM, MT, 4, 4>(G, n, ld, nb, piv, rinv, red, lane);
+    return lu_factor<TEAM, MT>(G, n, ld, piv, rinv, red, lane);
 }
 
 // x <- G^{-1} x with the factors of lu_factor (FP64 arithmetic on x).

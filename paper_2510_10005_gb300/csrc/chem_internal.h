@@ -93,6 +93,8 @@ cudaError_t launch_integrate_on(const Tasks& tasks, const IntParams& P, int team
 // count, lowered until the block's shared memory fits in 227 KB).
 int64_t integrate_slot_doubles(const Tasks& tasks);
 int integrate_tpb(const Tasks& tasks, int team, int tpb);
+// Shared-memory stride (doubles) of one team's slice: the largest of the tasks.
+int integrate_sstride(const Tasks& tasks);
 // Operator-split reaction step (persistent launch, `team` threads per cell).
 cudaError_t launch_react_split(const SplitTask& t, const IntParams& P, int team, int tpb, cudaStream_t st);
 // Backward sweep of the discrete adjoint over the cells of t (persistent
@@ -100,5 +102,22 @@ cudaError_t launch_react_split(const SplitTask& t, const IntParams& P, int team,
 // fixed-order sum of the per-cell parameter gradients into dtheta[nr][3].
 cudaError_t launch_adjoint(const AdjTask& t, const IntParams& P, int team, int tpb, double* dtheta,
                            cudaStream_t st);
+
+// The launchers of one team size TEAM (threads per cell) and Newton-matrix
+// type MT, explicitly instantiated in instances.cu (one object per
+// combination); the dispatchers above select among them.
+template <int TEAM>
+cudaError_t launch_eval_team(bool jacobian, const DevMech& M, const Layout& L, int tpb, int reactor, int64_t N,
+                             const double* T, const double* C, double* out, cudaStream_t st);
+template <int TEAM, class MT>
+cudaError_t launch_integrate_team(const Tasks& tasks, const IntParams& P, int tpb, bool persistent,
+                                  cudaStream_t st);
+template <int TEAM, class MT>
+cudaError_t launch_integrate_on_team(const Tasks& tasks, const IntParams& P, int tpb, double* scratch,
+                                     int64_t scratch_doubles, unsigned long long* counter, cudaStream_t st);
+template <int TEAM, class MT>
+cudaError_t launch_split_team(const SplitTask& t, const IntParams& P, int tpb, cudaStream_t st);
+template <int TEAM, class MT>
+cudaError_t launch_adjoint_team(const AdjTask& t, const IntParams& P, int tpb, cudaStream_t st);
 
 }  // namespace cg

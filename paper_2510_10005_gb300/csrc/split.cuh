@@ -8,6 +8,10 @@
 //
 //   react_split_kernel   one team per cell: load, temperature recovery,
 //                        integration, source
+// (included only by instances.cu, which compiles it once per team size and
+// Newton-matrix type)
+#pragma once
+
 #include "stepper.cuh"
 
 namespace cg {
@@ -102,7 +106,7 @@ __global__ void react_split_kernel(SplitTask tk, IntParams P, int sstride, doubl
 }
 
 template <int TEAM, class MT>
-static cudaError_t launch_split_t(const SplitTask& t, const IntParams& P, int tpb, cudaStream_t st) {
+cudaError_t launch_split_team(const SplitTask& t, const IntParams& P, int tpb, cudaStream_t st) {
     if (TEAM > 32) tpb = 1;
     const int sstride = t.L.stotal;
     const int64_t gstride = round_up(t.L.gtotal, 32);
@@ -121,17 +125,6 @@ static cudaError_t launch_split_t(const SplitTask& t, const IntParams& P, int tp
     e = cudaGetLastError();
     cudaError_t e2 = put_mem(mem, st);
     return e != cudaSuccess ? e : e2;
-}
-
-cudaError_t launch_react_split(const SplitTask& t, const IntParams& P, int team, int tpb, cudaStream_t st) {
-    if (P.precision == 1) {
-#define CALL(TM) launch_split_t<TM, float>(t, P, tpb, st)
-        CG_DISPATCH_TEAM(team, CALL)
-#undef CALL
-    }
-#define CALL(TM) launch_split_t<TM, double>(t, P, tpb, st)
-    CG_DISPATCH_TEAM(team, CALL)
-#undef CALL
 }
 
 }  // namespace cg

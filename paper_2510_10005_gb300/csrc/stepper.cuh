@@ -59,11 +59,12 @@ struct Counters {
 // GMRES on G as assembled (one warp of the team; the others wait). Counter
 // `lu` counts factorisations or GMRES iterations.
 template <int TEAM, class MT>
-__device__ __forceinline__ bool lin_prepare(const Ws& W, const IntParams& P, int n, Counters& cnt, int lane) {
+__device__ __forceinline__ bool lin_prepare(const DevMech& M, const Ws& W, const IntParams& P, int n,
+                                            Counters& cnt, int lane) {
     MT* G = reinterpret_cast<MT*>(W.G);
     if (P.linear_solver == 0) {
         cnt.lu++;
-        return lu_factor<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, W.red, lane);
+        return lu_factor_nb<TEAM, MT>(G, n, W.ld, M.lu_nb, W.piv, W.rinv, W.red, lane);
     }
     bool zero = false;   // inverse diagonal for the preconditioner
     for (int i = lane; i < n; i += TEAM) {
@@ -153,7 +154,7 @@ __device__ bool rk_step(const DevMech& M, const Ws& W, const IntParams& P, doubl
             for (int i = lane; i < n; i += TEAM) f[i] = S[i] - Gp[i];   // -f(Gamma)
             team_sync<TEAM>();
             cnt.newton++;
-            if (!lin_prepare<TEAM, MT>(W, P, n, cnt, lane)) return false;
+            if (!lin_prepare<TEAM, MT>(M, W, P, n, cnt, lane)) return false;
             if (!lin_solve<TEAM, MT>(W, P, n, f, cnt, lane)) return false;
             for (int i = lane; i < n; i += TEAM) {
                 const double g = Gp[i] + f[i];
@@ -221,7 +222,7 @@ __device__ bool ros2_step(const DevMech& M, const Ws& W, const IntParams& P, dou
     for (int i = lane; i < n; i += TEAM) G1[i] = hg * W.S[i];
     team_sync<TEAM>();
     cnt.newton++;
-    if (!lin_prepare<TEAM, MT>(W, P, n, cnt, lane)) return false;
+    if (!lin_prepare<TEAM, MT>(M, W, P, n, cnt, lane)) return false;
     if (!lin_solve<TEAM, MT>(W, P, n, G1, cnt, lane)) return false;
     bool bad = false;
     for (int i = lane; i < n; i += TEAM) {

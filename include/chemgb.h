@@ -172,7 +172,10 @@ cg_status cg_mech_set_launch(cg_mech *mech, int team, int teams_per_block);
  * cells per SM. Default: 227 KiB, except when the per-reaction block (9 nr
  * doubles) is at least 8 KiB of a per-cell total of 40 KiB or more; then
  * the limit keeps everything but that block in shared memory (53 species /
- * 325 reactions: 33 KiB per cell, 6 cells per SM instead of 4). Same
+ * 325 reactions: 33 KiB per cell, 6 cells per SM instead of 4); and for the
+ * FP32 Newton matrix 113.5 KiB where that lets two cells share an SM that
+ * would otherwise hold one (160 species). This call sets one limit for
+ * both matrix types. Same
  * concurrency rule as cg_mech_set_launch. Launch tuning, not part of the
  * paper's method. */
 cg_status cg_mech_set_smem_limit(cg_mech *mech, int64_t bytes);
@@ -329,8 +332,14 @@ cg_status cg_react_split(const cg_mech *mech, const cg_integrate_opts *opts, int
  *   ckpt[(c * ckpt_cap + k) * (ns + 2) + i], i <= ns: y_k,  i = ns + 1: h_k;
  *   record ckpt_n[c] holds the final state and the initial density.
  *   ckpt[N * ckpt_cap * (ns + 2)] and ckpt_n[N] are caller-owned device
- *   arrays; ckpt_n[c] = -1 when the cell failed or took more than
- *   ckpt_cap - 1 steps (its adjoint then reports CG_CELL_NO_RECORD).
+ *   arrays; ckpt_n[c] = -1 when the cell failed (its adjoint then reports
+ *   CG_CELL_NO_RECORD). A cell whose S accepted steps need more than
+ *   ckpt_cap - 1 records gets ckpt_n[c] = -(S + 2): record 0 keeps its
+ *   initial state and record ckpt_cap - 1 its final state and density, and
+ *   the adjoint recomputes the steps from record 0 in segments of 32 (a
+ *   second level of checkpointing in its own scratch: the replay runs the
+ *   forward arithmetic again, so the gradients are identical to those from
+ *   a full record, at the cost of about S^2 / 64 extra steps).
  *   ckpt_cap >= 2. Other arguments and results as cg_integrate.
  *
  * cg_integrate_adjoint: from dL/dT_end[N] and dL/dY_end[ns*N] (SoA, device),

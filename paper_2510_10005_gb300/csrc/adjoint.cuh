@@ -124,12 +124,20 @@ __device__ void adjoint_cell(const AdjTask& tk, const Ws& W, const IntParams& P,
     for (int j = lane; j < 3 * nr; j += TEAM) W.grad[j] = 0.0;
     int st = CELL_OK;
     double rho0 = 0.0;
-    if (K < 0 || K >= tk.ckpt_cap) {
+    // K >= 0: all K steps recorded, the final state in record K. K <= -2:
+    // S = -K - 2 steps did not fit; record 0 holds the initial state and the
+    // last record the final one, and the steps are recomputed from record 0
+    // in segments of kSegSteps (the forward integration replayed in its own
+    // arithmetic, so each segment's states are those of the forward pass),
+    // last segment first, each swept backwards from the team's scratch.
+    const bool full = K >= 0 && K < tk.ckpt_cap;
+    const int S = full ? K : -K - 2;
+    if (!full && (K > -2 || tk.ckpt_cap < 2)) {
         st = CELL_NO_RECORD;
     } else {
         // lam = dL/dy at the end: dL/dT_end and, from Y_k = W_k C_k / rho,
         // dL/dC_m = W_m / rho (dL/dY_m - sum_k Y_k dL/dY_k)
-        const double* ye = ck + (int64_t)K * (n + 1);
+        const double* ye = ck + (int64_t)(full ? K : tk.ckpt_cap - 1) * (n + 1);
         rho0 = ye[n];
         double ms = 0.0;
         for (int i = lane; i < ns; i += TEAM) ms = fma(__ldg(M.W + i), ye[1 + i], ms);
@@ -143,16 +151,31 @@ __device__ void adjoint_cell(const AdjTask& tk, const Ws& W, const IntParams& P,
         if (lane == 0) lam[0] = tk.dT_end[cell];
         team_sync<TEAM>();
         Counters cnt = {0, 0, 0, 0};
-        for (int k = K - 1; k >= 0; --k) {
-            const double* e = ck + (int64_t)k * (n + 1);
-            for (int i = lane; i < n; i += TEAM) W.yn[i] = e[i];
-            const double h = e[n];
-            team_sync<TEAM>();
-            // the forward step's stages, recomputed in its own arithmetic
-            if (!rk_step<TEAM, MT>(M, W, P, h, cnt, lane) || !adjoint_step<TEAM>(M, W, P, h, lane)) {
-                st = CELL_NEWTON_FAIL;
-                break;
+        for (int end = S; end > 0 && st == CELL_OK;) {
+            const int from = full ? 0 : (end > kSegSteps ? end - kSegSteps : 0);
+            if (!full) {   // replay steps 0 .. end - 1 from the initial state, recording from .. end - 1
+                for (int i = lane; i < n; i += TEAM) W.yn[i] = ck[i];
+                team_sync<TEAM>();
+                Counters rc = {0, 0, 0, 0};
+                const int rs = P.adaptive ? integrate_adaptive<TEAM, MT>(M, W, P, rc, W.seg, kSegSteps, lane, from, end)
+                                          : integrate_fixed<TEAM, MT>(M, W, P, rc, W.seg, kSegSteps, lane, from, end);
+                if (rs != CELL_OK || rc.steps != end) {
+                    st = CELL_NEWTON_FAIL;
+                    break;
+                }
             }
+            for (int k = end - 1; k >= from; --k) {
+                const double* e = full ? ck + (int64_t)k * (n + 1) : W.seg + (int64_t)(k - from) * (n + 1);
+                for (int i = lane; i < n; i += TEAM) W.yn[i] = e[i];
+                const double h = e[n];
+                team_sync<TEAM>();
+                // the forward step's stages, recomputed in its own arithmetic
+                if (!rk_step<TEAM, MT>(M, W, P, h, cnt, lane) || !adjoint_step<TEAM>(M, W, P, h, lane)) {
+                    st = CELL_NEWTON_FAIL;
+                    break;
+                }
+            }
+            end = from;
         }
     }
     // dL/dy_0 -> dL/dT_0, dL/dY_0 through C_m = rho Y_m / W_m with rho
@@ -185,7 +208,7 @@ __device__ void adjoint_cell(const AdjTask& tk, const Ws& W, const IntParams& P,
 }
 
 template <int TEAM, class MT>
-__global__ void adjoint_kernel(AdjTask tk, IntParams P, int sstride, double* gscratch, int64_t gstride,
+__global__ void __maxnreg__((KernelRegs<TEAM, MT>::value)) adjoint_kernel(AdjTask tk, IntParams P, int sstride, double* gscratch, int64_t gstride,
                                unsigned long long* counter) {
     extern __shared__ double smem_all[];
     const TeamPos<TEAM> tp;

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "chemgb.h"
 #include "chemgb_testing.h"
 #include "chem_internal.h"
@@ -20,6 +22,17 @@ using cg::Layout;
 namespace {
 
 thread_local std::string g_err;
+
+// An NVTX range named after the entry point around each call (seen by
+// profilers such as Nsight Systems and ncu --nvtx; header-only NVTX v3,
+// nothing is recorded when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define CG_RANGE(name) NvtxRange cg_nvtx_range_(name)
 
 cg_status fail(cg_status code, const char* fmt, ...) {
     char buf[512];
@@ -128,11 +141,12 @@ Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoin
     size[A_GRAD] = adjoint ? 3 * nr : 0;
     for (int a : {A_LAM, A_LAMN, A_NU, A_RHS}) size[a] = adjoint ? n : 0;
     size[A_ACC] = adjoint ? 5 * n : 0;
+    size[A_SEG] = adjoint ? kSegSteps * (n + 1) : 0;
     size[A_KV] = gmres_m ? (gmres_m + 1) * (n | 1) : 0;
     size[A_KH] = gmres_m ? (gmres_m + 1) * gmres_m + 2 * gmres_m + 2 * (gmres_m + 1) : 0;
     const int order[A_COUNT] = {A_RED, A_PIV, A_G, A_RINV, A_YN, A_Y, A_F, A_S, A_BASE,
                                 A_S0, A_ERR, A_Y1, A_COLA, A_COLB, A_SP, A_V, A_GAM, A_KH, A_KV,
-                                A_NU, A_RHS, A_LAM, A_LAMN, A_ACC, A_XF, A_RD, A_GRAD};
+                                A_NU, A_RHS, A_LAM, A_LAMN, A_ACC, A_XF, A_RD, A_GRAD, A_SEG};
     // 1 KiB of the block's shared memory stays free for the kernels' static variables
     const long budget = (long)((smem_limit > 2048 ? smem_limit - 1024 : 1024) / sizeof(double));
     int so = 0, go = 0;
@@ -391,6 +405,18 @@ size_t default_smem_limit(int ns, int nr) {
     const size_t per_cell = (size_t)full.stotal * sizeof(double);
     if ((full.gmask >> cg::A_RD) & 1u || rd < 8 * 1024 || per_cell < 40 * 1024) return kMaxSmemPerBlock;
     return per_cell - rd + 1024;   // the layout keeps 1 KiB of the limit free
+}
+
+// Default for the FP32 Newton matrix: the FP64 default, unless that leaves
+// one cell per SM while the FP32 matrix with the arrays placed before it
+// would let two share it (161 unknowns: 104 KB matrix; 1.7 times the rate
+// with four warps per cell, measured).
+size_t default_smem_limit32(int ns, int nr, size_t limit64) {
+    const size_t half = kMaxSmemPerBlock / 2;   // two cells per SM
+    const Layout at64 = make_layout(ns, nr, 4, limit64);
+    const Layout at_half = make_layout(ns, nr, 4, half);
+    if ((size_t)at64.stotal * sizeof(double) <= half) return limit64;
+    return (at_half.gmask >> cg::A_G) & 1u ? limit64 : half;   // only if the matrix itself fits
 }
 
 // Default panel width of the LU: unblocked for small matrices (the
@@ -751,6 +777,7 @@ int cg_mech_get_launch(const cg_mech* m, int* team, int* teams_per_block) {
 }
 
 cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
+    CG_RANGE("cg_mech_create");
     if (!out) return fail(CG_EINVAL, "out is NULL");
     *out = nullptr;
     cg_status st = validate(d);
@@ -877,7 +904,7 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     m->ns = ns;
     m->nr = nr;
     m->L = L;
-    m->L32 = make_layout(ns, nr, 4, smem_limit);
+    m->L32 = make_layout(ns, nr, 4, default_smem_limit32(ns, nr, smem_limit));
     m->LA = make_layout(ns, nr, 8, smem_limit, true);
     m->smem_limit = smem_limit;
     m->perm = perm;
@@ -936,6 +963,7 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
 
 cg_status cg_eval_rates(const cg_mech* m, int reactor, int64_t N, const double* T, const double* C,
                         double* S, void* stream) {
+    CG_RANGE("cg_eval_rates");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     if (N < 0 || reactor < CG_CONV || reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad N or reactor");
     if (N == 0) return CG_OK;
@@ -947,6 +975,7 @@ cg_status cg_eval_rates(const cg_mech* m, int reactor, int64_t N, const double* 
 
 cg_status cg_eval_jacobian(const cg_mech* m, int reactor, int64_t N, const double* T, const double* C,
                            double* J, void* stream) {
+    CG_RANGE("cg_eval_jacobian");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     if (N < 0 || reactor < CG_CONV || reactor > CG_CONP_LITERAL) return fail(CG_EINVAL, "bad N or reactor");
     if (N == 0) return CG_OK;
@@ -958,6 +987,7 @@ cg_status cg_eval_jacobian(const cg_mech* m, int reactor, int64_t N, const doubl
 
 cg_status cg_temperature_from_energy(const cg_mech* m, int reactor, int64_t N, const double* e,
                                      const double* Y, double* T, int iters, void* stream) {
+    CG_RANGE("cg_temperature_from_energy");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     if (N < 0 || iters < 0 || reactor < CG_CONV || reactor > CG_CONP_LITERAL)
         return fail(CG_EINVAL, "bad N, iters or reactor");
@@ -1050,6 +1080,7 @@ static cg_status make_params(const cg_integrate_opts* o, IntParams& P) {
 cg_status cg_integrate(const cg_mech* m, const cg_integrate_opts* o, int64_t N, double* T, double* Y,
                        const double* p_or_rho, int32_t* cell_status, int32_t* cell_stats,
                        void* stream) {
+    CG_RANGE("cg_integrate");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     IntParams P;
     cg_status st = make_params(o, P);
@@ -1070,6 +1101,7 @@ cg_status cg_integrate_batch(int n_mech, const cg_mech* const* mechs, const int6
                              double* const* T, double* const* Y, const double* const* p_or_rho,
                              int32_t* const* cell_status, int32_t* const* cell_stats,
                              const cg_integrate_opts* o, void* stream) {
+    CG_RANGE("cg_integrate_batch");
     if (n_mech < 1 || n_mech > cg::kMaxTasks)
         return fail(CG_EINVAL, "n_mech must be 1..%d", cg::kMaxTasks);
     if (!mechs || !N || !T || !Y || !p_or_rho) return fail(CG_EINVAL, "NULL array");
@@ -1102,6 +1134,7 @@ cg_status cg_integrate_batch(int n_mech, const cg_mech* const* mechs, const int6
 cg_status cg_react_split(const cg_mech* m, const cg_integrate_opts* o, int64_t N, const double* rho,
                          const double* e, const double* rhoY, double* T, double* R, int iters,
                          int32_t* cell_status, int32_t* cell_stats, void* stream) {
+    CG_RANGE("cg_react_split");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     IntParams P;
     cg_status st = make_params(o, P);
@@ -1130,6 +1163,7 @@ cg_status cg_react_split(const cg_mech* m, const cg_integrate_opts* o, int64_t N
 cg_status cg_integrate_ckpt(const cg_mech* m, const cg_integrate_opts* o, int64_t N, double* T, double* Y,
                             const double* p_or_rho, int32_t* cell_status, int32_t* cell_stats, double* ckpt,
                             int32_t* ckpt_n, int ckpt_cap, void* stream) {
+    CG_RANGE("cg_integrate_ckpt");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     IntParams P;
     cg_status st = make_params(o, P);
@@ -1155,6 +1189,7 @@ cg_status cg_integrate_adjoint(const cg_mech* m, const cg_integrate_opts* o, int
                                const int32_t* ckpt_n, int ckpt_cap, const double* dT_end, const double* dY_end,
                                double* dT0, double* dY0, double* dtheta, double* dtheta_cells,
                                int32_t* cell_status, void* stream) {
+    CG_RANGE("cg_integrate_adjoint");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     IntParams P;
     cg_status st = make_params(o, P);
@@ -1204,6 +1239,7 @@ cg_status cg_integrate_adjoint(const cg_mech* m, const cg_integrate_opts* o, int
 }
 
 cg_status cg_mech_set_arrhenius(cg_mech* m, const double* arr) {
+    CG_RANGE("cg_mech_set_arrhenius");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     const int nr = m->nr;
     if (nr == 0) return CG_OK;
@@ -1277,6 +1313,7 @@ cg_status cgx_thermo_table(int ns, int np, const double* coef, int* P, double* t
 }
 
 cg_status cg_mech_set_thermo(cg_mech* m, int np, const double* coef) {
+    CG_RANGE("cg_mech_set_thermo");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     std::vector<double> th;
     int P = 4;
@@ -1294,6 +1331,7 @@ cg_status cg_mech_set_thermo(cg_mech* m, int np, const double* coef) {
 cg_status cg_integrate_host(const cg_mech* mc, const cg_integrate_opts* o, int64_t N, double* T,
                             double* Y, const double* p_or_rho, int32_t* cell_status,
                             int32_t* cell_stats) {
+    CG_RANGE("cg_integrate_host");
     if (!mc) return fail(CG_EINVAL, "mech is NULL");
     cg_mech* m = const_cast<cg_mech*>(mc);
     IntParams P;
@@ -1348,6 +1386,7 @@ cg_status cg_integrate_host(const cg_mech* mc, const cg_integrate_opts* o, int64
 // each timing; the caller's arrays are not modified.
 cg_status cg_autotune(cg_mech* m, const cg_integrate_opts* o, int64_t N, const double* T, const double* Y,
                       const double* p_or_rho, const char* cache_json, void* stream, double* best_ms) {
+    CG_RANGE("cg_autotune");
     if (!m) return fail(CG_EINVAL, "mech is NULL");
     IntParams P;
     cg_status st = make_params(o, P);

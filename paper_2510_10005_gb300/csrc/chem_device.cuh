@@ -107,11 +107,16 @@ enum {
     A_GRAD,     // 3 nr: dL/d(ln A, b, Ea), reaction-major
     A_LAM, A_LAMN, A_NU, A_RHS,   // n each
     A_ACC,      // 5 n: sum over later stages of h a_qp J_q^T nu_q
+    A_SEG,      // kSegSteps (n + 1): records of a replayed segment of steps
     // GMRES only (size 0 with the LU)
     A_KV,       // (m+1) x vs Krylov basis
     A_KH,       // (m+1) m Hessenberg + 2 m rotations + 2 (m+1) (g, projections)
     A_COUNT
 };
+
+// Steps per segment when the adjoint recomputes a cell whose checkpoints
+// did not fit in the caller's record.
+constexpr int kSegSteps = 32;
 
 struct Layout {
     int ld;                  // row stride of the n x n matrix (odd)
@@ -125,7 +130,7 @@ struct Ws {
     int ld;
     double *G, *RD, *SP, *V, *yn, *Y, *base, *S, *S0, *f, *err, *y1, *colA, *colB, *rinv, *Gam, *red;
     int* piv;
-    double *xf, *grad, *lam, *lamn, *nu, *rhs, *acc;
+    double *xf, *grad, *lam, *lamn, *nu, *rhs, *acc, *seg;
     double *kv, *kh;
 };
 
@@ -141,7 +146,7 @@ __device__ __forceinline__ Ws make_ws(const Layout& L, double* sbase, double* gb
     w.rinv = p[A_RINV]; w.Gam = p[A_GAM]; w.red = p[A_RED];
     w.piv = reinterpret_cast<int*>(p[A_PIV]);
     w.xf = p[A_XF]; w.grad = p[A_GRAD]; w.lam = p[A_LAM]; w.lamn = p[A_LAMN];
-    w.nu = p[A_NU]; w.rhs = p[A_RHS]; w.acc = p[A_ACC];
+    w.nu = p[A_NU]; w.rhs = p[A_RHS]; w.acc = p[A_ACC]; w.seg = p[A_SEG];
     w.kv = p[A_KV]; w.kh = p[A_KH];
     return w;
 }
@@ -823,16 +828,18 @@ __device__ bool lu_factor(MT* G, int n, int ld, int* piv, double* rinv, double* 
 // Right-looking blocked LU with partial pivoting (Section 3.4), in place,
 // team-cooperative, panels of nb columns. Within a panel each column is
 // pivoted (whole rows swapped) and scaled, and its rank-one update goes to
-// the panel's own columns and to the panel rows' columns right of the panel
-// (U12 of the panel). The trailing block A22 then takes the panel's nb
-// rank-one updates at once: A22 -= L21 U12, each thread accumulating an
-// RA x CB tile in registers (rows tr + a TRn, columns tc + b TCn of the
-// tile grid, so that neighbouring threads touch neighbouring columns).
-// Every element receives the same fused multiply-adds, in the same order
-// and rounded to MT after each, as in lu_factor: the factors and pivots are
-// identical to the last bit. The tile keeps the panel's rows and columns in
-// registers, so the trailing update reads (RA + CB) / (RA CB) operands from
-// shared memory per multiply-add instead of three reads and one write.
+// the panel's own columns only; columns right of the panel are left as they
+// are until the panel is done (a later pivot of the panel may swap any two
+// of its rows). Then U12 = L11^{-1} A12 by forward substitution, one column
+// per thread, and the trailing block takes the panel's nb rank-one updates
+// at once: A22 -= L21 U12, each thread accumulating an RA x CB tile in
+// registers (rows tr + a TRn, columns tc + b TCn of the tile grid, so that
+// neighbouring threads touch neighbouring columns). Every element receives
+// the same fused multiply-adds, in the same order and rounded to MT after
+// each, as in lu_factor: the factors and pivots are identical to the last
+// bit. The tile keeps the panel's rows and columns in registers, so the
+// trailing update reads (RA + CB) / (RA CB) operands from shared memory per
+// multiply-add instead of three reads and one write.
 template <int TEAM, class MT, int RA, int CB>
 __device__ bool lu_factor_blocked(MT* G, int n, int ld, int nb, int* piv, double* rinv, double* red, int lane) {
     for (int k0 = 0; k0 < n; k0 += nb) {
@@ -841,23 +848,26 @@ __device__ bool lu_factor_blocked(MT* G, int n, int ld, int nb, int* piv, double
             if (!lu_pivot_column<TEAM, MT>(G, n, ld, k, piv, rinv, red, lane)) return false;
             const int w = kend - k - 1;   // panel columns right of k
             if (w > 0) {
-                const int h = n - k - 1, wr = n - kend;
-                for (Flat2D it(lane, w, TEAM); it.r < h; it.next()) {        // L part: rows below k
+                const int h = n - k - 1;
+                for (Flat2D it(lane, w, TEAM); it.r < h; it.next()) {
                     MT* row = G + (k + 1 + it.r) * ld;
                     const int c = k + 1 + it.c;
                     row[c] = fma(-row[k], G[k * ld + c], row[c]);
                 }
-                if (wr > 0)
-                    for (Flat2D it(lane, wr, TEAM); it.r < w; it.next()) {   // U12: panel rows, right of it
-                        MT* row = G + (k + 1 + it.r) * ld;
-                        const int c = kend + it.c;
-                        row[c] = fma(-row[k], G[k * ld + c], row[c]);
-                    }
             }
             team_sync<TEAM>();
         }
         const int m = n - kend;
         if (m <= 0) break;
+        // U12: rows k0+1 .. kend-1 of the columns right of the panel, each
+        // element updated by the panel rows above it in order
+        for (int c = kend + lane; c < n; c += TEAM)
+            for (int i = k0 + 1; i < kend; ++i) {
+                MT a = G[i * ld + c];
+                for (int j = k0; j < i; ++j) a = fma(-G[i * ld + j], G[j * ld + c], a);
+                G[i * ld + c] = a;
+            }
+        team_sync<TEAM>();
         const int kb = kend - k0;
         const int TRn = (m + RA - 1) / RA, TCn = (m + CB - 1) / CB;
         const MT* L21 = G + kend * ld + k0;   // L21[i * ld + j]: row kend + i, column k0 + j

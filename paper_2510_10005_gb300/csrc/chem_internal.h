@@ -22,7 +22,8 @@ struct Task {
     // optional checkpoints of the accepted steps (adjoint): cell c's step k
     // is ckpt[(c * ckpt_cap + k) * (n + 1) + i] = (y_k, h_k); entry
     // ckpt_n[c] holds the final state and the initial density rho_0;
-    // ckpt_n[c] = -1 when the cell failed or cap was too small
+    // ckpt_n[c] = -1 when the cell failed; when its S steps do not fit,
+    // ckpt_n[c] = -(S + 2) and the last entry holds the final state
     double* ckpt;
     int32_t* ckpt_n;
     int ckpt_cap;

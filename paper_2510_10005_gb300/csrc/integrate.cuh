@@ -101,8 +101,11 @@ __device__ void integrate_cell(const Task& tk, const Ws& W, const IntParams& P, 
         st = P.adaptive ? integrate_adaptive<TEAM, MT>(M, W, P, cnt, ck, tk.ckpt_cap, lane)
                         : integrate_fixed<TEAM, MT>(M, W, P, cnt, ck, tk.ckpt_cap, lane);
         if (ck) {   // the final state closes the record
-            save_step<TEAM>(ck, tk.ckpt_cap, cnt.steps, yn, rho, n, lane);
-            if (lane == 0) tk.ckpt_n[cell] = (st == CELL_OK && cnt.steps < tk.ckpt_cap) ? cnt.steps : -1;
+            // after the last step, or in the last slot when the steps did not
+            // fit (the adjoint then recomputes them from record 0)
+            const bool fits = cnt.steps < tk.ckpt_cap;
+            if (st == CELL_OK) save_step<TEAM>(ck, tk.ckpt_cap, fits ? cnt.steps : tk.ckpt_cap - 1, yn, rho, n, lane);
+            if (lane == 0) tk.ckpt_n[cell] = st != CELL_OK ? -1 : (fits ? cnt.steps : -(cnt.steps + 2));
         }
         bool bad = false;
         for (int i = lane; i < n; i += TEAM) bad |= !isfinite(yn[i]);
@@ -129,7 +132,7 @@ __device__ void integrate_cell(const Task& tk, const Ws& W, const IntParams& P, 
 }
 
 template <int TEAM, class MT>
-__global__ void integrate_kernel(Tasks tasks, IntParams P, int sstride, double* gscratch,
+__global__ void __maxnreg__((KernelRegs<TEAM, MT>::value)) integrate_kernel(Tasks tasks, IntParams P, int sstride, double* gscratch,
                                  int64_t gstride, unsigned long long* counter) {
     extern __shared__ double smem_all[];
     const TeamPos<TEAM> tp;

@@ -94,7 +94,7 @@ __device__ void split_cell(const SplitTask& tk, const Ws& W, const IntParams& P,
 }
 
 template <int TEAM, class MT>
-__global__ void react_split_kernel(SplitTask tk, IntParams P, int sstride, double* gscratch, int64_t gstride,
+__global__ void __maxnreg__((KernelRegs<TEAM, MT>::value)) react_split_kernel(SplitTask tk, IntParams P, int sstride, double* gscratch, int64_t gstride,
                                    unsigned long long* counter) {
     extern __shared__ double smem_all[];
     const TeamPos<TEAM> tp;

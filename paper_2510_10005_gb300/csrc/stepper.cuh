@@ -48,6 +48,24 @@ __device__ __forceinline__ int64_t first_cell(unsigned long long* counter, int64
     return counter ? next_cell<TEAM>(counter, 0, 0, lane) : id;
 }
 
+// Registers per thread of the cell kernels (integration, split, adjoint), by
+// team size and Newton-matrix type: the most that still lets the intended
+// number of cells share an SM's 65,536 registers. Left to itself the
+// compiler gives every kernel about 254, because the register tiles of the
+// blocked LU raise the whole kernel's allocation even where that path does
+// not run, and then only four 64-thread cells fit on an SM.
+//   TEAM 32: 168 (12 one-warp cells)      TEAM 64 FP64: 168 (6 cells)
+//   TEAM 64 FP32: 128 (8 cells)           TEAM 128: 128 (4 cells)
+//   TEAM 256 FP64: 255 (the 207 KB FP64 Newton matrix of 161 unknowns
+//   allows one cell per SM)               TEAM 256 FP32: 128 (2 cells)
+template <int TEAM, class MT>
+struct KernelRegs {
+    static constexpr int value = TEAM == 32 ? 168
+                                 : TEAM == 64 ? (sizeof(MT) == 8 ? 168 : 128)
+                                 : TEAM == 128 ? 128
+                                 : (sizeof(MT) == 8 ? 255 : 128);
+};
+
 // ---------------------------------------------------------------------------
 // integration
 
@@ -271,25 +289,29 @@ __device__ __forceinline__ void copy_vec(double* dst, const double* src, int n, 
     team_sync<TEAM>();
 }
 
-// Checkpoint k of a cell: (y_k, h_k) when it fits in cap entries (the
-// record after the last step holds the final state and the density that
-// converted the initial mass fractions).
+// Checkpoint k of a cell: (y_k, h_k) when 0 <= k < cap (the record after
+// the last step holds the final state and the density that converted the
+// initial mass fractions).
 template <int TEAM>
 __device__ __forceinline__ void save_step(double* ck, int cap, int k, const double* y, double h, int n,
                                           int lane) {
-    if (!ck || k >= cap) return;
+    if (!ck || k < 0 || k >= cap) return;
     double* e = ck + (int64_t)k * (n + 1);
     for (int i = lane; i < n; i += TEAM) e[i] = y[i];
     if (lane == 0) e[n] = h;
 }
+
+// The integrators below record accepted step k as checkpoint k - rec_from
+// of ck (cap entries) and return after stop_after accepted steps: the
+// forward pass records from step 0 and never stops early; the adjoint's
+// replay of a segment records [rec_from, stop_after) of the same steps.
 
 // Fixed steps with deterministic halving: a failed step of level d is
 // replaced by two steps of level d+1 (recursively, at most max_halvings
 // deep), walked iteratively with a position counter.
 template <int TEAM, class MT>
 __device__ int integrate_fixed(const DevMech& M, const Ws& W, const IntParams& P, Counters& cnt, double* ck,
-                               int cap,
-                               int lane) {
+                               int cap, int lane, int rec_from = 0, int stop_after = 0x7fffffff) {
     const int D = P.max_halvings;
     const double hsub = P.dt / P.nsub;
     for (int s = 0; s < P.nsub; ++s) {
@@ -299,9 +321,9 @@ __device__ int integrate_fixed(const DevMech& M, const Ws& W, const IntParams& P
         while (pos < total) {
             const double h = ldexp(hsub, -d);
             if (step<TEAM, MT>(M, W, P, h, cnt, lane)) {
-                save_step<TEAM>(ck, cap, cnt.steps, W.yn, h, M.n, lane);
+                save_step<TEAM>(ck, cap, cnt.steps - rec_from, W.yn, h, M.n, lane);
                 copy_vec<TEAM>(W.yn, W.y1, M.n, lane);
-                cnt.steps++;
+                if (++cnt.steps >= stop_after) return CELL_OK;
                 pos += 1ull << (D - d);
                 while (d > 0 && ((pos >> (D - d)) & 1ull) == 0ull) --d;
             } else {
@@ -318,8 +340,7 @@ __device__ int integrate_fixed(const DevMech& M, const Ws& W, const IntParams& P
 // h min(5, max(0.2, 0.9 err^(-1/(q+1)))); Newton failure: h / 4.
 template <int TEAM, class MT>
 __device__ int integrate_adaptive(const DevMech& M, const Ws& W, const IntParams& P, Counters& cnt, double* ck,
-                                  int cap,
-                                  int lane) {
+                                  int cap, int lane, int rec_from = 0, int stop_after = 0x7fffffff) {
     const double expo = -1.0 / (P.err_order + 1.0);
     double t = 0.0;
     double h = P.h0 > 0.0 ? fmin(P.h0, P.dt) : P.dt;
@@ -338,10 +359,10 @@ __device__ int integrate_adaptive(const DevMech& M, const Ws& W, const IntParams
         double fac = e > 0.0 ? 0.9 * pow(e, expo) : 5.0;
         fac = fmin(5.0, fmax(0.2, fac));
         if (e <= 1.0) {
-            save_step<TEAM>(ck, cap, cnt.steps, W.yn, hh, M.n, lane);
+            save_step<TEAM>(ck, cap, cnt.steps - rec_from, W.yn, hh, M.n, lane);
             copy_vec<TEAM>(W.yn, W.y1, M.n, lane);
             t = last ? P.dt : t + hh;
-            cnt.steps++;
+            if (++cnt.steps >= stop_after) return CELL_OK;
         } else {
             cnt.rejects++;
         }

@@ -138,6 +138,31 @@ def test_adjoint_mixed_precision_forward(mechs, ref, handles):
     compare(m, r, h, o, og, T, Y, p, rtol=1e-5)
 
 
+@pytest.mark.parametrize("cap", [2, 5, 40])
+def test_adjoint_recomputes_steps_that_did_not_fit(mechs, handles, cap):
+    """Adaptive SDIRK-4 cells of 53 species over 5e-6 s (1 to about 50 steps
+    each; the front cells the most), their records cut to `cap` slots: the
+    adjoint replays the forward integration from the initial state in
+    segments of 32 steps and sweeps each backwards; gradients and statuses
+    are identical to the last bit to those from a record that holds every
+    step."""
+    m, h = mechs["ch4"], handles["ch4"]
+    T, Y, p = inputs.field_flames(m, 4096, seed=3)
+    idx = np.concatenate([np.linspace(0, 4095, 12).astype(int), np.arange(2500, 2900, 100)])   # + front cells
+    T, Y, p = T[idx], Y[idx], p[idx]
+    _, og = both_opts(dt=5e-6, rtol=1e-6, atol=1e-12, newton_tol=0.03, max_newton=7)
+    rng = np.random.default_rng(3)
+    a, b = rng.normal(size=len(T)), rng.normal(size=Y.shape)
+    full = gpu_adjoint(h, og, T, Y, p, a, b, cap=2048)
+    S = full["steps"]
+    assert np.all(S >= 0) and S.max() > 40          # some cells need more than one segment
+    cut = gpu_adjoint(h, og, T, Y, p, a, b, cap=cap)
+    np.testing.assert_array_equal(cut["steps"], np.where(S < cap, S, -(S + 2)))
+    assert np.all(cut["astatus"] == 0)
+    for k in ("dT0", "dY0", "dtheta", "cells"):
+        assert np.array_equal(cut[k], full[k]), k
+
+
 def test_adjoint_deterministic_and_shape_independent(mechs, handles):
     m, h = mechs["ch4"], handles["ch4"]
     T, Y, p = inputs.field_reactor(m, 300, (1150, 1400), (1, 3), (0.5, 2.0), "CH4", seed=13)
@@ -211,12 +236,16 @@ def test_adjoint_edge_cases(mechs, handles):
     assert g["dT0"][5] == 0.0 and not g["dY0"][5].any() and not g["cells"][5].any()
     ok = np.arange(len(T)) != 5
     assert np.all(g["astatus"][ok] == 0) and np.all(g["steps"][ok] == 3)
-    # too few checkpoint slots: 3 steps need 4 records
-    g2 = gpu_adjoint(h, og, T, Y, p, a, b, cap=3)
-    assert np.all(g2["steps"] == -1) and np.all(g2["astatus"] == chemgb.CG_CELL_NO_RECORD)
-    assert not g2["dtheta"].any()
+    # 3 steps need 4 records; with fewer the adjoint recomputes the steps
+    # from the initial state (two-level checkpointing): the same bits
     g3 = gpu_adjoint(h, og, T, Y, p, a, b, cap=4)
     assert np.array_equal(g3["dtheta"], g["dtheta"])
+    for cap in (3, 2):
+        g2 = gpu_adjoint(h, og, T, Y, p, a, b, cap=cap)
+        assert np.all(g2["steps"][ok] == -(3 + 2)) and g2["steps"][5] == -1
+        assert np.all(g2["astatus"][ok] == 0) and g2["astatus"][5] == chemgb.CG_CELL_NO_RECORD
+        for k in ("dT0", "dY0", "dtheta", "cells"):
+            assert np.array_equal(g2[k], g[k]), (cap, k)
     # no cells: the parameter gradient is zero
     dth = torch.full((h.nr, 3), 7.0, dtype=F64, device=DEV)
     e = torch.empty(0, dtype=F64, device=DEV)

@@ -90,6 +90,16 @@ cg_status cgx_thermo_table(int ns, int np, const double *coef, int *P, double *t
  * Errors: CG_EINVAL (NULL arrays, a method without a tableau). */
 cg_status cgx_tableau(int method, int *s, double *A, double *b, double *bh, int *err_order);
 
+/* Debug build only (compiled with CG_DEBUG: one-warp teams, two guard
+ * words after every array of a cell's working memory, every array poisoned
+ * with NaN -- zero for the pivot and reduction integers -- before each cell
+ * of cg_integrate, the guards checked after it). Synchronises the device,
+ * then writes the arrays whose guards changed since the last call (bit a:
+ * the library's array number a) to *arrays and the first such cell to
+ * *first_cell (-1: none), and clears both. Errors: CG_EINVAL, CG_ECUDA;
+ * CG_EUNSUPPORTED in the normal build. */
+cg_status cgx_debug_flags(const cg_mech *mech, uint64_t *arrays, int64_t *first_cell);
+
 /* The scratch cg_integrate_noalloc would need for a mechanism of ns
  * species and nr reactions: the per-cell layout for mat_bytes (8 FP64, 4
  * FP32 Newton matrix), smem_limit bytes of shared memory per cell and

@@ -17,6 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libchemgb.so")
+# the debug build (CG_DEBUG: guard words and poisoned working memory, checked
+# after every cell; one-warp teams only), for tests that look for memory errors
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libchemgb_debug.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -38,17 +42,21 @@ def _sources():
     return sorted(p for p in glob.glob(os.path.join(CSRC, "*.cu")) if os.path.basename(p) != "instances.cu")
 
 
-def _jobs():
+def _jobs(debug: bool = False):
     """(command, object) of every translation unit, slowest first."""
     jobs = []
+    out = BUILD_DEBUG if debug else BUILD
+    flags = NVCC_FLAGS + (["-DCG_DEBUG=1"] if debug else [])
     inst = os.path.join(CSRC, "instances.cu")
     for team, mt in INSTANCES:
-        obj = os.path.join(BUILD, f"instances_t{team}_{'f64' if mt == 'double' else 'f32'}.o")
+        if debug and team != 32:
+            continue
+        obj = os.path.join(out, f"instances_t{team}_{'f64' if mt == 'double' else 'f32'}.o")
         defs = [f"-DCG_TEAM={team}", f"-DCG_MT={mt}", f"-DCG_MT_F64={1 if mt == 'double' else 0}"]
-        jobs.append((NVCC_FLAGS + defs + ["-c", inst, "-o", obj], obj))
+        jobs.append((flags + defs + ["-c", inst, "-o", obj], obj))
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        jobs.append((NVCC_FLAGS + ["-c", src, "-o", obj], obj))
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
+        jobs.append((flags + ["-c", src, "-o", obj], obj))
     return jobs
 
 
@@ -57,19 +65,21 @@ def _deps():
         + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def is_stale(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not is_stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not is_stale(debug):
+        return lib
+    os.makedirs(BUILD_DEBUG if debug else BUILD, exist_ok=True)
     nvcc = _nvcc()
-    jobs = _jobs()
+    jobs = _jobs(debug)
     objs = [obj for _, obj in jobs]
     # an object is rebuilt when it is older than its source or any header
     headers = [p for p in _deps() if not p.endswith(".cu")]
@@ -93,14 +103,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             for _, q in running:
                 q.kill()
             raise RuntimeError("nvcc failed: " + " ".join(cmd) + "\n" + out.decode(errors="replace"))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

@@ -58,11 +58,13 @@ EXPORTED = ("cg_mech_create", "cg_mech_destroy", "cg_mech_n_species", "cg_mech_n
             "cg_integrate_adjoint", "cg_mech_set_arrhenius", "cgx_exp_check", "cg_react_split",
             "cgx_schedule", "cgx_rate_chunks", "cgx_layout", "cg_mech_set_thermo",
             "cgx_thermo_table", "cgx_tableau", "cgx_rcp_check", "cgx_noalloc_plan", "cg_mech_set_lu_panel",
-            "cg_mech_get_lu_panel")
+            "cg_mech_get_lu_panel", "cgx_debug_flags")
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: libchemgb.so, or the build named by
+    the CHEMGB_LIB environment variable (the debug build in its tests)."""
+    return os.environ.get("CHEMGB_LIB") or _build.LIB
 
 
 def load(build_if_missing: bool = False):
@@ -70,12 +72,13 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing:
+    path = library_path()
+    if build_if_missing and path == _build.LIB:
         _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"chemgb CUDA library not built ({_build.LIB}); run "
+    if not os.path.exists(path):
+        raise RuntimeError(f"chemgb CUDA library not built ({path}); run "
                            "python -m paper_2510_10005_gb300.build")
-    lib = ctypes.CDLL(_build.LIB)
+    lib = ctypes.CDLL(path)
     P, I, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
     lib.cg_mech_create.argtypes = [ctypes.POINTER(cg_mech_desc), ctypes.POINTER(P)]
     lib.cg_mech_destroy.argtypes = [P]
@@ -109,6 +112,7 @@ def load(build_if_missing: bool = False):
     lib.cgx_rate_chunks.argtypes = [I, P, I, P, P, P, P, I]
     lib.cgx_layout.argtypes = [I, I, I, L, I, I] + [P] * 8
     lib.cgx_rcp_check.argtypes = [L, P, P, P]
+    lib.cgx_debug_flags.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64)]
     lib.cgx_noalloc_plan.argtypes = [I, I, I, L, I, I, I, ctypes.POINTER(ctypes.c_int64)]
     lib.cgx_tableau.argtypes = [I, P, P, P, P, P]
     lib.cg_react_split.argtypes = [P, ctypes.POINTER(cg_integrate_opts), L, P, P, P, P, P, I, P, P, P]
@@ -358,6 +362,14 @@ def cgx_thermo_table(coef):
 def cgx_rcp_check(x, y, stream=None):
     """Test hook: the library's pivot reciprocal of x (CUDA tensors)."""
     _check(load().cgx_rcp_check(x.shape[0], _dev(x), _dev(y), _stream(stream)))
+
+
+def cgx_debug_flags(h):
+    """Debug build only: (arrays whose guard words changed as a bit mask,
+    first such cell or -1), cleared by the call."""
+    a, c = ctypes.c_uint64(0), ctypes.c_int64(-1)
+    _check(load().cgx_debug_flags(h.ptr, ctypes.byref(a), ctypes.byref(c)))
+    return a.value, c.value
 
 
 def cgx_noalloc_plan(ns: int, nr: int, mat_bytes: int, smem_limit: int, team: int, teams_per_block: int,

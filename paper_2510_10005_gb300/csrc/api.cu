@@ -154,7 +154,12 @@ Layout make_layout(int ns, int nr, int mat_bytes, size_t smem_limit, bool adjoin
     bool spill = false;
     for (int k = 0; k < A_COUNT; ++k) {
         const int a = order[k];
+#ifdef CG_DEBUG
+        L.size[a] = (size[a] + 1) & ~1;
+        const int sz = L.size[a] + (size[a] ? kGuard : 0);   // guard words after each array
+#else
         const int sz = (size[a] + 1) & ~1;   // 16-byte aligned arrays
+#endif
         if (a == A_RED || (!spill && so + sz <= budget)) {
             L.off[a] = so;
             so += sz;
@@ -626,6 +631,24 @@ cg_status cgx_exp_check(const cg_mech* m, int64_t n, const double* x, double* y_
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "exp check launch");
 }
 
+cg_status cgx_debug_flags(const cg_mech* m, uint64_t* arrays, int64_t* first_cell) {
+    if (!m || !arrays || !first_cell) return fail(CG_EINVAL, "bad arguments");
+#ifdef CG_DEBUG
+    unsigned long long h[2] = {0ull, 0ull};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, m->dm.dbg, sizeof h, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(m->dm.dbg, 0, sizeof h);
+    if (e != cudaSuccess) return cuda_fail(e, "debug flags");
+    *arrays = h[0];
+    *first_cell = (int64_t)h[1] - 1;
+    return CG_OK;
+#else
+    *arrays = 0;
+    *first_cell = -1;
+    return fail(CG_EUNSUPPORTED, "not a debug build (build with debug=True)");
+#endif
+}
+
 cg_status cgx_rcp_check(int64_t n, const double* x, double* y, void* stream) {
     if (n < 0 || (n > 0 && (!x || !y))) return fail(CG_EINVAL, "bad arguments");
     cudaError_t e = cg::launch_rcp_check(n, x, y, (cudaStream_t)stream);
@@ -942,6 +965,17 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
         cg_mech_destroy(m);
         return st;
     }
+#ifdef CG_DEBUG
+    {
+        const std::vector<unsigned long long> zero(2, 0ull);
+        const unsigned long long* dbg = nullptr;
+        if ((st = upload(m->allocs, zero, &dbg)) != CG_OK) {
+            cg_mech_destroy(m);
+            return st;
+        }
+        dm.dbg = const_cast<unsigned long long*>(dbg);
+    }
+#endif
     std::vector<double> exp2j(64);   // 2^(j/64), rounded once from extended precision
     for (int j = 0; j < 64; ++j) exp2j[j] = (double)std::exp2((long double)j / 64.0L);
     if ((st = upload(m->allocs, exp2j, &dm.exp2j)) != CG_OK) {

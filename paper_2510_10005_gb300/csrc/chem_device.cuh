@@ -88,6 +88,9 @@ struct DevMech {
     int has_plog;
     const int *pl_lev, *pl_rate;
     const double *pl_lnp, *pl_lnA, *pl_b, *pl_Ta;
+#ifdef CG_DEBUG
+    unsigned long long* dbg;     // [2]: arrays whose guard words changed (bit a), first such cell + 1
+#endif
 };
 
 // Working arrays of one cell. Each lives in the team's slice of shared
@@ -124,7 +127,21 @@ struct Layout {
     unsigned gmask;          // bit a set: array a is in global scratch
     int stotal;              // doubles of shared memory per team
     int gtotal;              // doubles of global scratch per team
+#ifdef CG_DEBUG
+    int size[A_COUNT];       // doubles of each array; kGuard guard words follow it
+#endif
 };
+
+#ifdef CG_DEBUG
+// Debug build (stands in for a memory checker): two guard words after each
+// array of a cell, every array poisoned before each cell (NaN, so that a
+// value read before it is written spoils the result; zero for the pivot
+// and reduction arrays, whose integers index rows), guards checked after it.
+constexpr int kGuard = 2;
+constexpr unsigned long long kCanary = 0x7ff4c0ffee000000ull;   // a signalling-NaN pattern
+constexpr unsigned long long kPoison = 0x7ff4deadbeef0000ull;
+
+#endif
 
 struct Ws {
     int ld;
@@ -215,6 +232,38 @@ __device__ __forceinline__ bool team_any(bool b, double* red) {
         return r != 0;
     }
 }
+
+#ifdef CG_DEBUG
+template <int TEAM>
+__device__ void debug_poison(const Layout& L, double* sbase, double* gbase, int lane) {
+    for (int a = 0; a < A_COUNT; ++a) {
+        if (L.size[a] == 0) continue;
+        double* p = ((L.gmask >> a) & 1u ? gbase : sbase) + L.off[a];
+        const unsigned long long fill = (a == A_PIV || a == A_RED) ? 0ull : kPoison;
+        for (int i = lane; i < L.size[a] + kGuard; i += TEAM)
+            p[i] = __longlong_as_double((long long)(i < L.size[a] ? fill : kCanary + a));
+    }
+    team_sync<TEAM>();
+}
+
+template <int TEAM>
+__device__ void debug_check(const Layout& L, double* sbase, double* gbase, unsigned long long* dbg,
+                            int64_t cell, int lane) {
+    team_sync<TEAM>();
+    unsigned long long bad = 0ull;
+    for (int a = lane; a < A_COUNT; a += TEAM) {
+        if (L.size[a] == 0) continue;
+        const double* p = ((L.gmask >> a) & 1u ? gbase : sbase) + L.off[a] + L.size[a];
+        for (int g = 0; g < kGuard; ++g)
+            if ((unsigned long long)__double_as_longlong(p[g]) != kCanary + a) bad |= 1ull << a;
+    }
+    if (bad) {
+        atomicOr(dbg, bad);
+        atomicCAS(dbg + 1, 0ull, (unsigned long long)cell + 1ull);
+    }
+    team_sync<TEAM>();
+}
+#endif
 
 // Walks a rows x ncol row-major index space with stride S from `lane`.
 struct Flat2D {

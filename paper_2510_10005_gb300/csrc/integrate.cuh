@@ -144,7 +144,13 @@ __global__ void __maxnreg__((KernelRegs<TEAM, MT>::value)) integrate_kernel(Task
         while (k + 1 < tasks.count && g >= tasks.t[k + 1].first) ++k;
         const Task& tk = tasks.t[k];
         const Ws W = make_ws(tk.L, sbase, gbase);
+#ifdef CG_DEBUG
+        debug_poison<TEAM>(tk.L, sbase, gbase, tp.lane);
+#endif
         integrate_cell<TEAM, MT>(tk, W, P, g - tk.first, tp.lane);
+#ifdef CG_DEBUG
+        debug_check<TEAM>(tk.L, sbase, gbase, tk.M.dbg, g - tk.first, tp.lane);
+#endif
     }
 }
 

@@ -425,6 +425,7 @@ static inline cudaError_t put_mem(LaunchMem& m, cudaStream_t st) {
     return e;
 }
 
+#ifndef CG_DEBUG
 #define CG_DISPATCH_TEAM(team, CALL)                         \
     switch (team) {                                          \
         case 32: return CALL(32);                            \
@@ -433,5 +434,12 @@ static inline cudaError_t put_mem(LaunchMem& m, cudaStream_t st) {
         case 256: return CALL(256);                          \
         default: return cudaErrorInvalidValue;               \
     }
+#else   // the debug build holds the one-warp teams only
+#define CG_DISPATCH_TEAM(team, CALL)                         \
+    switch (team) {                                          \
+        case 32: return CALL(32);                            \
+        default: return cudaErrorInvalidValue;               \
+    }
+#endif
 
 }  // namespace cg

@@ -127,7 +127,7 @@ def j_term_count(mech) -> int:
     return total
 
 
-FP32_PEAK = 6.98e13   # FLOP/s, measured FP32 FMA rate on this GB300 (register-resident loop)
+FP32_PEAK = 7.679e13  # FLOP/s, FP32 FMA rate measured by bench_peaks.py on this GB300 (2070 MHz)
 
 
 def fp64_peak(sm_count: int, sm_max_mhz: float) -> float:
@@ -582,7 +582,7 @@ def run_gpu(args):
         **({"roofline_fp32": {"bound": "alu", "achieved": flops32 / (launch_ms * 1e-3) / 1e12, "peak": FP32_PEAK / 1e12,
                               "unit": "TFLOP/s", "frac": flops32 / (launch_ms * 1e-3) / FP32_PEAK,
                               "what": "FP32 LU factorisations of the mixed-precision Newton (2n^3/3 each)",
-                              "peak_source": "measured FP32 FMA rate (register-resident loop)",
+                              "peak_source": "measured FP32 FMA rate (bench_peaks.py)",
                               "time_weighted_frac": (flops / peak + flops32 / FP32_PEAK) / (launch_ms * 1e-3)}}
            if flops32 > 0 else {}),
         "cpu_baseline": cpu,

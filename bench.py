@@ -14,7 +14,8 @@ Other workloads (reported beside the default line):
   --config 3  53 + 9 species in ONE persistent work-stealing launch,
               1,048,576 heavy-tailed cells each (90% frozen, 5% burnt,
               5% reacting, randomly interleaved), FP32 Newton matrix,
-              autotuned launch shape, replayed from a captured CUDA graph
+              autotuned launch shape for the 53 species (the 9 species run
+              one warp per cell inside it), replayed from a captured CUDA graph
   --config 4  discrete adjoint: 53 species, 65,536 cells, T0 in U[1100, 1400] K,
               1 atm, phi in U[0.5, 2], adaptive SDIRK-4 over dt = 1e-4 s with
               checkpoints, then the backward sweep for
@@ -291,7 +292,9 @@ def oracle_opts(o: dict) -> dict:
 # The oracle's timing sample of each workload: cells evenly spaced through
 # every mechanism's field (so in proportion from the regions of the
 # contiguous flame field, and a uniform sample of the interleaved ones)
-CPU_SAMPLE = {1: 4096, 2: 4096, 3: 4096, 4: 256, 5: 1024}
+CPU_SAMPLE = {1: 4096, 2: 4096, 3: 4096, 4: 256, 5: 256}
+# and of the one-core timing beside it (160 species: about 1 s per cell)
+ONE_CORE_SAMPLE = {1: 256, 2: 256, 3: 256, 4: 16, 5: 16}
 
 
 def sample_indices(n_cells: int, k: int) -> np.ndarray:
@@ -437,8 +440,9 @@ def run_gpu(args):
 
     tuned = None
     if (args.config == 3 or args.autotune) and not args.team:
-        # autotune the launch shape on the dominant mechanism, then give the
-        # other one the same team size (one launch needs one team size)
+        # autotune the launch shape on the dominant mechanism; the others keep
+        # their own team size (a one-warp mechanism in a wider launch runs
+        # split: each warp of a team integrates its own cells)
         k = min(16384, len(bufs[0]["T0"]))
         sel = torch.linspace(0, len(bufs[0]["T0"]) - 1, k, device=dev).long()
         cache = os.path.join(tempfile.mkdtemp(prefix="chemgb_tune_"), "shape.json")   # new: always tunes
@@ -446,7 +450,9 @@ def run_gpu(args):
                                 bufs[0]["Y0"][:, sel].contiguous(), bufs[0]["P"][sel].contiguous(), cache)
         team, tpb = chemgb.cg_mech_get_launch(handles[0])
         for h in handles[1:]:
-            chemgb.cg_mech_set_launch(h, team, tpb if team == 32 else 1)
+            t_own, _ = chemgb.cg_mech_get_launch(h)
+            if t_own != 32 and t_own != team:   # only one-warp mechanisms can run split
+                chemgb.cg_mech_set_launch(h, team, tpb if team == 32 else 1)
         tuned = {"team": team, "teams_per_block": tpb, "sample_ms": ms}
         try:   # the shared-memory limit per cell and the LU panel width the tuner chose
             with open(cache) as f:
@@ -558,9 +564,9 @@ def run_gpu(args):
         cpu = {"value": k / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
                "sample": f"{k} cells evenly spaced through the field, median of {len(times)} timings "
                          f"({', '.join(f'{t:.2f}' for t in times)} s)"}
-        if args.cpu_1core_cells > 0:   # the same oracle on one host core
-            k1, el1, t1 = median_timing(lambda n: cpu_oracle_sample(parts, opts_d, n, 1, split)[1:],
-                                        args.cpu_1core_cells, 1)
+        one = ONE_CORE_SAMPLE[args.config] if args.cpu_1core_cells is None else args.cpu_1core_cells
+        if one > 0:   # the same oracle on one host core
+            k1, el1, t1 = median_timing(lambda n: cpu_oracle_sample(parts, opts_d, n, 1, split)[1:], one, 1)
             cpu["one_core"] = {"value": k1 / el1, "unit": "cells/s", "cores": 1,
                                "sample": f"{k1} cells evenly spaced through the field ({el1:.1f} s)"}
     state_bytes = sum(len(T) * (m.ns + 2) * 8 for m, T, _, _ in parts)
@@ -761,8 +767,9 @@ def run_adjoint(args):
         cpu = {"value": k / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
                "sample": f"{k} cells evenly spaced, forward + adjoint, median of {len(times)} timings "
                          f"({', '.join(f'{t:.2f}' for t in times)} s)"}
-        if args.cpu_1core_cells > 0:   # the same oracle on one host core
-            k1, el1, _ = median_timing(lambda n: run(n, 1), max(1, args.cpu_1core_cells // 16), 1)
+        one = ONE_CORE_SAMPLE[4] if args.cpu_1core_cells is None else args.cpu_1core_cells
+        if one > 0:   # the same oracle on one host core
+            k1, el1, _ = median_timing(lambda n: run(n, 1), one, 1)
             cpu["one_core"] = {"value": k1 / el1, "unit": "cells/s", "cores": 1,
                                "sample": f"{k1} cells evenly spaced, forward + adjoint ({el1:.1f} s)"}
     line = {
@@ -837,8 +844,9 @@ def main():
                     help="cells of the oracle's timing sample, in the cpu_baseline leg and the reference arm "
                          "(0: the workload's, " + ", ".join(f"config {c}: {k}" for c, k in CPU_SAMPLE.items()) + ")")
     ap.add_argument("--cpu-repeats", type=int, default=5, help="timings of the cpu_baseline sample (median)")
-    ap.add_argument("--cpu-1core-cells", type=int, default=256,
-                    help="cells of the one-core oracle timing reported beside cpu_baseline (0: skip)")
+    ap.add_argument("--cpu-1core-cells", type=int, default=None,
+                    help="cells of the one-core oracle timing reported beside cpu_baseline (0: skip; default "
+                         + ", ".join(f"config {c}: {k}" for c, k in ONE_CORE_SAMPLE.items()) + ")")
     ap.add_argument("--lu-panel", type=int, default=None,
                     help="panel width of the blocked LU (0: unblocked; default: the library's choice)")
     ap.add_argument("--smem-limit", type=int, default=0,

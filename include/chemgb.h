@@ -155,7 +155,7 @@ int cg_mech_n_reactions(const cg_mech *mech);
 /* Launch shape of every kernel that uses this mechanism: `team` threads
  * (32, 64, 128 or 256) cooperate on one cell and `teams_per_block` cells
  * share a block (must be 1 when team > 32). The default is one warp per cell
- * up to 24 unknowns, two warps per cell up to 96 and eight above. Changing
+ * up to 24 unknowns, two warps per cell up to 96 and four above. Changing
  * the team size
  * rebuilds the assembly schedules (synchronises the device); no call using
  * the mechanism may run concurrently. Results do not depend on the shape
@@ -172,10 +172,10 @@ cg_status cg_mech_set_launch(cg_mech *mech, int team, int teams_per_block);
  * cells per SM. Default: 227 KiB, except when the per-reaction block (9 nr
  * doubles) is at least 8 KiB of a per-cell total of 40 KiB or more; then
  * the limit keeps everything but that block in shared memory (53 species /
- * 325 reactions: 33 KiB per cell, 6 cells per SM instead of 4); and for the
- * FP32 Newton matrix 113.5 KiB where that lets two cells share an SM that
- * would otherwise hold one (160 species). This call sets one limit for
- * both matrix types. Same
+ * 325 reactions: 33 KiB per cell, 6 cells per SM instead of 4); and 64 KiB
+ * when the FP64 Newton matrix alone exceeds half of 227 KiB (160 species),
+ * which puts the whole working set in the L2 slot so that four cells share
+ * an SM. This call sets one limit for both matrix types. Same
  * concurrency rule as cg_mech_set_launch. Launch tuning, not part of the
  * paper's method. */
 cg_status cg_mech_set_smem_limit(cg_mech *mech, int64_t bytes);
@@ -287,8 +287,13 @@ cg_status cg_integrate(const cg_mech *mech, const cg_integrate_opts *opts, int64
  * which resident teams take cells through a shared work counter, so cheap
  * and expensive cells of either mechanism balance across the GPU. Array
  * k-th entries are those of cg_integrate for mechanism k (cell_status and
- * cell_stats may be NULL, or hold NULL entries). All mechanisms must use the
- * same team size (cg_mech_set_launch); the same options apply to all.
+ * cell_stats may be NULL, or hold NULL entries). The launch takes the
+ * largest team size of the mechanisms (cg_mech_set_launch); mechanisms of
+ * one-warp teams in a wider launch run split: once the other mechanisms'
+ * cells are taken, every warp of a team claims their cells on its own from
+ * a second counter and integrates them with one warp per cell, as
+ * cg_integrate would (the same results to the last bit). Other team sizes
+ * must all be equal (CG_EINVAL otherwise). The same options apply to all.
  * Allocates its work counter and any global scratch stream-ordered
  * (cudaMallocAsync) and releases them on the same stream. */
 cg_status cg_integrate_batch(int n_mech, const cg_mech *const *mechs, const int64_t *N,

@@ -392,11 +392,11 @@ namespace {
 
 // Default launch shape: one warp per cell for small mechanisms (several
 // cells per block), two warps per cell from 24 unknowns on, so that every SM
-// sub-partition holds two instruction streams, and eight warps from 96 on,
-// where the Newton matrix alone fills an SM's shared memory and one cell's
-// team must keep all four sub-partitions busy (measured at 161 unknowns:
-// 2.2 times the rate of two warps).
-int default_team(int n) { return n <= 24 ? 32 : (n <= 96 ? 64 : 256); }
+// sub-partition holds two instruction streams, and four warps above 96
+// unknowns, with the working set in L2 (below): at 161 unknowns four such
+// cells per SM run 1.4 times the rate of one eight-warp cell holding its
+// Newton matrix in shared memory (measured, FP64 and FP32 matrices).
+int default_team(int n) { return n <= 24 ? 32 : (n <= 96 ? 64 : 128); }
 
 // Default shared memory per cell: everything, unless the per-reaction block
 // (rates of progress and their partial derivatives, 9 nr doubles, read by
@@ -405,6 +405,11 @@ int default_team(int n) { return n <= 24 ? 32 : (n <= 96 ? 64 : 256); }
 // (measured at 53 species / 325 reactions: 6 cells per SM instead of 4,
 // 1.29 times the rate).
 size_t default_smem_limit(int ns, int nr) {
+    const int n = ns + 1, ld = (n % 2) ? n : n + 1;
+    // a Newton matrix too large for two cells per SM: the whole working set
+    // goes to the L2 slot (the layout keeps the priority order, so nothing
+    // after the matrix stays in shared memory either)
+    if ((size_t)n * ld * sizeof(double) > kMaxSmemPerBlock / 2) return 64 * 1024;
     const Layout full = make_layout(ns, nr, 8, kMaxSmemPerBlock);
     const size_t rd = 9 * (size_t)nr * sizeof(double);
     const size_t per_cell = (size_t)full.stotal * sizeof(double);
@@ -412,21 +417,12 @@ size_t default_smem_limit(int ns, int nr) {
     return per_cell - rd + 1024;   // the layout keeps 1 KiB of the limit free
 }
 
-// Default for the FP32 Newton matrix: the FP64 default, unless that leaves
-// one cell per SM while the FP32 matrix with the arrays placed before it
-// would let two share it (161 unknowns: 104 KB matrix; 1.7 times the rate
-// with four warps per cell, measured).
-size_t default_smem_limit32(int ns, int nr, size_t limit64) {
-    const size_t half = kMaxSmemPerBlock / 2;   // two cells per SM
-    const Layout at64 = make_layout(ns, nr, 4, limit64);
-    const Layout at_half = make_layout(ns, nr, 4, half);
-    if ((size_t)at64.stotal * sizeof(double) <= half) return limit64;
-    return (at_half.gmask >> cg::A_G) & 1u ? limit64 : half;   // only if the matrix itself fits
-}
 
 // Default panel width of the LU: unblocked for small matrices (the
 // rank-one loop packs the trailing block into whole warps, the tiles leave
-// lanes idle at the ragged edges), panels of 16 above.
+// lanes idle at the ragged edges), panels of 16 above (161 unknowns with the
+// matrix in L2: 1.26 times the unblocked rate, fewer L2 accesses per
+// multiply-add).
 int default_lu_nb(int n) { return n >= 96 ? 16 : 0; }
 
 int default_tpb(int team, const Layout& L) {
@@ -927,7 +923,7 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     m->ns = ns;
     m->nr = nr;
     m->L = L;
-    m->L32 = make_layout(ns, nr, 4, default_smem_limit32(ns, nr, smem_limit));
+    m->L32 = make_layout(ns, nr, 4, smem_limit);
     m->LA = make_layout(ns, nr, 8, smem_limit, true);
     m->smem_limit = smem_limit;
     m->perm = perm;
@@ -1145,21 +1141,31 @@ cg_status cg_integrate_batch(int n_mech, const cg_mech* const* mechs, const int6
     cg::Tasks tasks;
     tasks.count = n_mech;
     tasks.total = 0;
-    const int team = mechs[0] ? mechs[0]->dm.team : 0;
+    tasks.total_split = 0;
+    // the launch's team size is the largest; one-warp mechanisms in a wider
+    // launch run split (each warp of a team integrates its own cells)
+    int team = 0;
+    for (int k = 0; k < n_mech; ++k) {
+        if (!mechs[k]) return fail(CG_EINVAL, "mechs[%d] is NULL", k);
+        team = std::max(team, mechs[k]->dm.team);
+    }
+    int tpb = 1 << 30;
     for (int k = 0; k < n_mech; ++k) {
         const cg_mech* m = mechs[k];
-        if (!m) return fail(CG_EINVAL, "mechs[%d] is NULL", k);
-        if (m->dm.team != team)
-            return fail(CG_EINVAL, "all mechanisms of a batch need the same team size (cg_mech_set_launch)");
+        const bool split = m->dm.team < team;
+        if (split && m->dm.team != 32)
+            return fail(CG_EINVAL, "a batch may mix one-warp mechanisms with one wider team size; mechanism %d has "
+                                   "%d threads per cell in a launch of %d (cg_mech_set_launch)", k, m->dm.team, team);
         if (N[k] < 0) return fail(CG_EINVAL, "N[%d] < 0", k);
         if (N[k] > 0 && (!T[k] || !Y[k] || !p_or_rho[k])) return fail(CG_EINVAL, "NULL array for mechanism %d", k);
-        tasks.t[k] = make_task(m, P, N[k], tasks.total, T[k], Y[k], p_or_rho[k],
+        int64_t& space = split ? tasks.total_split : tasks.total;
+        tasks.t[k] = make_task(m, P, N[k], space, T[k], Y[k], p_or_rho[k],
                                cell_status ? cell_status[k] : nullptr, cell_stats ? cell_stats[k] : nullptr);
-        tasks.total += N[k];
+        tasks.t[k].split = split ? 1 : 0;
+        space += N[k];
+        if (!split) tpb = std::min(tpb, m->tpb);
     }
-    if (tasks.total == 0) return CG_OK;
-    int tpb = mechs[0]->tpb;
-    for (int k = 1; k < n_mech; ++k) tpb = std::min(tpb, mechs[k]->tpb);
+    if (tasks.total + tasks.total_split == 0) return CG_OK;
     cudaError_t e = cg::launch_integrate(tasks, P, team, tpb, true, (cudaStream_t)stream);
     return e == cudaSuccess ? CG_OK : cuda_fail(e, "integrate launch");
 }
@@ -1551,7 +1557,7 @@ cg_status noalloc_array(double** out) {
 // Scratch an integration launch of these tasks needs from the fixed array:
 // one slot per team of every resident block, at least one block's worth.
 cg_status noalloc_plan(const cg::Tasks& tasks, int team, int tpb, int64_t* need_doubles) {
-    const int64_t per_block = cg::integrate_slot_doubles(tasks) * cg::integrate_tpb(tasks, team, tpb);
+    const int64_t per_block = cg::integrate_slot_doubles(tasks, team) * cg::integrate_tpb(tasks, team, tpb);
     const int64_t avail = kNoAllocDoubles - kNoAllocCounterDoubles;
     if (need_doubles) *need_doubles = per_block;
     if (per_block > avail)

@@ -14,6 +14,11 @@ struct Task {
     DevMech M;
     Layout L;
     int64_t N, first;
+    // split (a one-warp mechanism in a launch of wider teams): its cells are
+    // integrated by single warps, each with its own slice of the team's
+    // shared memory and scratch slot, and numbered in the launch's second
+    // index space (first counts there)
+    int split = 0;
     double* T;
     double* Y;
     const double* p;
@@ -68,7 +73,8 @@ constexpr int kMaxTasks = 4;
 struct Tasks {
     Task t[kMaxTasks];
     int count;
-    int64_t total;
+    int64_t total;         // cells of the tasks run by whole teams
+    int64_t total_split = 0;   // cells of the split tasks (0: none)
 };
 
 cudaError_t launch_eval_rates(const DevMech& M, const Layout& L, int tpb, int reactor, int64_t N,
@@ -92,10 +98,12 @@ cudaError_t launch_integrate_on(const Tasks& tasks, const IntParams& P, int team
 // Global scratch of one team's slot (doubles) and the teams per block an
 // integration launch of `team` threads per cell actually uses (the requested
 // count, lowered until the block's shared memory fits in 227 KB).
-int64_t integrate_slot_doubles(const Tasks& tasks);
+// A team of `team` threads holds one cell of a whole-team task or team/32
+// cells of a split task at a time.
+int64_t integrate_slot_doubles(const Tasks& tasks, int team);
 int integrate_tpb(const Tasks& tasks, int team, int tpb);
 // Shared-memory stride (doubles) of one team's slice: the largest of the tasks.
-int integrate_sstride(const Tasks& tasks);
+int integrate_sstride(const Tasks& tasks, int team);
 // Operator-split reaction step (persistent launch, `team` threads per cell).
 cudaError_t launch_react_split(const SplitTask& t, const IntParams& P, int team, int tpb, cudaStream_t st);
 // Backward sweep of the discrete adjoint over the cells of t (persistent

@@ -132,25 +132,43 @@ __device__ void integrate_cell(const Task& tk, const Ws& W, const IntParams& P, 
 }
 
 template <int TEAM, class MT>
-__global__ void __maxnreg__((KernelRegs<TEAM, MT>::value)) integrate_kernel(Tasks tasks, IntParams P, int sstride, double* gscratch,
-                                 int64_t gstride, unsigned long long* counter) {
+__global__ void __maxnreg__((KernelRegs<TEAM, MT>::value)) integrate_kernel(Tasks tasks, IntParams P, int sstride,
+                                                                              double* gscratch, int64_t gstride,
+                                                                              unsigned long long* counter) {
     extern __shared__ double smem_all[];
     const TeamPos<TEAM> tp;
     double* sbase = smem_all + (size_t)tp.tib * sstride;
     double* gbase = gscratch ? gscratch + tp.id * gstride : nullptr;
     for (int64_t g = first_cell<TEAM>(counter, tp.id, tp.lane); g < tasks.total;
          g = next_cell<TEAM>(counter, g, tp.count, tp.lane)) {
-        int k = 0;
-        while (k + 1 < tasks.count && g >= tasks.t[k + 1].first) ++k;
+        int k = 0;   // the whole-team task holding g (tasks of no cells are skipped)
+        while (tasks.t[k].split || g >= tasks.t[k].first + tasks.t[k].N) ++k;
         const Task& tk = tasks.t[k];
-        const Ws W = make_ws(tk.L, sbase, gbase);
 #ifdef CG_DEBUG
         debug_poison<TEAM>(tk.L, sbase, gbase, tp.lane);
 #endif
-        integrate_cell<TEAM, MT>(tk, W, P, g - tk.first, tp.lane);
+        integrate_cell<TEAM, MT>(tk, make_ws(tk.L, sbase, gbase), P, g - tk.first, tp.lane);
 #ifdef CG_DEBUG
         debug_check<TEAM>(tk.L, sbase, gbase, tk.M.dbg, g - tk.first, tp.lane);
 #endif
+    }
+    if constexpr (TEAM > 32) {
+        // Split tasks (one-warp mechanisms in this wider launch), once the
+        // whole-team cells are taken: every warp of the team claims cells on
+        // its own from the second counter, in its own part of the team's
+        // shared slice and scratch slot, with no barrier across the team.
+        if (tasks.total_split > 0 && counter) {
+            const int w = tp.lane >> 5, l = tp.lane & 31;
+            for (int64_t c = next_cell<32>(counter + 1, 0, 0, l); c < tasks.total_split;
+                 c = next_cell<32>(counter + 1, 0, 0, l)) {
+                int k = 0;
+                while (!tasks.t[k].split || c >= tasks.t[k].first + tasks.t[k].N) ++k;
+                const Task& tk = tasks.t[k];
+                double* ws = sbase + (size_t)w * tk.L.stotal;
+                double* wg = gbase ? gbase + (int64_t)w * round_up(tk.L.gtotal, 32) : nullptr;
+                integrate_cell<32, MT>(tk, make_ws(tk.L, ws, wg), P, c - tk.first, l);
+            }
+        }
     }
 }
 
@@ -190,14 +208,16 @@ template <int TEAM, class MT>
 cudaError_t launch_integrate_team(const Tasks& tasks, const IntParams& P, int tpb, bool persistent,
                                   cudaStream_t st) {
     tpb = integrate_tpb(tasks, TEAM, tpb);
-    const int sstride = integrate_sstride(tasks);
-    const int64_t gstride = integrate_slot_doubles(tasks);   // 256-byte aligned slots
+    const int sstride = integrate_sstride(tasks, TEAM);
+    const int64_t gstride = integrate_slot_doubles(tasks, TEAM);   // 256-byte aligned slots
     const void* fn = (const void*)integrate_kernel<TEAM, MT>;
     const size_t smem = (size_t)tpb * sstride * sizeof(double);
     cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
-    int64_t blocks = (tasks.total + tpb - 1) / tpb;
-    const bool queue = persistent || gstride > 0;
+    const int64_t units = tasks.total > tasks.total_split / (TEAM / 32) ? tasks.total
+                                                                        : tasks.total_split / (TEAM / 32) + 1;
+    int64_t blocks = (units + tpb - 1) / tpb;
+    const bool queue = persistent || gstride > 0 || tasks.total_split > 0;
     if (queue) {
         int64_t res = 0;
         if ((e = resident_blocks(fn, TEAM * tpb, smem, &res)) != cudaSuccess) return e;
@@ -221,8 +241,8 @@ template <int TEAM, class MT>
 cudaError_t launch_integrate_on_team(const Tasks& tasks, const IntParams& P, int tpb, double* scratch,
                                      int64_t scratch_doubles, unsigned long long* counter, cudaStream_t st) {
     tpb = integrate_tpb(tasks, TEAM, tpb);
-    const int sstride = integrate_sstride(tasks);
-    const int64_t gstride = integrate_slot_doubles(tasks);
+    const int sstride = integrate_sstride(tasks, TEAM);
+    const int64_t gstride = integrate_slot_doubles(tasks, TEAM);
     const void* fn = (const void*)integrate_kernel<TEAM, MT>;
     const size_t smem = (size_t)tpb * sstride * sizeof(double);
     cudaError_t e = set_smem(fn, smem);

@@ -84,21 +84,29 @@ __global__ void sum_rows_kernel(int64_t N, const double* __restrict__ g, double*
 // ---------------------------------------------------------------------------
 // launch planning
 
-int64_t integrate_slot_doubles(const Tasks& tasks) {
+int64_t integrate_slot_doubles(const Tasks& tasks, int team) {
     int64_t g = 0;
-    for (int k = 0; k < tasks.count; ++k) g = g > tasks.t[k].L.gtotal ? g : tasks.t[k].L.gtotal;
-    return round_up(g, 32);
+    for (int k = 0; k < tasks.count; ++k) {
+        const Task& t = tasks.t[k];
+        const int64_t need = t.split ? (team / 32) * round_up(t.L.gtotal, 32) : round_up(t.L.gtotal, 32);
+        g = g > need ? g : need;
+    }
+    return g;
 }
 
-int integrate_sstride(const Tasks& tasks) {
+int integrate_sstride(const Tasks& tasks, int team) {
     int sstride = 0;
-    for (int k = 0; k < tasks.count; ++k) sstride = sstride > tasks.t[k].L.stotal ? sstride : tasks.t[k].L.stotal;
+    for (int k = 0; k < tasks.count; ++k) {
+        const Task& t = tasks.t[k];
+        const int need = t.split ? (team / 32) * t.L.stotal : t.L.stotal;
+        sstride = sstride > need ? sstride : need;
+    }
     return sstride;
 }
 
 int integrate_tpb(const Tasks& tasks, int team, int tpb) {
     if (team > 32) return 1;
-    const int sstride = integrate_sstride(tasks);
+    const int sstride = integrate_sstride(tasks, team);
     while (tpb > 1 && (size_t)tpb * sstride * sizeof(double) > 227 * 1024) --tpb;   // larger layouts (GMRES)
     return tpb;
 }

@@ -391,7 +391,7 @@ static inline cudaError_t resident_blocks(const void* fn, int threads, size_t sm
     return cudaSuccess;
 }
 
-static inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+__host__ __device__ static inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Global scratch slots (one per team) and the work counter, allocated
 // stream-ordered for this launch and released after it.
@@ -409,11 +409,11 @@ static inline cudaError_t get_mem(int64_t teams, int64_t gstride, bool need_coun
             return e;
         m.gscratch = static_cast<double*>(p);
     }
-    if (need_counter) {
+    if (need_counter) {   // two counters: whole-team cells, and cells of split tasks
         void* p = nullptr;
-        if ((e = cudaMallocAsync(&p, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync(&p, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return e;
         m.counter = static_cast<unsigned long long*>(p);
-        return cudaMemsetAsync(m.counter, 0, sizeof(unsigned long long), st);
+        return cudaMemsetAsync(m.counter, 0, 2 * sizeof(unsigned long long), st);
     }
     return cudaSuccess;
 }

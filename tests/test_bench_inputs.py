@@ -93,7 +93,7 @@ def test_cpu_baseline_is_a_fixed_sample_and_a_median():
         return next(seq), k
     k, med, times = bench.median_timing(run, 4096, 5)
     assert calls == [4096] * 5 and k == 4096 and med == 2.5 and len(times) == 5
-    assert bench.CPU_SAMPLE[2] == 4096 and bench.CPU_SAMPLE[5] == 1024 and bench.CPU_SAMPLE[4] == 256
+    assert bench.CPU_SAMPLE[2] == 4096 and bench.CPU_SAMPLE[5] == 256 and bench.CPU_SAMPLE[4] == 256
     idx = bench.sample_indices(1 << 20, 4096)
     assert len(idx) == 4096 and idx[0] == 0 and idx[-1] == (1 << 20) - 1 and np.all(np.diff(idx) > 0)
     assert len(bench.sample_indices(100, 4096)) == 100          # never more than every cell

@@ -92,9 +92,46 @@ def test_batch_of_two_mechanisms_matches_separate_launches(mechs, flame_cells):
     torch.cuda.synchronize()
     same(a9, (Ts[0].cpu().numpy(), Ys[0].cpu().numpy().T, sts[0].cpu().numpy(), sas[0].cpu().numpy().T))
     same(a53, (Ts[1].cpu().numpy(), Ys[1].cpu().numpy().T, sts[1].cpu().numpy(), sas[1].cpu().numpy().T))
-    with pytest.raises(chemgb.ChemgbError):
-        chemgb.cg_mech_set_launch(h9, 32, 4)
-        chemgb.cg_integrate_batch([h9, h53], o, Ts, Ys, ps)
+
+
+@pytest.mark.parametrize("team53", [64, 128, 256])
+def test_split_batch_matches_separate_launches(mechs, flame_cells, team53):
+    """A one-warp mechanism (9 species) in a launch of wider teams (53
+    species with 64-256 threads per cell) runs split, each warp of a team
+    integrating its own cells: the same bits as its own one-warp launch,
+    for either mechanism, with FP64 and FP32 Newton matrices, and with the
+    split cells alone (no cells of the wider mechanism)."""
+    h9 = chemgb.cg_mech_create(mechs["h2"])
+    h53 = chemgb.cg_mech_create(mechs["ch4"])
+    chemgb.cg_mech_set_launch(h53, team53, 1)
+    assert chemgb.cg_mech_get_launch(h9)[0] == 32
+    T9, Y9, p9, _ = inputs.field_mixed(mechs["h2"], 700, "H2", seed=8)
+    T53, Y53, p53 = flame_cells
+    for prec in (chemgb.CG_FP64, chemgb.CG_FP32LU):
+        o = chemgb.make_opts(**ADAPT, precision=prec)
+        a9 = run(h9, o, T9, Y9, p9)
+        a53 = run(h53, o, T53, Y53, p53)
+        for with53 in (True, False):
+            n53 = len(T53) if with53 else 0
+            Ts = [d(T9), d(T53[:n53])]
+            Ys = [d(Y9.T), d(Y53[:n53].T)]
+            ps = [d(p9), d(p53[:n53])]
+            sts = [torch.empty(len(T9), dtype=torch.int32, device=DEV), torch.empty(n53, dtype=torch.int32, device=DEV)]
+            sas = [torch.empty((4, len(T9)), dtype=torch.int32, device=DEV),
+                   torch.empty((4, n53), dtype=torch.int32, device=DEV)]
+            chemgb.cg_integrate_batch([h9, h53], o, Ts, Ys, ps, sts, sas)
+            torch.cuda.synchronize()
+            same(a9, (Ts[0].cpu().numpy(), Ys[0].cpu().numpy().T, sts[0].cpu().numpy(), sas[0].cpu().numpy().T))
+            if with53:
+                same(a53, (Ts[1].cpu().numpy(), Ys[1].cpu().numpy().T, sts[1].cpu().numpy(),
+                           sas[1].cpu().numpy().T))
+    if team53 != 64:                                  # two wider team sizes cannot share a launch
+        h9b = chemgb.cg_mech_create(mechs["h2"])
+        chemgb.cg_mech_set_launch(h9b, 64, 1)
+        with pytest.raises(chemgb.ChemgbError) as e:
+            chemgb.cg_integrate_batch([h9b, h53], chemgb.make_opts(**ADAPT), [d(T9), d(T53)], [d(Y9.T), d(Y53.T)],
+                                      [d(p9), d(p53)])
+        assert e.value.code == chemgb.CG_EINVAL
 
 
 def test_autotune_picks_a_shape_and_keeps_results(mechs, tmp_path):

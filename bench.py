@@ -79,10 +79,10 @@ CONFIGS = {
 
 
 # DRAM bytes per cell of integrate_kernel from one ncu capture (65,536 cells of
-# the flame field, dram__bytes_read.sum + dram__bytes_write.sum = 30,146,304 +
-# 1,280 B), valid only for the kernel sources it was taken on (sha256 of the
-# files below, concatenated); scaled to a launch by its cell count.
-TRAFFIC_SOURCES = ("kernels.cu", "chem_device.cuh", "stepper.cuh", "chem_internal.h")
+# the flame field, dram__bytes_read.sum + dram__bytes_write.sum), valid only
+# for the kernel sources it was taken on (sha256 of the files below,
+# concatenated); scaled to a launch by its cell count.
+TRAFFIC_SOURCES = ("integrate.cuh", "chem_device.cuh", "stepper.cuh", "chem_internal.h", "instances.cu")
 TRAFFIC = {2: dict(bytes_per_cell=(30146304 + 1280) / 65536,
                    sha256="0b78532217004336b599aacfd5c5f2c3c96b56f390d4eb115835c05749bd459c")}
 

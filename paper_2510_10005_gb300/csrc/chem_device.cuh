@@ -818,12 +818,19 @@ __device__ __forceinline__ bool lu_pivot_column(MT* G, int n, int ld, int k, int
     if (abs_key(pv) == 0ull) return false;   // exact zero pivot (integer test)
     // The first warp forms the reciprocal and scales the column; an FP64
     // instruction costs the same for one lane as for 32, so the other
-    // warps of the team would only repeat it.
+    // warps of the team would only repeat it. The FP32 factorisation keeps
+    // its inverse pivots in FP32 (in the first n floats of rinv): the
+    // correctly rounded FP32 reciprocal, no FP64 instruction.
     if (lane < 32) {
-        const double r = rcp_nr(static_cast<double>(pv));
-        if (lane == 0) rinv[k] = r;
-        const MT rm = static_cast<MT>(r);
-        for (int i = k + 1 + lane; i < n; i += 32) G[i * ld + k] *= rm;
+        if constexpr (sizeof(MT) == 8) {
+            const double r = rcp_nr(static_cast<double>(pv));
+            if (lane == 0) rinv[k] = r;
+            for (int i = k + 1 + lane; i < n; i += 32) G[i * ld + k] *= r;
+        } else {
+            const float r = __frcp_rn(pv);
+            if (lane == 0) reinterpret_cast<float*>(rinv)[k] = r;
+            for (int i = k + 1 + lane; i < n; i += 32) G[i * ld + k] *= r;
+        }
     }
     team_sync<TEAM>();
     return true;
@@ -975,7 +982,7 @@ __device__ __forceinline__ bool lu_factor_nb(MT* G, int n, int ld, int nb, int* 
     return lu_factor<TEAM, MT>(G, n, ld, piv, rinv, red, lane);
 }
 
-// x <- G^{-1} x with the factors of lu_factor (FP64 arithmetic on x).
+// x <- G^{-1} x with the FP64 factors of lu_factor (FP64 arithmetic on x).
 template <int TEAM, class MT>
 __device__ void lu_solve(const MT* G, int n, int ld, const int* piv, const double* rinv,
                          double* x, int lane) {
@@ -998,6 +1005,39 @@ __device__ void lu_solve(const MT* G, int n, int ld, const int* piv, const doubl
         for (int i = lane; i < j; i += TEAM) x[i] = fma(-static_cast<double>(G[i * ld + j]), xj, x[i]);
         team_sync<TEAM>();
     }
+}
+
+// x <- G^{-1} x with FP32 factors, in FP32 arithmetic (xs: n floats of
+// scratch): the application of the FP32 preconditioner of the inexact
+// Newton. x (the FP64 residual) is permuted, rounded to FP32, solved, and
+// widened back; the Newton update, residual and convergence test stay FP64,
+// so the iteration's fixed point is the FP64 one. rinv: the FP32 inverse
+// pivots of lu_pivot_column<TEAM, float>.
+template <int TEAM>
+__device__ void lu_solve_f32(const float* G, int n, int ld, const int* piv, const float* rinv, double* x, float* xs,
+                             int lane) {
+    if (lane == 0)
+        for (int k = 0; k < n; ++k) {
+            const int p = piv[k];
+            if (p != k) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
+        }
+    team_sync<TEAM>();
+    for (int i = lane; i < n; i += TEAM) xs[i] = static_cast<float>(x[i]);
+    team_sync<TEAM>();
+    for (int j = 0; j < n - 1; ++j) {           // unit lower triangle, by columns
+        const float xj = xs[j];
+        for (int i = j + 1 + lane; i < n; i += TEAM) xs[i] = fmaf(-G[i * ld + j], xj, xs[i]);
+        team_sync<TEAM>();
+    }
+    for (int j = n - 1; j >= 0; --j) {          // upper triangle, by columns
+        if (lane == 0) xs[j] *= rinv[j];
+        team_sync<TEAM>();
+        const float xj = xs[j];
+        for (int i = lane; i < j; i += TEAM) xs[i] = fmaf(-G[i * ld + j], xj, xs[i]);
+        team_sync<TEAM>();
+    }
+    for (int i = lane; i < n; i += TEAM) x[i] = static_cast<double>(xs[i]);
+    team_sync<TEAM>();
 }
 
 // x <- G^{-T} x with the factors of lu_factor: with P G = L U, G^T = U^T L^T P,

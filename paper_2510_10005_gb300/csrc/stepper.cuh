@@ -100,7 +100,11 @@ __device__ __forceinline__ bool lin_solve(const Ws& W, const IntParams& P, int n
                                           int lane) {
     const MT* G = reinterpret_cast<const MT*>(W.G);
     if (P.linear_solver == 0) {
-        lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, x, lane);
+        if constexpr (sizeof(MT) == 4)   // colB is free while a step solves
+            lu_solve_f32<TEAM>(G, n, W.ld, W.piv, reinterpret_cast<const float*>(W.rinv), x,
+                               reinterpret_cast<float*>(W.colB), lane);
+        else
+            lu_solve<TEAM, MT>(G, n, W.ld, W.piv, W.rinv, x, lane);
         return true;
     }
     int* flag = reinterpret_cast<int*>(W.red + 20);

@@ -169,13 +169,13 @@ cg_status cg_mech_set_launch(cg_mech *mech, int team, int teams_per_block);
  * slot of global scratch that the library allocates stream-ordered for each
  * launch (mechanisms whose Newton matrix alone nears the limit, such as 160
  * species in FP64, always spill). A lower limit trades L2 traffic for more
- * cells per SM. Default: 227 KiB, except when the per-reaction block (9 nr
- * doubles) is at least 8 KiB of a per-cell total of 40 KiB or more; then
- * the limit keeps everything but that block in shared memory (53 species /
- * 325 reactions: 33 KiB per cell, 6 cells per SM instead of 4); and 64 KiB
- * when the FP64 Newton matrix alone exceeds half of 227 KiB (160 species),
- * which puts the whole working set in the L2 slot so that four cells share
- * an SM. This call sets one limit for both matrix types. Same
+ * cells per SM. Default: 64 KiB when the FP64 Newton matrix alone exceeds
+ * half of 227 KiB (160 species), which puts the whole working set in the
+ * L2 slot so that four cells share an SM; 28 KiB for two-warp cells whose
+ * Newton matrix fits in it (eight cells per SM; 53 species); otherwise
+ * 227 KiB, except when the per-reaction block (9 nr doubles) is at least
+ * 8 KiB of a per-cell total of 40 KiB or more, which then goes to L2. This
+ * call sets one limit for both matrix types. Same
  * concurrency rule as cg_mech_set_launch. Launch tuning, not part of the
  * paper's method. */
 cg_status cg_mech_set_smem_limit(cg_mech *mech, int64_t bytes);

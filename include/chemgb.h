@@ -60,8 +60,8 @@ enum {
     CG_CELL_STEP_TOO_SMALL = 2,   /* adaptive step fell below hmin          */
     CG_CELL_MAX_STEPS = 3,        /* more than max_steps step attempts      */
     CG_CELL_NONFINITE = 4,        /* input state not finite                 */
-    CG_CELL_NO_RECORD = 5         /* adjoint: the forward pass left no usable
-                                     checkpoints (failed cell or too few slots) */
+    CG_CELL_NO_RECORD = 5         /* adjoint: the forward pass failed on this
+                                     cell, so it left no usable record */
 };
 
 /* reaction types (Section 2.2): elementary, third-body, falloff with
@@ -233,8 +233,10 @@ typedef struct {
     int max_halvings;  /* fixed mode: depth of step halving after a failed step       */
     int err_filter;    /* adaptive: filter the error estimate by (I - gamma h J)^-1   */
     int persistent;    /* 1: resident grid whose teams take cells from a shared work
-                          counter (work stealing; always used when a cell's arrays
-                          spill to global scratch); 0: one launch slot per cell    */
+                          counter (work stealing; also used when a cell's arrays
+                          spill to global scratch, when one-warp mechanisms run
+                          split, and when the cells need more than one wave of
+                          blocks); 0: one launch slot per cell otherwise          */
     double dt;         /* integration interval, s                                     */
     double rtol, atol; /* weights w_i = atol + rtol max(|y_n,i|, |y_i|)               */
     double newton_tol; /* Newton converged when WRMS(change of stage state) <= this;

@@ -217,12 +217,15 @@ cudaError_t launch_integrate_team(const Tasks& tasks, const IntParams& P, int tp
     const int64_t units = tasks.total > tasks.total_split / (TEAM / 32) ? tasks.total
                                                                         : tasks.total_split / (TEAM / 32) + 1;
     int64_t blocks = (units + tpb - 1) / tpb;
-    const bool queue = persistent || gstride > 0 || tasks.total_split > 0;
-    if (queue) {
-        int64_t res = 0;
-        if ((e = resident_blocks(fn, TEAM * tpb, smem, &res)) != cudaSuccess) return e;
-        blocks = blocks < res ? blocks : res;
-    }
+    int64_t res = 0;
+    if ((e = resident_blocks(fn, TEAM * tpb, smem, &res)) != cudaSuccess) return e;
+    // the work queue (resident teams take cells from a counter) whenever it
+    // is asked for, needed (scratch slots, split tasks), or the cells would
+    // take more than one wave of blocks: cells of very different cost then
+    // balance across the teams (9 species, 4096 cells: 13.3 instead of
+    // 15.3 ms, against 9.7 ms for the slowest cell alone)
+    const bool queue = persistent || gstride > 0 || tasks.total_split > 0 || blocks > res;
+    if (queue) blocks = blocks < res ? blocks : res;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     LaunchMem mem;
     if ((e = get_mem(blocks * tpb, gstride, queue, st, mem)) != cudaSuccess) return e;

@@ -221,28 +221,35 @@ def big_cells(big):
 @pytest.mark.parametrize("precision", [chemgb.CG_FP64, chemgb.CG_FP32LU])
 def test_big_mechanism_backward_euler(big, big_cells, precision):
     """Fixed-step backward Euler, Newton iterated until its change is below
-    1e-10 of the state: the FP64 Newton matrix lands on the oracle's root to
-    1e-10; the FP32 one (an inexact Newton whose residual stays FP64) to
-    1e-8. The step is 1e-7 s: at 1e-6 s the FP32 factorisation of the worst
-    conditioned cells contracts too slowly for 20 iterations and those cells
-    halve their step, which the FP64 Newton does not (another valid step
-    sequence, compared by the adaptive test below), with at most 40 Newton
-    iterations."""
+    1e-10 of the state (at most 20 iterations): the FP64 Newton matrix lands
+    on the oracle's root to 1e-10; the FP32 one (an inexact Newton whose
+    residual stays FP64, its preconditioner applied in FP32) to 1e-8, with
+    1e-7 s steps. On the worst conditioned cells the FP32 preconditioner may
+    not contract at the full step, and the integrator's fallback halves it:
+    such a cell (at most 5 %) must show exactly one failed attempt and two
+    half steps, and must agree to 1e-8 with the oracle taking those two half
+    steps."""
     m, r, h = big
     T, Y, p = big_cells
-    # the FP32 preconditioner contracts more slowly than the FP64 Newton's
-    # quadratic convergence: 40 iterations (the oracle needs about 4)
-    o = dict(BE, dt=1e-6) if precision == chemgb.CG_FP64 else dict(BE, dt=1e-7, max_newton=40)
+    o = dict(BE, dt=1e-6 if precision == chemgb.CG_FP64 else 1e-7)
     To, Yo, so, sto = r.integrate(T, Y, p, o, nthreads=8)
     Tg, Yg, sg, stg = run(h, chemgb.make_opts(**o, precision=precision), T, Y, p)
     np.testing.assert_array_equal(sg, so)      # a cell that exhausts its halvings fails on both sides
     ok = so == 0
     assert ok.mean() > 0.9
-    np.testing.assert_array_equal(stg[ok, :2], sto[ok, :2])      # the same halving path everywhere
+    same = ok & np.all(stg[:, :2] == sto[:, :2], axis=1)
     if precision == chemgb.CG_FP64:
+        np.testing.assert_array_equal(same, ok)                  # the same halving path everywhere
         check_fixed("big_160sp_be_fp64", Tg[ok], Yg[ok], To[ok], Yo[ok], 1e-10, 1e-22)
-    else:
-        check_fixed("big_160sp_be_fp32lu", Tg[ok], Yg[ok], To[ok], Yo[ok], 1e-8, 1e-18)
+        return
+    check_fixed("big_160sp_be_fp32lu", Tg[same], Yg[same], To[same], Yo[same], 1e-8, 1e-18)
+    other = ok & ~same
+    assert other.mean() <= 0.05
+    if other.any():
+        np.testing.assert_array_equal(stg[other, :2], np.tile([2, 1], (int(other.sum()), 1)))
+        To2, Yo2, so2, sto2 = r.integrate(T[other], Y[other], p[other], dict(o, nsub=2), nthreads=8)
+        assert np.all(so2 == 0) and np.all(sto2[:, :2] == [2, 0])
+        check_fixed("big_160sp_be_fp32lu_halved", Tg[other], Yg[other], To2, Yo2, 1e-8, 1e-18)
 
 
 @pytest.mark.parametrize("kind,team,panels", [("c7", 256, (16, 5, 64)), ("c7", 64, (16,)), ("ch4", 64, (8, 16)),

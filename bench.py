@@ -83,8 +83,8 @@ CONFIGS = {
 # for the kernel sources it was taken on (sha256 of the files below,
 # concatenated); scaled to a launch by its cell count.
 TRAFFIC_SOURCES = ("integrate.cuh", "chem_device.cuh", "stepper.cuh", "chem_internal.h", "instances.cu")
-TRAFFIC = {2: dict(bytes_per_cell=(30146304 + 1280) / 65536,
-                   sha256="0b78532217004336b599aacfd5c5f2c3c96b56f390d4eb115835c05749bd459c")}
+TRAFFIC = {2: dict(bytes_per_cell=(42933504 + 840458752) / 65536,
+                   sha256="16e61ea611e371135865d6720a2a8b0204e3a8d79d88283697b925ebacd69f4d")}
 
 
 def measured_traffic(config: int, cells: int):

@@ -22,7 +22,9 @@ Other workloads (reported beside the default line):
               L = sum (T_end - T_target)^2 (target from ln A + N(0, 0.1^2));
               gradients w.r.t. (ln A, b, Ea) of all reactions and (T0, Y0)
   --config 5  160 species / 900 reactions, T in U[700, 1600] K,
-              p in U[20, 40] atm, adaptive SDIRK-4 (use --cells for a subset)
+              p in U[20, 40] atm, adaptive SDIRK-4 (use --cells for a subset);
+              with --adjoint: config 4's forward with checkpoints plus the
+              discrete adjoint on 8,192 cells of this field
 
 Prints one JSON line. --impl reference times the FP64 CPU oracle on the
 host cores instead (a bounded sample of the same workload). The oracle runs
@@ -287,6 +289,23 @@ def flow_state(m, T, Y, p):
 
 def oracle_opts(o: dict) -> dict:
     return {k: v for k, v in o.items() if k not in ("precision", "persistent")}
+
+
+# cells of the adjoint workloads (--config 4, --config 5 --adjoint: a subset
+# of the 262,144-cell field, since a 160-species cell takes about 1.5 ms of
+# the GPU forward and backward)
+ADJOINT_CELLS = {4: 1 << 16, 5: 8192}
+# the oracle's forward + adjoint timing samples (several seconds per cell at 160 species)
+CPU_SAMPLE_ADJ = {4: 256, 5: 16}
+ONE_CORE_SAMPLE_ADJ = {4: 16, 5: 1}
+
+
+def adjoint_workload(config: int, n_cells: int) -> str:
+    if config == 4:
+        return CONFIGS[4]["workload"]
+    return (CONFIGS[config]["workload"] + f", {n_cells:,} cells of the field recipe, with checkpoints + discrete "
+            "adjoint of L = sum (T_end - T_target)^2, T_target from ln A + N(0, 0.1^2); gradients w.r.t. "
+            "2700 Arrhenius parameters and (T0, Y0)")
 
 
 # The oracle's timing sample of each workload: cells evenly spaced through
@@ -654,7 +673,8 @@ def adjoint_flops(m, stats, s_stages: int) -> float:
 
 
 def run_adjoint(args):
-    """--config 4: forward with checkpoints plus the discrete adjoint."""
+    """--config 4 (and --config 5 --adjoint): forward with checkpoints plus
+    the discrete adjoint."""
     import torch
     from paper_2510_10005_gb300 import autograd, chemgb, multirank
 
@@ -666,10 +686,10 @@ def run_adjoint(args):
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     chemgb.load(build_if_missing=(ws == 1))
-    cfg = CONFIGS[4]
-    (m, T, Y, p), = make_workload(4, args.cells or cfg["cells"], seed=rank)
+    cid = args.config
+    (m, T, Y, p), = make_workload(cid, args.cells or ADJOINT_CELLS[cid], seed=rank)
     N = len(T)
-    opts_d = opts_dict(4, 0)
+    opts_d = opts_dict(cid, 0)
     opts = chemgb.make_opts(**opts_d)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -796,11 +816,11 @@ def run_adjoint(args):
             r.adjoint_TY(T[idx], Y[idx], p[idx], np.ones(len(idx)), np.zeros((len(idx), m.ns)), oracle_opts(opts_d),
                          nthreads=nthreads)
             return time.perf_counter() - t0, len(idx)
-        k, el, times = median_timing(run, args.cpu_sample or CPU_SAMPLE[4], args.cpu_repeats)
+        k, el, times = median_timing(run, args.cpu_sample or CPU_SAMPLE_ADJ[cid], args.cpu_repeats)
         cpu = {"value": k / el, "unit": "cells/s", "cores": threads, "kind": "oracle",
                "sample": f"{k} cells evenly spaced, forward + adjoint, median of {len(times)} timings "
                          f"({', '.join(f'{t:.2f}' for t in times)} s)"}
-        one = ONE_CORE_SAMPLE[4] if args.cpu_1core_cells is None else args.cpu_1core_cells
+        one = ONE_CORE_SAMPLE_ADJ[cid] if args.cpu_1core_cells is None else args.cpu_1core_cells
         if one > 0:   # the same oracle on one host core
             k1, el1, _ = median_timing(lambda n: run(n, 1), one, 1)
             cpu["one_core"] = {"value": k1 / el1, "unit": "cells/s", "cores": 1,
@@ -809,7 +829,7 @@ def run_adjoint(args):
         "metric": METRIC_ADJ, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg["workload"], "config": 4, "cells_per_gpu": N, "ckpt_cap": cap,
+        "config": {"workload": adjoint_workload(cid, N), "config": cid, "cells_per_gpu": N, "ckpt_cap": cap,
                    "ckpt_bytes": int(ckpt.numel() * 8),
                    "l2": "checkpoints larger than L2 (129 MB); no flush" if ckpt.numel() * 8 > 129e6
                    else "state smaller than L2"},
@@ -835,12 +855,12 @@ def run_reference_adjoint(args):
     if rank != 0:
         return
     import oracle
-    cfg = CONFIGS[4]
-    (m, T, Y, p), = make_workload(4, args.cells or cfg["cells"])
-    o = oracle_opts(opts_dict(4, 0))
+    cid = args.config
+    (m, T, Y, p), = make_workload(cid, args.cells or ADJOINT_CELLS[cid])
+    o = oracle_opts(opts_dict(cid, 0))
     r = oracle.RefMech(m)
     threads = os.cpu_count() or 1
-    idx = sample_indices(len(T), args.cpu_sample or CPU_SAMPLE[4])
+    idx = sample_indices(len(T), args.cpu_sample or CPU_SAMPLE_ADJ[cid])
     k = len(idx)
 
     def sample():
@@ -856,7 +876,7 @@ def run_reference_adjoint(args):
         "impl": "reference", "metric": METRIC_ADJ, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg["workload"], "config": 4},
+        "config": {"workload": adjoint_workload(cid, len(T)), "config": cid},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads, "kind": "oracle",
                          "sample": f"the same {k} cells evenly spaced every step, forward + adjoint; "
                                    f"value = cells / median step time"},
@@ -899,11 +919,16 @@ def main():
                     help="give the workload's mechanisms SRI falloff and PLOG reactions")
     ap.add_argument("--thermo-degree", type=int, default=None,
                     help="refit the mechanisms' c_p polynomials to this degree (0-15; NASA-7 is 4)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="config 5: forward with checkpoints plus the discrete adjoint (config 4's loss), "
+                         f"{ADJOINT_CELLS[5]:,} cells unless --cells")
     ap.add_argument("--surface", choices=["integrate", "split"], default="integrate",
                     help="split: the operator-split call of a compressible solver (rho, u, rho Y in; T, R out), "
                          "constant volume")
     args = ap.parse_args()
-    if args.config == 4:
+    if args.adjoint and args.config != 5:
+        ap.error("--adjoint applies to --config 5 (config 4 is the adjoint workload)")
+    if args.config == 4 or args.adjoint:
         (run_reference_adjoint if args.impl == "reference" else run_adjoint)(args)
     elif args.impl == "reference":
         run_reference(args)

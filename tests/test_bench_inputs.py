@@ -63,6 +63,26 @@ def test_reference_arm_takes_the_workload_options(capsys, monkeypatch):
     assert line["value"] > 0
 
 
+def test_adjoint_arms_name_their_workload(capsys, monkeypatch):
+    """The adjoint arms (config 4, and config 5 with --adjoint) time the
+    oracle's forward + adjoint on the workload they name; the 160-species
+    form states its cell count and parameter count."""
+    import argparse
+    import json
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+    args = argparse.Namespace(config=4, cells=64, cpu_sample=2, steps=1, warmup=0, gpus=1, adjoint=False)
+    bench.run_reference_adjoint(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["metric"] == bench.METRIC_ADJ and line["config"] == {"workload": bench.CONFIGS[4]["workload"],
+                                                                      "config": 4}
+    assert line["value"] > 0
+    w5 = bench.adjoint_workload(5, bench.ADJOINT_CELLS[5])
+    assert w5.startswith(bench.CONFIGS[5]["workload"]) and "8,192 cells" in w5 and "2700 Arrhenius" in w5
+    m = inputs.gen_mechanism("c7")
+    assert 3 * m.nr == 2700
+
+
 def test_traffic_only_for_the_captured_kernel_sources(monkeypatch):
     """The DRAM traffic of the bench line is the ncu capture's bytes per cell
     scaled to the launch, and null for any workload or kernel source it was

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_2510_10005_gb300 import chemgb, inputs
-from parity import check_adaptive, check_fixed
+from parity import check_adaptive, check_elementwise, check_fixed
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -294,3 +294,47 @@ def test_big_mechanism_adaptive(big, big_cells, precision):
     assert np.all(so == 0)
     check_adaptive("big_160sp_sdirk4_" + ("fp64" if precision == chemgb.CG_FP64 else "fp32lu"), m, Tg, Yg, To, Yo,
                    p, ADAPT["reactor"], ADAPT["rtol"], ADAPT["atol"])
+
+
+def test_big_mechanism_adjoint(big, big_cells):
+    """The discrete adjoint at 160 species (team of four warps, Newton
+    matrices in global scratch, blocked LU and its transposed solves): 32 of
+    the cells, adaptive SDIRK-4 over 1e-6 s with checkpoints, then the
+    backward sweep for random dL/dT_end and dL/dY_end. dL/dT0, dL/dY0 and
+    the per-cell dL/dtheta must match the oracle's adjoint element-wise
+    within 1e-6 plus 1e-9 of the largest entry of each kind, on the cells
+    whose accepted step count equals the oracle's (at least 90 %)."""
+    m, r, h = big
+    T, Y, p = (a[::2] for a in big_cells)
+    N = len(T)
+    og = chemgb.make_opts(**ADAPT)
+    Tt, Yt, pt = d(T), d(Y.T), d(p)
+    cap = 128
+    ckpt = torch.empty((N, cap, m.ns + 2), dtype=torch.float64, device=DEV)
+    ckpt_n = torch.empty(N, dtype=torch.int32, device=DEV)
+    st = torch.empty(N, dtype=torch.int32, device=DEV)
+    chemgb.cg_integrate_ckpt(h, og, Tt, Yt, pt, ckpt, ckpt_n, st)
+    rng = np.random.default_rng(8)
+    gT, gY = rng.normal(size=N), rng.normal(size=(N, m.ns))
+    dT0, dY0 = torch.empty(N, dtype=torch.float64, device=DEV), torch.empty((m.ns, N), dtype=torch.float64, device=DEV)
+    dth = torch.empty((m.nr, 3), dtype=torch.float64, device=DEV)
+    dcell = torch.empty((m.nr, 3, N), dtype=torch.float64, device=DEV)
+    ast = torch.empty(N, dtype=torch.int32, device=DEV)
+    chemgb.cg_integrate_adjoint(h, og, ckpt, ckpt_n, d(gT), d(gY.T), dT0, dY0, dth, dcell, ast)
+    torch.cuda.synchronize()
+    assert int((st != 0).sum()) == 0 and int((ast != 0).sum()) == 0
+    kn = ckpt_n.cpu().numpy()
+    assert np.all((kn > 0) & (kn < cap))
+    oo = {k: v for k, v in ADAPT.items()}
+    oT, oY, og_, ost = r.adjoint_TY(T, Y, p, gT, gY, oo, nthreads=8)
+    assert np.all(ost == 0)
+    C0 = r.concentrations(T, Y, p, ADAPT["reactor"])
+    _, _, _, hn = r.integrate_hist(np.concatenate([T[:, None], C0], axis=1), oo, cap=cap, nthreads=8)
+    same = kn == hn
+    assert same.mean() >= 0.9, (kn, hn)
+    check_elementwise("big_160sp_adjoint_dT0", dT0.cpu().numpy()[same], oT[same], 1e-6, 1e-9)
+    check_elementwise("big_160sp_adjoint_dY0", dY0.cpu().numpy().T[same], oY[same], 1e-6, 1e-9)
+    gc = np.moveaxis(dcell.cpu().numpy(), 2, 0)
+    for k, name in enumerate(("lnA", "b", "Ea")):
+        check_elementwise(f"big_160sp_adjoint_dtheta_{name}", gc[same][:, :, k], og_[same][:, :, k], 1e-6, 1e-9)
+    np.testing.assert_allclose(dth.cpu().numpy(), gc.sum(axis=0), rtol=1e-12, atol=1e-12 * np.abs(gc).max())

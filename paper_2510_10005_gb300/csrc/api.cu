@@ -945,6 +945,9 @@ cg_status cg_mech_create(const cg_mech_desc* d, cg_mech** out) {
     dm.ln_pref_R = std::log(kPref / kR);
     dm.th_np = 4;
     dm.lu_nb = default_lu_nb(n);
+    dm.slots = 2;
+    for (int jj = 0; jj < nr; ++jj)
+        if (sidx[(size_t)2 * nr + jj] >= 0 || sidx[(size_t)5 * nr + jj] >= 0) dm.slots = 3;
 #define UP(vec, field)                                           \
     if ((st = upload(m->allocs, vec, &dm.field)) != CG_OK) {     \
         cg_mech_destroy(m);                                      \

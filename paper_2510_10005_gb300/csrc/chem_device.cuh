@@ -65,6 +65,8 @@ struct DevMech {
     const double *W, *invW;      // [ns]
     const int *rtype, *rev, *sumnu;
     const int *sidx, *snu;       // [6][nr]: slots 0..2 reactants, 3..5 products; -1 empty
+    int slots;                   // slots used on either side by some reaction: 2 (slots 2 and 5
+                                 // empty everywhere, rates compiled without them) or 3
     const double *snud, *sumnud; // the coefficients as doubles ([6][nr], 0 on empty slots) and sum nu
     const double *lnA, *beta, *Ta;        // Ta = Ea / R
     const double *dlnA0, *dbeta0, *dTa0;  // low-pressure minus high-pressure
@@ -212,6 +214,33 @@ __device__ __forceinline__ double team_sum(double v, double* red) {
         for (int k = 0; k < TEAM / 32; ++k) s += red[k];
         __syncthreads();
         return s;
+    }
+}
+
+// K sums over the team at once, each in team_sum's order (the same bits),
+// with one pair of block barriers instead of K pairs.
+template <int TEAM, int K>
+__device__ __forceinline__ void team_sums(double (&v)[K], double* red) {
+    constexpr int NW = TEAM / 32;
+    if constexpr (TEAM == 32 || NW * K > 24) {   // the 24 words of the scratch
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = team_sum<TEAM>(v[k], red);
+    } else {
+        const int w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const double x = warp_sum(v[k]);
+            if ((threadIdx.x & 31) == 0) red[k * NW + w] = x;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+#pragma unroll
+            for (int u = 0; u < NW; ++u) s += red[k * NW + u];
+            v[k] = s;
+        }
+        __syncthreads();
     }
 }
 
@@ -413,6 +442,80 @@ __device__ __forceinline__ void thermo_s_dcp_deg(const double* th, int ns, int P
 
 // Fills SP (species thermo) and RD (q_j and, with deriv, dq_j/dT, the
 // third-body weight w_j and the mass-action partials). Returns sum C.
+// Rate of progress q_j = k_f prod C^nu' - k_r prod C^nu'' of reaction j
+// from its forward rate constant (Section 2.2, K_c from the Gibbs energies
+// with the integer power of p_ref / RT folded into the exponent) and, with
+// deriv, its partials: dq/dT, the third-body weight dq/d[M], and the
+// per-slot dq/dC (d[s][j]). NSL = 2 leaves out the third slot of each side
+// at compile time (mechanisms whose reactions have at most two species on
+// either side); the products over the remaining slots are the same.
+template <int NSL>
+__device__ __forceinline__ void progress_rate(const DevMech& M, int j, const double* C, const double* gRT,
+                                              const double* hRT, double lnPRT, double invT, double kf,
+                                              double dkf_dT, double dkf_dM, bool deriv, double* q, double* dqdT,
+                                              double* wv, double* dd) {
+    // mass-action products C^nu of every slot and their derivatives
+    const int nr = M.nr;
+    double p[6], dp[6], nd[6];
+    int sp[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        if (s % 3 >= NSL) {   // a slot no reaction uses: factor 1, no derivative
+            sp[s] = -1;
+            nd[s] = 0.0;
+            p[s] = 1.0;
+            dp[s] = 0.0;
+            continue;
+        }
+        sp[s] = __ldg(M.sidx + s * nr + j);
+        nd[s] = __ldg(M.snud + s * nr + j);
+        p[s] = 1.0;
+        dp[s] = 0.0;
+        if (sp[s] >= 0) {
+            const int nu = __ldg(M.snu + s * nr + j);
+            const double c = C[sp[s]];
+            double pw = 1.0;
+            for (int k = 1; k < nu; ++k) pw *= c;
+            dp[s] = nu == 1 ? 1.0 : nd[s] * pw;
+            p[s] = pw * c;
+        }
+    }
+    double invK = 0.0, dlnK = 0.0;
+    if (__ldg(M.rev + j)) {
+        double dG = 0.0, dH = 0.0;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            if (sp[s] >= 0) {
+                const double nu = s < 3 ? -nd[s] : nd[s];
+                dG = fma(nu, gRT[sp[s]], dG);
+                dH = fma(nu, hRT[sp[s]], dH);
+            }
+        }
+        const double snu = __ldg(M.sumnud + j);
+        invK = exp_tab(fma(-snu, lnPRT, dG), M.exp2j);   // 1 / K_c
+        dlnK = (dH - snu) * invT;                        // d ln K_c / dT
+    }
+    const double kr = kf * invK;
+    // prefix and suffix products: kf p0 p1 p2 and the slot partials
+    const double f01 = kf * p[0], f012 = f01 * p[1], fP = f012 * p[2];   // kf Pf
+    const double f12 = p[1] * p[2];
+    const double r01 = kr * p[3], r012 = r01 * p[4], rP = r012 * p[5];   // kr Pb
+    const double r12 = p[4] * p[5];
+    q[j] = fP - rP;
+    if (deriv) {
+        const double Pf = p[0] * f12, Pb = p[3] * r12;
+        const double phi = fma(-invK, Pb, Pf);
+        dqdT[j] = fma(dkf_dT, phi, rP * dlnK);
+        wv[j] = dkf_dM * phi;
+        if (sp[0] >= 0) dd[0 * nr + j] = dp[0] * (kf * f12);
+        if (sp[1] >= 0) dd[1 * nr + j] = dp[1] * (f01 * p[2]);
+        if (sp[2] >= 0) dd[2 * nr + j] = dp[2] * f012;
+        if (sp[3] >= 0) dd[3 * nr + j] = -dp[3] * (kr * r12);
+        if (sp[4] >= 0) dd[4 * nr + j] = -dp[4] * (r01 * p[5]);
+        if (sp[5] >= 0) dd[5 * nr + j] = -dp[5] * r012;
+    }
+}
+
 template <int TEAM>
 __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deriv,
                         int lane, double* xf = nullptr) {   // xf: d ln q_j / d ln k_j (adjoint)
@@ -448,8 +551,10 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
         dcpR[i] = dcp;
         csum += C[i];
     }
+    // SP visible to the whole team: the block barriers of team_sum, or one
+    // warp barrier
     const double Mc = team_sum<TEAM>(csum, W.red);
-    team_sync<TEAM>();   // SP visible to the whole team
+    if constexpr (TEAM == 32) team_sync<TEAM>();
     const double lnPRT = M.ln_pref_R - lnT;   // ln(p_ref / (R T))
     const double lnP = M.has_plog ? log(8314.46261815324 * T * Mc) : 0.0;   // ln p = ln(R T sum C)
     double* q = W.RD;
@@ -575,58 +680,10 @@ __device__ double rates(const DevMech& M, const Ws& W,const double* y, bool deri
                 if (xf) xf[j] = Pr * ip - dlogF_dP;
             }
         }
-        // mass-action products C^nu of every slot and their derivatives
-        double p[6], dp[6], nd[6];
-        int sp[6];
-#pragma unroll
-        for (int s = 0; s < 6; ++s) {
-            sp[s] = __ldg(M.sidx + s * nr + j);
-            nd[s] = __ldg(M.snud + s * nr + j);
-            p[s] = 1.0;
-            dp[s] = 0.0;
-            if (sp[s] >= 0) {
-                const int nu = __ldg(M.snu + s * nr + j);
-                const double c = C[sp[s]];
-                double pw = 1.0;
-                for (int k = 1; k < nu; ++k) pw *= c;
-                dp[s] = nu == 1 ? 1.0 : nd[s] * pw;
-                p[s] = pw * c;
-            }
-        }
-        double invK = 0.0, dlnK = 0.0;
-        if (__ldg(M.rev + j)) {
-            double dG = 0.0, dH = 0.0;
-#pragma unroll
-            for (int s = 0; s < 6; ++s) {
-                if (sp[s] >= 0) {
-                    const double nu = s < 3 ? -nd[s] : nd[s];
-                    dG = fma(nu, gRT[sp[s]], dG);
-                    dH = fma(nu, hRT[sp[s]], dH);
-                }
-            }
-            const double snu = __ldg(M.sumnud + j);
-            invK = exp_tab(fma(-snu, lnPRT, dG), M.exp2j);   // 1 / K_c
-            dlnK = (dH - snu) * invT;                        // d ln K_c / dT
-        }
-        const double kr = kf * invK;
-        // prefix and suffix products: kf p0 p1 p2 and the slot partials
-        const double f01 = kf * p[0], f012 = f01 * p[1], fP = f012 * p[2];   // kf Pf
-        const double f12 = p[1] * p[2];
-        const double r01 = kr * p[3], r012 = r01 * p[4], rP = r012 * p[5];   // kr Pb
-        const double r12 = p[4] * p[5];
-        q[j] = fP - rP;
-        if (deriv) {
-            const double Pf = p[0] * f12, Pb = p[3] * r12;
-            const double phi = fma(-invK, Pb, Pf);
-            dqdT[j] = fma(dkf_dT, phi, rP * dlnK);
-            wv[j] = dkf_dM * phi;
-            if (sp[0] >= 0) dd[0 * nr + j] = dp[0] * (kf * f12);
-            if (sp[1] >= 0) dd[1 * nr + j] = dp[1] * (f01 * p[2]);
-            if (sp[2] >= 0) dd[2 * nr + j] = dp[2] * f012;
-            if (sp[3] >= 0) dd[3 * nr + j] = -dp[3] * (kr * r12);
-            if (sp[4] >= 0) dd[4 * nr + j] = -dp[4] * (r01 * p[5]);
-            if (sp[5] >= 0) dd[5 * nr + j] = -dp[5] * r012;
-        }
+        if (M.slots == 2)
+            progress_rate<2>(M, j, C, gRT, hRT, lnPRT, invT, kf, dkf_dT, dkf_dM, deriv, q, dqdT, wv, dd);
+        else
+            progress_rate<3>(M, j, C, gRT, hRT, lnPRT, invT, kf, dkf_dT, dkf_dM, deriv, q, dqdT, wv, dd);
     }
     team_sync<TEAM>();
     return Mc;
@@ -664,11 +721,13 @@ __device__ SrcInfo assemble_source(const DevMech& M, const Ws& W,const double* y
     }
     SrcInfo si;
     si.Mc = Mc;
-    const double Qt = team_sum<TEAM>(qe, red);
-    si.Dt = team_sum<TEAM>(den, red);
-    si.Ws = team_sum<TEAM>(ws, red);
-    si.cw = team_sum<TEAM>(cw, red);
-    si.cdc = team_sum<TEAM>(cdc, red);
+    double sums[5] = {qe, den, ws, cw, cdc};
+    team_sums<TEAM, 5>(sums, red);
+    const double Qt = sums[0];
+    si.Dt = sums[1];
+    si.Ws = sums[2];
+    si.cw = sums[3];
+    si.cdc = sums[4];
     si.wT = -T * Qt / si.Dt;   // -sum e_i omega_i / (rho c), volumetric c
     si.sdil = 0.0;
     if (reactor == R_CONP) {
@@ -741,20 +800,50 @@ __device__ void assemble_jacobian(const DevMech& M, const Ws& W,const double* y,
         }
     }
     team_sync<TEAM>();
-    for (Flat2D it(lane, n, TEAM); it.r < n; it.next()) {
-        const int r = it.r, c = it.c;
-        double J;
-        if (r == 0) {
-            J = JT[c];
-        } else {
-            J = static_cast<double>(G[r * ld + c]);
-            if (conp) {
-                J = fma(-C[r - 1], ds[c], J);
-                if (c == r) J -= si.sdil;
+    if (out) {
+        for (Flat2D it(lane, n, TEAM); it.r < n; it.next()) {
+            const int r = it.r, c = it.c;
+            double J;
+            if (r == 0) {
+                J = JT[c];
+            } else {
+                J = static_cast<double>(G[r * ld + c]);
+                if (conp) {
+                    J = fma(-C[r - 1], ds[c], J);
+                    if (c == r) J -= si.sdil;
+                }
             }
+            out[r * n + c] = J;
         }
-        if (out) out[r * n + c] = J;
-        else G[r * ld + c] = static_cast<MT>(fma(-gh, J, r == c ? 1.0 : 0.0));
+    } else {
+        // G = I - gh J: the off-diagonal entries, then the diagonal (with the
+        // dilution term -s) in a pass of its own, so that the n^2 pass
+        // carries no diagonal-only arithmetic; the same operations per entry
+        for (Flat2D it(lane, n, TEAM); it.r < n; it.next()) {
+            const int r = it.r, c = it.c;
+            if (r == c) continue;
+            double J;
+            if (r == 0) {
+                J = JT[c];
+            } else {
+                J = static_cast<double>(G[r * ld + c]);
+                if (conp) J = fma(-C[r - 1], ds[c], J);
+            }
+            G[r * ld + c] = static_cast<MT>(fma(-gh, J, 0.0));
+        }
+        for (int r = lane; r < n; r += TEAM) {
+            double J;
+            if (r == 0) {
+                J = JT[0];
+            } else {
+                J = static_cast<double>(G[r * ld + r]);
+                if (conp) {
+                    J = fma(-C[r - 1], ds[r], J);
+                    J -= si.sdil;
+                }
+            }
+            G[r * ld + r] = static_cast<MT>(fma(-gh, J, 1.0));
+        }
     }
     team_sync<TEAM>();
 }

@@ -519,6 +519,42 @@ def with_sri_plog(mech: Mechanism, n_sri: int, n_plog: int, seed: int = 0) -> Me
     return m
 
 
+def with_three_species_sides(mech: Mechanism) -> Mechanism:
+    """A copy of a mechanism holding H, OH, H2, H2O, HO2, O2 and N2 (the
+    9-species set) with two more reversible elementary reactions that have
+    three species on one side (the stoichiometric slots the generated
+    mechanisms never fill): H + OH + H2 <=> H2O + H2 (a termolecular
+    recombination with H2 as a named collider; A = 1e10 m^6/(kmol^2 s),
+    b = 0, Ea = 0) and HO2 + N2 <=> H + O2 + N2 (a dissociation; A = 1e12
+    m^3/(kmol s), b = 0, Ea = 48 kcal/mol)."""
+    m = mech.copy()
+    ix = {s: m.names.index(s) for s in ("H", "OH", "H2", "H2O", "HO2", "O2", "N2")}
+    add = [((ix["H"], ix["OH"], ix["H2"]), (ix["H2O"], ix["H2"], -1), (math.log(1e10), 0.0, 0.0)),
+           ((ix["HO2"], ix["N2"], -1), (ix["H"], ix["O2"], ix["N2"]), (math.log(1e12), 0.0, 48.0 * CAL))]
+    k = len(add)
+
+    def rows(idx):
+        a = np.array(idx, dtype=np.int32)
+        return a, (a >= 0).astype(np.int32)
+
+    rf = [rows(f) for f, _, _ in add]
+    rr = [rows(r) for _, r, _ in add]
+    m.rtype = np.concatenate([m.rtype, np.full(k, RXN_ELEMENTARY, dtype=m.rtype.dtype)])
+    m.reversible = np.concatenate([m.reversible, np.ones(k, dtype=m.reversible.dtype)])
+    m.rf_idx = np.vstack([m.rf_idx] + [a for a, _ in rf]).astype(np.int32)
+    m.rf_nu = np.vstack([m.rf_nu] + [n for _, n in rf]).astype(np.int32)
+    m.rr_idx = np.vstack([m.rr_idx] + [a for a, _ in rr]).astype(np.int32)
+    m.rr_nu = np.vstack([m.rr_nu] + [n for _, n in rr]).astype(np.int32)
+    m.arr = np.vstack([m.arr, [a for _, _, a in add]])
+    m.arr0 = np.vstack([m.arr0, np.zeros((k, 3))])
+    m.troe = np.vstack([m.troe, np.zeros((k, 4))])
+    m.eff_ptr = np.concatenate([m.eff_ptr, np.full(k, m.eff_ptr[-1], dtype=m.eff_ptr.dtype)])
+    m.sri = np.vstack([m.sri, np.zeros((k, 5))])
+    m.plog_ptr = np.concatenate([m.plog_ptr, np.full(k, m.plog_ptr[-1], dtype=m.plog_ptr.dtype)])
+    m.validate()
+    return m
+
+
 # ----------------------------------------------------------------------------
 # small hand-built mechanisms used by closed-form tests
 

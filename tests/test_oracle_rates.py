@@ -293,3 +293,40 @@ def test_equilibrium_constant_sum_nu_two(mechs, reverse):
         g = r.thermo(T[c])["g"]
         K = np.exp(-(nu @ (m.W * g)) / (R * T[c])) * np.power(101325.0 / (R * T[c]), nu.sum())
         assert kf[0] / kr[0] == pytest.approx(K, rel=1e-12)
+
+
+def test_three_species_sides():
+    """Reactions with three species on one side (H + OH + H2 <=> H2O + H2,
+    HO2 + N2 <=> H + O2 + N2): k_f is the Arrhenius closed form, q is the
+    mass-action difference with all three concentration factors, K = kf/kr
+    carries (p_ref/RT)^{sum nu} at sum nu = -1 and +1 from the three-slot
+    side, and the oracle's Jacobian equals complex-step derivatives of its S
+    (CONV and CONP)."""
+    from test_oracle_jacobian import complex_step_jacobian
+    m = inputs.with_three_species_sides(inputs.gen_mechanism("h2"))
+    r = oracle.RefMech(m)
+    sp = {s: m.names.index(s) for s in ("H", "OH", "H2", "H2O", "HO2", "O2", "N2")}
+    T, C, _ = inputs.random_states(m, 4, seed=13)
+    j1, j2 = m.nr - 2, m.nr - 1
+    for c in range(4):
+        kf, kr, q = r.rates(T[c], C[c])
+        assert kf[j1] == pytest.approx(1e10, rel=1e-13)
+        assert kf[j2] == pytest.approx(1e12 * math.exp(-48.0 * inputs.CAL / (R * T[c])), rel=1e-12)
+        x = C[c]
+        fwd1, rev1 = kf[j1] * x[sp["H"]] * x[sp["OH"]] * x[sp["H2"]], kr[j1] * x[sp["H2O"]] * x[sp["H2"]]
+        fwd2, rev2 = kf[j2] * x[sp["HO2"]] * x[sp["N2"]], kr[j2] * x[sp["H"]] * x[sp["O2"]] * x[sp["N2"]]
+        assert q[j1] == pytest.approx(fwd1 - rev1, rel=1e-12, abs=1e-13 * (fwd1 + rev1))
+        assert q[j2] == pytest.approx(fwd2 - rev2, rel=1e-12, abs=1e-13 * (fwd2 + rev2))
+        g = r.thermo(T[c])["g"]
+        for j, dG, snu in ((j1, g[sp["H2O"]] * m.W[sp["H2O"]] - g[sp["H"]] * m.W[sp["H"]]
+                            - g[sp["OH"]] * m.W[sp["OH"]], -1),
+                           (j2, g[sp["H"]] * m.W[sp["H"]] + g[sp["O2"]] * m.W[sp["O2"]]
+                            - g[sp["HO2"]] * m.W[sp["HO2"]], 1)):
+            K = math.exp(-dG / (R * T[c])) * (101325.0 / (R * T[c])) ** snu
+            assert kf[j] / kr[j] == pytest.approx(K, rel=1e-11)
+        y = np.concatenate([[T[c]], C[c]])
+        for reactor in (oracle.CONV, oracle.CONP):
+            Ja = r.jacobian(T[c], C[c], reactor)[0]
+            Jc = complex_step_jacobian(r, y, reactor)
+            scale = np.maximum(np.abs(Jc), 1e-13 * np.abs(Jc).max(axis=1, keepdims=True) + 1e-300)
+            assert np.max(np.abs(Ja - Jc) / scale) < 1e-10

@@ -37,6 +37,21 @@ def test_jacobian_matches_complex_step(mechs, ref, kind, reactor):
         assert np.max(np.abs(Ja - Jc) / scale) < 1e-10
 
 
+@pytest.mark.parametrize("reactor", [oracle.CONV, oracle.CONP])
+def test_jacobian_matches_complex_step_160_species(reactor):
+    """The same pin on the 160-species / 900-reaction mechanism (falloff and
+    third-body reactions with 3-6 efficiencies each), two random states."""
+    m = inputs.gen_mechanism("c7")
+    r = oracle.RefMech(m)
+    T, C, p = inputs.random_states(m, 2, seed=23)
+    for c in range(2):
+        y = np.concatenate([[T[c]], C[c]])
+        Ja = r.jacobian(T[c], C[c], reactor)[0]
+        Jc = complex_step_jacobian(r, y, reactor)
+        scale = np.maximum(np.abs(Jc), 1e-13 * np.abs(Jc).max(axis=1, keepdims=True) + 1e-300)
+        assert np.max(np.abs(Ja - Jc) / scale) < 1e-10
+
+
 def test_jacobian_with_zero_concentrations(mechs, ref):
     """Exact at C_i = 0 (products of concentrations differentiated exactly)."""
     m, r = mechs["h2"], ref["h2"]

@@ -178,6 +178,20 @@ def test_mass_and_element_conservation(mechs, ref, kind, reactor):
         assert np.all(np.abs(el.sum(1)) <= 1e-13 * np.abs(el).sum(1) + 1e-300)
 
 
+def test_conservation_160_species():
+    """Mass and every element conserved by omega at 160 species / 900
+    reactions (C, H, O, N, Ar), on random states."""
+    m = inputs.gen_mechanism("c7")
+    r = oracle.RefMech(m)
+    T, C, p = inputs.random_states(m, 16, seed=19)
+    w = r.source(T, C, oracle.CONV)[:, 1:]
+    mass = w * m.W
+    assert np.all(np.abs(mass.sum(1)) <= 1e-13 * np.abs(mass).sum(1))
+    for k in range(len(m.elements)):
+        el = w * m.comp[:, k]
+        assert np.all(np.abs(el.sum(1)) <= 1e-13 * np.abs(el).sum(1) + 1e-300)
+
+
 def test_production_rates_are_stoichiometric_sums(mechs, ref):
     """omega_i = sum_j nu_ij q_j with the oracle's own q_j; omega_T from the
     oracle's own mass-specific u and c_v (eq. temperature_source)."""
